@@ -1,0 +1,54 @@
+"""The seeded input generators: SplitMix64 against its published output,
+draw ranges, lattice sizes, vacancies, and the workload recipes."""
+import numpy as np
+
+from tbpm_inputs import lattice, rng, workloads
+
+
+def test_splitmix64_published_sequence():
+    # SplitMix64 seeded with 0 yields 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f
+    with np.errstate(over="ignore"):
+        states = rng.GAMMA * np.arange(1, 4, dtype=np.uint64)
+    out = [int(v) for v in rng.mix64(states)]
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_draws_are_counter_based_and_in_range():
+    u = rng.uniform(5, 7, 1000)
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert np.array_equal(rng.uniform(5, 7, 10, offset=990), u[990:])
+    assert not np.array_equal(rng.uniform(5, 8, 10), u[:10])
+    x = rng.normal(9, 1, 200000)
+    assert abs(x.mean()) < 0.01 and abs(x.std() - 1.0) < 0.01
+    th = rng.phases(3, 2, 100)
+    assert th.shape == (2, 100) and th.min() >= 0 and th.max() < 2 * np.pi
+
+
+def test_graphene_counts_and_vacancies():
+    g = lattice.graphene(10, 12, pbc=True)
+    assert g.n_orb == 240 and g.n_hop == 360
+    pairs = {(min(a, b), max(a, b)) for a, b in zip(g.hop_i, g.hop_j)}
+    assert len(pairs) == g.n_hop and all(a != b for a, b in pairs)
+    deg = np.bincount(np.concatenate([g.hop_i, g.hop_j]), minlength=g.n_orb)
+    assert np.all(deg == 3)
+    o = lattice.graphene(10, 12, pbc=False)
+    assert o.n_hop == 360 - 12 - 10
+    v = lattice.graphene(20, 20, pbc=True, seed=4, vacancy_frac=0.01, onsite_w=1.0)
+    assert v.n_orb == 800 - 8 and v.meta["vacancies"] == 8
+    assert v.hop_i.max() < v.n_orb and v.hop_j.max() < v.n_orb
+    assert v.onsite.shape == (v.n_orb,) and np.all(np.abs(v.onsite) <= 0.5)
+    deg = np.bincount(np.concatenate([v.hop_i, v.hop_j]), minlength=v.n_orb)
+    assert deg.max() == 3 and deg.min() >= 1
+
+
+def test_workload_recipes():
+    w = workloads.graphene_dos()
+    assert w.sample.n_orb == 8192 and w.s == 9.0 and w.n_steps == 1024
+    seed, Ls, Ws, seeds = workloads.batch_params()
+    assert len(Ls) == 32 and set(Ls) <= set(workloads.BATCH_SIDES)
+    assert all(0 <= W < 2 for W in Ws) and len(set(seeds)) == 32
+    small = workloads.batched_graphene(n_samples=3, n_states=2, sides=(4, 6))
+    assert small.n_samples == 3 and small.offsets[-1] == small.sample.n_orb
+    th = small.thetas()
+    assert [t.shape for t in th] == [(2, int(small.offsets[k + 1] - small.offsets[k]))
+                                     for k in range(3)]
