@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the TBPM time-evolution path on GB300.
+
+Workload: disordered periodic graphene, 2048 x 2048 cells (8,388,608 sites,
+1% vacancies -> 8,304,722 orbitals), Anderson onsite U[-0.5, 0.5] eV,
+t = -2.7 eV, s = 9.5 eV, 4 random-phase states, 1024 steps of z = s tau =
+pi/2 (M = 16 coefficients, 15 sparse products per step), DOS on 4096 bins.
+One step of this benchmark is the whole path on that input: Hamiltonian
+build on the GPU, initial states, 1024 time steps, correlation and DOS.
+
+Metric: orbital-Chebyshev-steps/s = N_orb * states * steps * (M - 1) / time.
+``value`` is the complex-FP32 form (FP64 reductions and norm carry); the
+FP64 form, its speedup ratio and the DOS L1 distance between the two are in
+``fp64_form``.  ``--impl reference`` times the CPU FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--L", type=int, default=2048, help="lattice side (default: the full workload)")
+    ap.add_argument("--time-steps", type=int, default=1024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def n_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def workload_inputs(L, n_steps, rank):
+    from tbpm_inputs import rng, workloads
+    w = workloads.disordered_graphene(L=L, n_steps=n_steps)
+    # weak scaling: rank r propagates its own states (seed offset by the rank)
+    seed = w.sample_seeds[0] + 7919 * rank
+    theta = rng.phases(seed, w.n_states, w.sample.n_orb)
+    return w, theta
+
+
+def config_dict(w, args, world):
+    return {"workload": f"disordered_graphene_{args.L}x{args.L}",
+            "n_orb": int(w.sample.n_orb), "n_bonds": int(w.sample.n_hop),
+            "states_per_gpu": w.n_states, "time_steps": w.n_steps, "z": "pi/2",
+            "s_eV": w.s, "chebyshev_products_per_step": None, "dos_bins": w.n_energies,
+            "onsite_disorder_eV": "U[-0.5,0.5]", "vacancies": "1%",
+            "l2": "inputs larger than L2 (state vectors 266 MB FP32 / 531 MB FP64)",
+            "parallelism": f"replicas x{world} (states sharded, no collective)"}
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in Path(self.path).read_text().splitlines():
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(f[1]), max=float(f[2]), power=float(f[3]),
+                                     hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+                except ValueError:
+                    continue
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        loaded = [r for r in rows if r["power"] > 300] or rows
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded),
+                "sm_max_mhz": max(r["max"] for r in rows),
+                "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": max(r["power"] for r in rows),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ reference --
+def oracle_sample(w, theta, budget_s=15.0):
+    """Time the CPU FP64 oracle, as it stands, on a bounded sample of the same
+    workload: one state, the first k time steps (k sized to ~budget_s)."""
+    import oracle
+    psi0 = oracle.phase_states(theta[:1])
+    t0 = time.perf_counter()
+    oracle.propagate(w.sample, w.s, w.z, 1, psi0)
+    one = time.perf_counter() - t0
+    k = max(1, min(w.n_steps, int(budget_s / max(one, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.propagate(w.sample, w.s, w.z, k, psi0)
+    dt = time.perf_counter() - t0
+    M = oracle.n_terms(w.z)
+    units = w.sample.n_orb * 1 * k * (M - 1)
+    return dict(value=units / dt, unit="orbital-Chebyshev-steps/s", cores=1, kind="oracle",
+                sample=f"1 state x {k} time steps of the {w.sample.n_orb}-orbital workload "
+                       f"(single-threaded C, {dt:.1f} s)"), dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w, theta = workload_inputs(args.L, args.time_steps, 0)
+    M = 16
+    per_step_budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    vals = []
+    times = []
+    sample_desc = None
+    for i in range(args.warmup + args.steps):
+        cb, dt = oracle_sample(w, theta, per_step_budget)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+            times.append(dt)
+            sample_desc = cb["sample"]
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "orbital-Chebyshev-steps/s", "value": v,
+            "unit": "orbital-Chebyshev-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w, args, 1),
+            "cpu_baseline": {"value": v, "unit": "orbital-Chebyshev-steps/s", "cores": 1,
+                             "kind": "oracle", "sample": sample_desc},
+            "e2e": {"value": v, "unit": "orbital-Chebyshev-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    line["config"]["chebyshev_products_per_step"] = M - 1
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- gb300 leg --
+def kernel_traffic():
+    """DRAM bytes per launch of the interior term kernel from the committed
+    ncu summary, valid only while the kernel source is unchanged."""
+    p = ROOT / "profiles" / "term_kernel_traffic.json"
+    if not p.exists():
+        return None, None
+    d = json.loads(p.read_text())
+    src = ROOT / "paper_2209_00806_gb300" / "csrc" / "cheb_kernels.cu"
+    h = hashlib.sha256(src.read_bytes()).hexdigest()
+    if d.get("source_sha256") != h:
+        return None, d
+    return d, d
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2209_00806_gb300 as tb
+    from paper_2209_00806_gb300 import _native as N
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    w, theta = workload_inputs(args.L, args.time_steps, rank)
+    smp = w.sample
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    d_on = torch.as_tensor(smp.onsite, device=dev)
+    d_hi = torch.as_tensor(smp.hop_i, device=dev)
+    d_hj = torch.as_tensor(smp.hop_j, device=dev)
+    d_hv = torch.as_tensor(smp.hop_v, device=dev)
+    d_th = torch.as_tensor(theta, device=dev)
+    S, NT = w.n_states, w.n_steps
+    M = len(tb.tbpm_bessel_coefficients(w.z))
+    units_per_step = smp.n_orb * S * NT * (M - 1)
+    prop = tb.Propagator(local, stream.cuda_stream)
+    corr_d = torch.empty((1, S, NT + 1), dtype=torch.complex128, device=dev)
+
+    def one_step(precision, flags):
+        prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s)
+        prop.set_phase_states(d_th)
+        prop.propagate(w.z, NT, precision, out=corr_d, flags=flags)
+        c = corr_d.mean(dim=1)[0].cpu().numpy()
+        return tb.dos(c, w.tau, *w.e_range, w.n_energies)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    def timed(precision, flags):
+        for _ in range(args.warmup):
+            one_step(precision, flags)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st_acc = {"ms_term": 0.0, "n_term": 0, "ms_total": 0.0, "launches": 0, "renorm": 0,
+                  "drift": 0.0}
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                res = one_step(precision, flags)
+                st = prop.stats()
+                st_acc["ms_term"] += st["ms_term_avg"] * st["term_launches"]
+                st_acc["n_term"] += st["term_launches"]
+                st_acc["launches"] += st["kernel_launches"] + 12   # + builder kernels
+                st_acc["renorm"] += st["renormalisations"]
+                st_acc["drift"] = max(st_acc["drift"], st["max_norm_drift"])
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        st = prop.stats()
+        ms_term = st_acc["ms_term"] / max(1, st_acc["n_term"])
+        return dict(ms=ms, res=res, stats=st, ms_term=ms_term, clocks=clk.summary(),
+                    launches=st_acc["launches"], renorm=st_acc["renorm"], drift=st_acc["drift"])
+
+    PROFILE = N.TBPM_PROP_PROFILE
+    r32 = timed(N.TBPM_FP32, PROFILE)
+    r64 = timed(N.TBPM_FP64, PROFILE)
+
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+
+    def roofline(r, key):
+        b = r["stats"]["bytes_term"]
+        ach = b / (r["ms_term"] * 1e-3) / 1e9
+        tr, meta = kernel_traffic()
+        traffic = None
+        if tr is not None and key in tr:
+            traffic = tr[key]["dram_bytes_per_launch_full_size"]
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": traffic, "peak_source": peak_note,
+                "kernel": "interior Clenshaw term (k_term)", "algorithmic_bytes_per_launch": b,
+                "ms_per_launch": r["ms_term"]}
+
+    total_units = units_per_step * args.steps * world
+    v32 = total_units / (r32["ms"] * 1e-3)
+    v64 = total_units / (r64["ms"] * 1e-3)
+    en, d32 = r32["res"]
+    _, d64 = r64["res"]
+    l1 = float(np.sum(np.abs(d32 - d64)) * (en[1] - en[0]))
+
+    # end to end through the C ABI with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        h_on = torch.from_numpy(np.ascontiguousarray(smp.onsite)).pin_memory()
+        h_hi = torch.from_numpy(np.ascontiguousarray(smp.hop_i)).pin_memory()
+        h_hj = torch.from_numpy(np.ascontiguousarray(smp.hop_j)).pin_memory()
+        h_hv = torch.from_numpy(np.ascontiguousarray(smp.hop_v)).pin_memory()
+        h_th = torch.from_numpy(np.ascontiguousarray(theta)).pin_memory()
+        h_c = torch.empty((1, S, NT + 1), dtype=torch.complex128).pin_memory()
+
+        def host_step():
+            N.tbpm_build_hamiltonian(prop.ctx, smp.n_orb, h_on.data_ptr(), smp.n_hop,
+                                     h_hi.data_ptr(), h_hj.data_ptr(), h_hv.data_ptr(), w.s, 1,
+                                     None, N.TBPM_HOST, 0)
+            N.tbpm_set_phase_states(prop.ctx, S, h_th.data_ptr(), N.TBPM_HOST)
+            N.tbpm_propagate(prop.ctx, w.z, NT, N.TBPM_FP32, h_c.data_ptr(), N.TBPM_HOST, 0)
+            c = h_c.numpy().mean(axis=1)[0]
+            return tb.dos(c, w.tau, *w.e_range, w.n_energies)
+
+        for _ in range(args.warmup):
+            host_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = sum(x.numel() * x.element_size() for x in (h_on, h_hi, h_hj, h_hv, h_th))
+        d2h = h_c.numel() * h_c.element_size() + S * (NT + 1) * 8   # correlations + norms
+        e2e = {"value": total_units / dt, "unit": "orbital-Chebyshev-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * dt / args.steps, "precision": "fp32"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _ = oracle_sample(w, theta, 15.0)
+
+    if rank == 0:
+        cfg = config_dict(w, args, world)
+        cfg["chebyshev_products_per_step"] = M - 1
+        cfg["state_groups"] = r32["stats"]["group_width"]
+        line = {
+            "metric": "orbital-Chebyshev-steps/s", "value": v32,
+            "unit": "orbital-Chebyshev-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "reductions": "f64", "data": "synthetic", "config": cfg,
+            "roofline": roofline(r32, "fp32"),
+            "fp64_form": {"value": v64, "ms_per_step": r64["ms"] / args.steps, "dtype": "f64",
+                          "roofline": roofline(r64, "fp64"), "clocks": r64["clocks"],
+                          "max_norm_drift": r64["drift"]},
+            "speedup_fp32_over_fp64": v32 / v64,
+            "dos_l1_fp32_vs_fp64": l1,
+            "fp32_renormalisations": r32["renorm"], "fp32_max_norm_drift": r32["drift"],
+            "e2e": e2e, "gpu_launches": int(r32["launches"]),
+            "clocks": r32["clocks"], "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    prop.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,213 @@
+/*
+ * tbpm.h -- C ABI of the GB300 tight-binding propagation method (TBPM) library.
+ *
+ * The library evolves random initial states under a sparse tight-binding
+ * Hamiltonian, |psi(t + tau)> = exp(-i H tau) |psi(t)>, by the Chebyshev-Bessel
+ * expansion of arXiv 2209.00806 (Sec. 2.2, Eq. psi_t), records the correlation
+ * C(t) = <psi(0)|psi(t)> (Sec. 2.2, Eq. corr_dos) and turns it into a density
+ * of states (Sec. 2.4, Eq. dos_tbpm).  All propagation arithmetic runs in CUDA
+ * kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *  - Status: every int-returning call returns TBPM_OK (0) or one TBPM_E_* code;
+ *    tbpm_last_error() then holds a one-line message.  A failed call leaves
+ *    the context usable unless the code is TBPM_E_CUDA.
+ *  - Complex numbers are two adjacent doubles (re, im), i.e. C99 double
+ *    complex / numpy complex128.
+ *  - Orbital indices are the caller's numbering, 0 .. n_orb-1.  Any internal
+ *    row order is invisible: states and gradients come back in caller order.
+ *  - Pointers marked "host or device" are read from host memory when
+ *    where == TBPM_HOST and from device memory (of the context's device)
+ *    when where == TBPM_DEVICE.  The library copies what it keeps; the caller
+ *    keeps ownership of every pointer it passes.
+ *  - Energies are in eV and times in hbar/eV (hbar = 1).
+ *  - One context per CUDA stream; contexts share no state.  Calls on one
+ *    context must not run concurrently from several host threads.
+ */
+#ifndef TBPM_H
+#define TBPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TBPM_OK 0
+#define TBPM_E_INVALID_ARG 1    /* bad size, index, pointer or flag */
+#define TBPM_E_SPECTRAL_BOUND 2 /* s is below a bound on the spectral radius of H */
+#define TBPM_E_OOM 3            /* device allocation failed */
+#define TBPM_E_CUDA 4           /* a CUDA call failed; the message names it */
+#define TBPM_E_NORM_DRIFT 5     /* |<phi|phi> - 1| exceeded the hard bound */
+#define TBPM_E_NONFINITE 6      /* NaN or Inf met in a state or a reduction */
+#define TBPM_E_TIMEOUT 7        /* a bounded device-side wait gave up */
+#define TBPM_E_STATE 8          /* call order: e.g. propagate before build */
+#define TBPM_E_UNSUPPORTED 9    /* valid request this build does not provide */
+
+/* ---- precision of the propagation --------------------------------------- */
+#define TBPM_FP64 0  /* complex128 states, FP64 H~, FP64 reductions */
+#define TBPM_FP32 1  /* complex64 states, FP32 H~, FP64 reductions and norm carry */
+
+/* ---- where a pointer lives ---------------------------------------------- */
+#define TBPM_HOST 0
+#define TBPM_DEVICE 1
+
+/* ---- window of the DOS transform (Sec. 2.4) ----------------------------- */
+#define TBPM_WINDOW_HANN 0
+
+/* ---- flags of tbpm_build_hamiltonian ------------------------------------ */
+#define TBPM_BUILD_STRICT_BOUND 1 /* fail with TBPM_E_SPECTRAL_BOUND if the
+                                     Gershgorin bound of H exceeds s */
+#define TBPM_BUILD_NO_FP64 2      /* keep only FP32 values (saves memory) */
+#define TBPM_BUILD_NO_FP32 4      /* keep only FP64 values */
+#define TBPM_BUILD_REORDER_RCM 8  /* reverse Cuthill-McKee row order per sample */
+
+/* ---- flags of tbpm_propagate -------------------------------------------- */
+#define TBPM_PROP_PROFILE 1   /* time the kernels with CUDA events (tbpm_stats) */
+#define TBPM_PROP_GRAPH 2     /* replay each time step as a captured CUDA graph */
+#define TBPM_PROP_RESUME 4    /* continue from the current states instead of
+                                 restarting from psi0; C is still <psi0|phi> */
+#define TBPM_PROP_PERSISTENT 8 /* one cooperative launch per time step with a
+                                  bounded grid barrier between terms */
+
+typedef struct tbpm_ctx tbpm_ctx;
+
+/* Counters and timings of the last tbpm_propagate / adjoint on a context. */
+typedef struct tbpm_stats {
+    int n_terms;             /* M: Chebyshev coefficients m = 0 .. M-1 */
+    int n_steps;             /* time steps of the last call */
+    int n_groups;            /* state groups (each one blocked launch set) */
+    int group_width[8];      /* states per group */
+    int64_t n_rows;          /* padded device rows */
+    int64_t nnz;             /* stored off-diagonal entries (incl. padding) */
+    int64_t nnz_true;        /* off-diagonal entries of H (2 x bonds) */
+    int64_t renormalisations;/* FP32: norm-carry events over all states */
+    int64_t kernel_launches; /* kernels launched by the last call */
+    double gershgorin;       /* Gershgorin bound of H~ = H / s (dimensionless) */
+    double ms_total;         /* device time of the last call (PROFILE) */
+    double ms_term_avg;      /* average duration of one interior Chebyshev
+                                term kernel (PROFILE) */
+    double ms_final_avg;     /* average duration of the closing term kernel */
+    double ms_reduce_avg;    /* average duration of the correlation reduction */
+    int64_t term_launches;   /* interior term launches that were timed */
+    double bytes_term;       /* algorithmic bytes of one interior term launch */
+    double max_norm_drift;   /* max over steps and states of |<phi|phi> - 1| */
+} tbpm_stats;
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int tbpm_version(void);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` (a cudaStream_t,
+ * may be NULL for the legacy default stream) is borrowed: the library orders
+ * its work after what is already queued there and makes the stream wait for
+ * its results before each call returns.  The context owns every device
+ * buffer it allocates and frees them in tbpm_destroy. */
+int tbpm_create(tbpm_ctx **ctx, int device, void *cuda_stream);
+void tbpm_destroy(tbpm_ctx *ctx);
+
+/* Message of the last failed call on ctx (empty string if none).  Calls that
+ * fail before a context exists leave their message in a thread-local slot
+ * that tbpm_last_error(NULL) returns. */
+const char *tbpm_last_error(const tbpm_ctx *ctx);
+
+/* a1. Lattice -> Hamiltonian (Sec. 2.1, Eq. ham_mat_finite, with the hopping
+ * convention of Sec. 4.1: a bond (i, j, t) is the matrix element
+ * <phi_i|h|phi_j> = t, the conjugate element H_ji = t is implied), rescaled
+ * to H~ = H / s (Sec. 2.2).
+ *   n_orb          orbitals, 1 .. 2^31 - 1 in total
+ *   onsite         [n_orb] eps_i in eV, host or device, or NULL for zeros
+ *   n_hop, hop_i, hop_j, hop_v
+ *                  [n_hop] bonds, int64 indices and real hoppings in eV, host
+ *                  or device; i != j, both in the same sample.  A pair listed
+ *                  twice adds up.
+ *   s              rescale factor in eV, > 0
+ *   n_samples      independent samples packed block-diagonally (>= 1)
+ *   sample_offsets [n_samples + 1] host int64, orbitals of sample k are
+ *                  sample_offsets[k] .. sample_offsets[k+1]-1; NULL when
+ *                  n_samples == 1
+ *   where          TBPM_HOST or TBPM_DEVICE for all array arguments
+ *   flags          TBPM_BUILD_*
+ * Replaces any previous Hamiltonian and drops any states.  Runs on the GPU:
+ * counting, slice layout (sliced ELLPACK, 32-row slices), fill, per-row
+ * column sort (deterministic), Gershgorin bound.  Errors: INVALID_ARG (sizes,
+ * indices out of range, i == j, bond across samples), SPECTRAL_BOUND (with
+ * TBPM_BUILD_STRICT_BOUND), OOM, CUDA. */
+int tbpm_build_hamiltonian(tbpm_ctx *ctx, int64_t n_orb, const double *onsite,
+                           int64_t n_hop, const int64_t *hop_i, const int64_t *hop_j,
+                           const double *hop_v, double s, int n_samples,
+                           const int64_t *sample_offsets, int where, int flags);
+
+/* Initial states (Sec. 2.2, Eq. ini_state).  psi0 is complex128
+ * [n_states][n_orb] (host or device); state p of sample k is the slice
+ * sample_offsets[k] .. sample_offsets[k+1]-1 of row p, each slice its own
+ * state.  The library does not normalise.  1 <= n_states <= 64. */
+int tbpm_set_states(tbpm_ctx *ctx, int n_states, const double *psi0, int where);
+
+/* Random-phase initial states psi0_i = exp(i theta_i) / sqrt(N_k), N_k the
+ * orbital count of the sample holding i: random complex a_i with
+ * sum |a_i|^2 = 1 per sample (Sec. 2.2).  theta is double
+ * [n_states][n_orb] (host or device), drawn by the caller. */
+int tbpm_set_phase_states(tbpm_ctx *ctx, int n_states, const double *theta, int where);
+
+/* a2. Coefficients of the expansion (Sec. 2.2): J_m(z), m = 0 .. M-1, by
+ * Miller's backward recurrence in FP64 on the host, normalised with
+ * J_0 + 2 sum_k J_2k = 1.  M = first m > z with |J_m(z)| < tol.
+ * J_out holds max_terms doubles; *n_terms receives M.  0 < z <= 1000.
+ * Errors: INVALID_ARG; UNSUPPORTED if M > max_terms. */
+int tbpm_bessel_coefficients(double z, double tol, int max_terms, double *J_out,
+                             int *n_terms);
+
+/* a3-a6. Propagate every state for n_steps steps of tau = z / s and record
+ * C_n = <psi0|phi(n tau)>, n = 0 .. n_steps, per sample and state.
+ *   z          s * tau (> 0); coefficients cut at |J_m(z)| < 1e-15
+ *   precision  TBPM_FP64 or TBPM_FP32 (the Hamiltonian must hold that copy)
+ *   corr_out   complex128 [n_samples][n_states][n_steps + 1], host or device
+ *              (where_out), or NULL to keep C on the device only
+ *   flags      TBPM_PROP_*
+ * Each time step runs M-1 fused sparse-product terms of the Clenshaw form
+ * of the paper's Chebyshev sum and one deterministic FP64 reduction.
+ * In FP32 the norm of each state is carried in FP64: when |<phi|phi> - 1|
+ * exceeds 1e-5 the next step starts from phi / |phi|.
+ * Errors: STATE (no Hamiltonian or states), INVALID_ARG, NORM_DRIFT (drift
+ * above 1e-6 in FP64 or 1e-2 in FP32: s too small), NONFINITE, CUDA. */
+int tbpm_propagate(tbpm_ctx *ctx, double z, int n_steps, int precision, double *corr_out,
+                   int where_out, int flags);
+
+/* State-averaged correlation of the last propagation (Sec. 2.4, the average
+ * over S random states in Eq. dos_tbpm): complex128 [n_samples][n_steps + 1]
+ * written to host or device memory. */
+int tbpm_correlation(tbpm_ctx *ctx, double *corr_avg_out, int where_out);
+
+/* Current states phi(t) of the last propagation in caller order, complex128
+ * [n_states][n_orb] (host or device) -- a checkpoint; tbpm_set_states +
+ * TBPM_PROP_RESUME continues from it. */
+int tbpm_get_states(tbpm_ctx *ctx, double *phi_out, int where_out);
+
+/* Squared norms <phi|phi> per sample, state and step of the last
+ * propagation: double [n_samples][n_states][n_steps + 1], host. */
+int tbpm_get_norms(tbpm_ctx *ctx, double *norms_out);
+
+/* a7. DOS from one averaged correlation C_0 .. C_{n_steps} (host memory),
+ * Sec. 2.4, Eq. dos_tbpm:
+ *   D(E) = (tau/pi) [Re C_0 / 2 + sum_{n=1}^{N-1} w_n Re(exp(i E n tau) C_n)]
+ * (C(-t) = conj C(t), trapezoid rule, one-sided Hann w_n = (1+cos(pi n/N))/2),
+ * at bin centres E_k = e_min + (k + 1/2)(e_max - e_min)/n_e.  Pure host
+ * function, FP64.  D integrates to Re C_0 over a full period 2 pi / tau. */
+int tbpm_dos(const double *corr, int n_steps, double tau, int window, double e_min,
+             double e_max, int n_e, double *energies_out, double *dos_out);
+
+/* Launch shape of the propagation kernels for one precision: states are
+ * split into groups of power-of-two width <= max_group (FP64 <= 8,
+ * FP32 <= 16), each group propagated as one blocked sparse product per term;
+ * threads per block is a power of two in 64..1024.  Chosen by the
+ * library's autotuner or by hand.  Drops the current propagation buffers. */
+int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads);
+
+/* Statistics of the last call on ctx. */
+int tbpm_get_stats(tbpm_ctx *ctx, tbpm_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TBPM_H */

@@ -1,0 +1,955 @@
+// C ABI of the TBPM library: contexts, Hamiltonian build, states, the
+// time-step loop of the Chebyshev propagation, correlations and statistics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "tbpm_internal.cuh"
+
+using namespace tbpm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Group {
+    int B = 0, s0 = 0;
+    void *psi0 = nullptr;        // internal layout, precision of the group
+    void *buf[3] = {nullptr, nullptr, nullptr};
+    double *scale = nullptr;     // [n_samples * B]
+    int cur = 0;                 // buffer holding the current state
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+};
+
+}  // namespace
+
+struct tbpm_ctx {
+    int device = 0;
+    cudaStream_t user = nullptr;
+    cudaStream_t st = nullptr;
+    std::string err;
+
+    // Hamiltonian
+    bool have_h = false;
+    BuildOutput H;
+    int64_t n_orb = 0;
+    int n_samples = 0;
+    double s = 0.0;
+    std::vector<int64_t> sample_off, row_off;
+    int64_t *d_sample_chunk_off = nullptr;
+    double *d_inv_sqrt_n = nullptr;
+
+    // initial states, caller order, complex128 [n_states][n_orb]
+    int n_states = 0;
+    double2 *d_psi_user = nullptr;
+
+    // propagation state
+    int prec = -1;               // precision of the group buffers
+    int max_group[2] = {8, 16};  // widest state group per precision
+    int threads[2] = {256, 256}; // threads per block per precision
+    std::vector<Group> groups;
+    double *d_partial = nullptr;
+    int64_t partial_len = 0;
+    int *d_step = nullptr;       // [n_samples]
+    int *d_flags = nullptr;      // [0] error bits
+    unsigned long long *d_renorm = nullptr;
+    double2 *d_corr = nullptr;
+    double *d_norms = nullptr;
+    int corr_steps = -1;         // n_steps of the buffers above
+    bool have_run = false;
+    std::vector<cudaEvent_t> events;
+    tbpm_stats stats;
+};
+
+namespace {
+
+int fail(tbpm_ctx *c, int code, const std::string &m)
+{
+    if (c) c->err = m;
+    g_last_error = m;
+    return code;
+}
+
+#define CUDA_OR_FAIL(ctx, call)                                                    \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? TBPM_E_OOM : TBPM_E_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+template <typename T>
+int dalloc(tbpm_ctx *c, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? TBPM_E_OOM : TBPM_E_CUDA,
+                    std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                        " bytes: " + cudaGetErrorString(e));
+    }
+    return TBPM_OK;
+}
+
+void free_groups(tbpm_ctx *c)
+{
+    for (auto &g : c->groups) {
+        cudaFree(g.psi0);
+        for (int k = 0; k < 3; ++k) {
+            cudaFree(g.buf[k]);
+            if (g.graph[k]) cudaGraphExecDestroy(g.graph[k]);
+        }
+        cudaFree(g.scale);
+    }
+    c->groups.clear();
+    c->prec = -1;
+    c->have_run = false;
+}
+
+void free_outputs(tbpm_ctx *c)
+{
+    cudaFree(c->d_corr);
+    cudaFree(c->d_norms);
+    c->d_corr = nullptr;
+    c->d_norms = nullptr;
+    c->corr_steps = -1;
+}
+
+void free_hamiltonian(tbpm_ctx *c)
+{
+    free_groups(c);
+    free_outputs(c);
+    free_build(c->H);
+    cudaFree(c->d_sample_chunk_off);
+    cudaFree(c->d_inv_sqrt_n);
+    cudaFree(c->d_psi_user);
+    cudaFree(c->d_partial);
+    cudaFree(c->d_step);
+    c->d_sample_chunk_off = nullptr;
+    c->d_inv_sqrt_n = nullptr;
+    c->d_psi_user = nullptr;
+    c->d_partial = nullptr;
+    c->d_step = nullptr;
+    c->partial_len = 0;
+    c->n_states = 0;
+    c->have_h = false;
+}
+
+// Order our stream after the user's stream.
+int enter(tbpm_ctx *c)
+{
+    CUDA_OR_FAIL(c, cudaSetDevice(c->device));
+    cudaEvent_t e;
+    CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CUDA_OR_FAIL(c, cudaEventRecord(e, c->user));
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->st, e, 0));
+    cudaEventDestroy(e);
+    return TBPM_OK;
+}
+
+// Make the user's stream wait for our work.
+int leave(tbpm_ctx *c)
+{
+    cudaEvent_t e;
+    CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CUDA_OR_FAIL(c, cudaEventRecord(e, c->st));
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->user, e, 0));
+    cudaEventDestroy(e);
+    return TBPM_OK;
+}
+
+// Copy `bytes` from host or device memory into a fresh device buffer.
+template <typename T>
+int stage(tbpm_ctx *c, const T *src, size_t count, int where, T **dst, bool *owned)
+{
+    *owned = false;
+    *dst = nullptr;
+    if (!src) return TBPM_OK;
+    if (where == TBPM_DEVICE) {
+        *dst = const_cast<T *>(src);
+        return TBPM_OK;
+    }
+    int rc = dalloc(c, dst, count);
+    if (rc) return rc;
+    *owned = true;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, c->st));
+    return TBPM_OK;
+}
+
+// Reverse Cuthill-McKee order of one sample's orbitals [lo, hi): BFS from a
+// minimum-degree unvisited orbital, neighbours in increasing degree, order
+// reversed.  perm[u] = position of orbital u within its sample.
+void rcm_sample(int64_t lo, int64_t hi, const std::vector<int64_t> &adj_ptr,
+                const std::vector<int32_t> &adj, std::vector<int32_t> &perm)
+{
+    const int64_t n = hi - lo;
+    std::vector<int32_t> order;
+    order.reserve(n);
+    std::vector<char> seen(n, 0);
+    std::vector<int64_t> by_deg(n);
+    for (int64_t k = 0; k < n; ++k) by_deg[k] = k;
+    auto deg = [&](int64_t u) { return adj_ptr[lo + u + 1] - adj_ptr[lo + u]; };
+    std::stable_sort(by_deg.begin(), by_deg.end(),
+                     [&](int64_t a, int64_t b) { return deg(a) < deg(b); });
+    std::vector<int32_t> nb;
+    for (int64_t start : by_deg) {
+        if (seen[start]) continue;
+        size_t head = order.size();
+        order.push_back((int32_t)start);
+        seen[start] = 1;
+        while (head < order.size()) {
+            int64_t u = order[head++];
+            nb.clear();
+            for (int64_t e = adj_ptr[lo + u]; e < adj_ptr[lo + u + 1]; ++e) {
+                int64_t v = adj[e] - lo;
+                if (!seen[v]) { seen[v] = 1; nb.push_back((int32_t)v); }
+            }
+            std::stable_sort(nb.begin(), nb.end(),
+                             [&](int32_t a, int32_t b) { return deg(a) < deg(b); });
+            order.insert(order.end(), nb.begin(), nb.end());
+        }
+    }
+    for (int64_t k = 0; k < n; ++k) perm[lo + order[n - 1 - k]] = (int32_t)k;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+extern "C" int tbpm_version(void) { return 10000; }
+
+extern "C" const char *tbpm_last_error(const tbpm_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+extern "C" int tbpm_create(tbpm_ctx **out, int device, void *stream)
+{
+    if (!out) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx pointer is NULL");
+    *out = nullptr;
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || n_dev == 0)
+        return fail(nullptr, TBPM_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    if (device < 0 || device >= n_dev)
+        return fail(nullptr, TBPM_E_INVALID_ARG, "device index out of range");
+    tbpm_ctx *c = new tbpm_ctx();
+    c->device = device;
+    c->user = (cudaStream_t)stream;
+    memset(&c->stats, 0, sizeof(c->stats));
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_renorm, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        std::string m = std::string("context setup: ") + cudaGetErrorString(e);
+        tbpm_destroy(c);
+        return fail(nullptr, TBPM_E_CUDA, m);
+    }
+    *out = c;
+    return TBPM_OK;
+}
+
+extern "C" void tbpm_destroy(tbpm_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->st) cudaStreamSynchronize(c->st);
+    free_hamiltonian(c);
+    cudaFree(c->d_flags);
+    cudaFree(c->d_renorm);
+    for (auto e : c->events) cudaEventDestroy(e);
+    if (c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *onsite,
+                                      int64_t n_hop, const int64_t *hop_i,
+                                      const int64_t *hop_j, const double *hop_v, double s,
+                                      int n_samples, const int64_t *sample_offsets, int where,
+                                      int flags)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (n_orb < 1 || n_orb > INT32_MAX - (int64_t)kChunkRows * 64)
+        return fail(c, TBPM_E_INVALID_ARG, "n_orb out of range");
+    if (n_hop < 0 || (n_hop > 0 && (!hop_i || !hop_j || !hop_v)))
+        return fail(c, TBPM_E_INVALID_ARG, "bond arrays missing");
+    if (!(s > 0.0) || !std::isfinite(s)) return fail(c, TBPM_E_INVALID_ARG, "s must be > 0");
+    if (n_samples < 1 || (n_samples > 1 && !sample_offsets))
+        return fail(c, TBPM_E_INVALID_ARG, "bad sample description");
+    if (where != TBPM_HOST && where != TBPM_DEVICE)
+        return fail(c, TBPM_E_INVALID_ARG, "where must be TBPM_HOST or TBPM_DEVICE");
+    if ((flags & TBPM_BUILD_NO_FP64) && (flags & TBPM_BUILD_NO_FP32))
+        return fail(c, TBPM_E_INVALID_ARG, "both value precisions dropped");
+    std::vector<int64_t> off(n_samples + 1);
+    if (sample_offsets) {
+        for (int k = 0; k <= n_samples; ++k) off[k] = sample_offsets[k];
+    } else {
+        off[0] = 0;
+        off[1] = n_orb;
+    }
+    if (off[0] != 0 || off[n_samples] != n_orb)
+        return fail(c, TBPM_E_INVALID_ARG, "sample offsets must run from 0 to n_orb");
+    for (int k = 0; k < n_samples; ++k)
+        if (off[k + 1] <= off[k]) return fail(c, TBPM_E_INVALID_ARG, "empty or unsorted sample");
+    int rc = enter(c);
+    if (rc) return rc;
+    free_hamiltonian(c);
+
+    std::vector<int64_t> row_off(n_samples + 1, 0);
+    for (int k = 0; k < n_samples; ++k) {
+        int64_t n_k = off[k + 1] - off[k];
+        row_off[k + 1] = row_off[k] + (n_k + kChunkRows - 1) / kChunkRows * kChunkRows;
+    }
+    if (row_off[n_samples] > INT32_MAX) return fail(c, TBPM_E_INVALID_ARG, "too many rows");
+
+    // optional reverse Cuthill-McKee order per sample (host)
+    std::vector<int32_t> perm;
+    if (flags & TBPM_BUILD_REORDER_RCM) {
+        std::vector<int64_t> hi(n_hop), hj(n_hop);
+        if (where == TBPM_DEVICE) {
+            CUDA_OR_FAIL(c, cudaMemcpy(hi.data(), hop_i, n_hop * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            CUDA_OR_FAIL(c, cudaMemcpy(hj.data(), hop_j, n_hop * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        } else {
+            memcpy(hi.data(), hop_i, n_hop * sizeof(int64_t));
+            memcpy(hj.data(), hop_j, n_hop * sizeof(int64_t));
+        }
+        std::vector<int64_t> ptr(n_orb + 1, 0);
+        for (int64_t b = 0; b < n_hop; ++b) {
+            if (hi[b] < 0 || hi[b] >= n_orb || hj[b] < 0 || hj[b] >= n_orb)
+                return fail(c, TBPM_E_INVALID_ARG, "invalid bond list: index out of range");
+            ++ptr[hi[b] + 1];
+            ++ptr[hj[b] + 1];
+        }
+        for (int64_t u = 0; u < n_orb; ++u) ptr[u + 1] += ptr[u];
+        std::vector<int32_t> adj(ptr[n_orb]);
+        std::vector<int64_t> fillp(ptr.begin(), ptr.end() - 1);
+        for (int64_t b = 0; b < n_hop; ++b) {
+            adj[fillp[hi[b]]++] = (int32_t)hj[b];
+            adj[fillp[hj[b]]++] = (int32_t)hi[b];
+        }
+        for (int k = 0; k < n_samples; ++k)
+            for (int64_t u = off[k]; u < off[k + 1]; ++u)
+                for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e)
+                    if (adj[e] < off[k] || adj[e] >= off[k + 1])
+                        return fail(c, TBPM_E_INVALID_ARG, "invalid bond list: bond joins two samples");
+        perm.assign(n_orb, 0);
+        for (int k = 0; k < n_samples; ++k) rcm_sample(off[k], off[k + 1], ptr, adj, perm);
+    }
+
+    // stage inputs on the device
+    const double *d_on = nullptr, *d_hv = nullptr;
+    const int64_t *d_hi = nullptr, *d_hj = nullptr;
+    bool o1, o2, o3, o4;
+    rc = stage(c, onsite, n_orb, where, const_cast<double **>(&d_on), &o1);
+    if (!rc) rc = stage(c, hop_i, n_hop, where, const_cast<int64_t **>(&d_hi), &o2);
+    if (!rc) rc = stage(c, hop_j, n_hop, where, const_cast<int64_t **>(&d_hj), &o3);
+    if (!rc) rc = stage(c, hop_v, n_hop, where, const_cast<double **>(&d_hv), &o4);
+    int64_t *d_off = nullptr, *d_row_off = nullptr;
+    int32_t *d_perm = nullptr;
+    if (!rc) rc = dalloc(c, &d_off, n_samples + 1);
+    if (!rc) rc = dalloc(c, &d_row_off, n_samples + 1);
+    if (!rc && !perm.empty()) rc = dalloc(c, &d_perm, n_orb);
+    auto release = [&]() {
+        if (o1) cudaFree((void *)d_on);
+        if (o2) cudaFree((void *)d_hi);
+        if (o3) cudaFree((void *)d_hj);
+        if (o4) cudaFree((void *)d_hv);
+        cudaFree(d_off);
+        cudaFree(d_row_off);
+        cudaFree(d_perm);
+    };
+    if (rc) { release(); return rc; }
+    cudaMemcpyAsync(d_off, off.data(), (n_samples + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(d_row_off, row_off.data(), (n_samples + 1) * sizeof(int64_t),
+                    cudaMemcpyHostToDevice, c->st);
+    if (d_perm)
+        cudaMemcpyAsync(d_perm, perm.data(), n_orb * sizeof(int32_t), cudaMemcpyHostToDevice, c->st);
+
+    BuildInput in;
+    in.n_orb = n_orb;
+    in.onsite = d_on;
+    in.n_hop = n_hop;
+    in.hop_i = d_hi;
+    in.hop_j = d_hj;
+    in.hop_v = d_hv;
+    in.inv_s = 1.0 / s;
+    in.n_samples = n_samples;
+    in.d_sample_off = d_off;
+    in.d_sample_row_off = d_row_off;
+    in.d_perm = d_perm;
+    std::string msg;
+    rc = build_sell(in, !(flags & TBPM_BUILD_NO_FP64), !(flags & TBPM_BUILD_NO_FP32), c->H,
+                    c->st, msg);
+    cudaStreamSynchronize(c->st);
+    release();
+    if (rc) {
+        free_build(c->H);
+        return fail(c, rc, msg);
+    }
+    c->n_orb = n_orb;
+    c->n_samples = n_samples;
+    c->s = s;
+    c->sample_off = off;
+    c->row_off = row_off;
+    std::vector<int64_t> chunk_off(n_samples + 1);
+    std::vector<double> inv_sqrt(n_samples);
+    for (int k = 0; k <= n_samples; ++k) chunk_off[k] = row_off[k] / kChunkRows;
+    for (int k = 0; k < n_samples; ++k) inv_sqrt[k] = 1.0 / sqrt((double)(off[k + 1] - off[k]));
+    rc = dalloc(c, &c->d_sample_chunk_off, n_samples + 1);
+    if (!rc) rc = dalloc(c, &c->d_inv_sqrt_n, n_samples);
+    if (!rc) rc = dalloc(c, &c->d_step, n_samples);
+    if (rc) { free_hamiltonian(c); return rc; }
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_sample_chunk_off, chunk_off.data(),
+                                    (n_samples + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_inv_sqrt_n, inv_sqrt.data(), n_samples * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->st));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));
+    c->have_h = true;
+    c->stats.gershgorin = c->H.gershgorin;
+    c->stats.n_rows = c->H.n_rows;
+    c->stats.nnz = c->H.nnz_pad;
+    c->stats.nnz_true = c->H.nnz_true;
+    if ((flags & TBPM_BUILD_STRICT_BOUND) && c->H.gershgorin > 1.0) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "Gershgorin bound of H is %.6g eV, above s = %.6g eV",
+                 c->H.gershgorin * s, s);
+        free_hamiltonian(c);
+        return fail(c, TBPM_E_SPECTRAL_BOUND, buf);
+    }
+    c->err.clear();
+    return leave(c);
+}
+
+static int set_states_common(tbpm_ctx *c, int n_states, const double *src, int where,
+                             bool phases)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->have_h) return fail(c, TBPM_E_STATE, "build the Hamiltonian first");
+    if (n_states < 1 || n_states > kMaxStates || !src)
+        return fail(c, TBPM_E_INVALID_ARG, "n_states must be 1..64 with data");
+    if (where != TBPM_HOST && where != TBPM_DEVICE)
+        return fail(c, TBPM_E_INVALID_ARG, "where must be TBPM_HOST or TBPM_DEVICE");
+    int rc = enter(c);
+    if (rc) return rc;
+    free_groups(c);
+    cudaFree(c->d_psi_user);
+    c->d_psi_user = nullptr;
+    c->n_states = 0;
+    const size_t count = (size_t)n_states * c->n_orb;
+    rc = dalloc(c, &c->d_psi_user, count);
+    if (rc) return rc;
+    if (phases) {
+        const double *d_theta = nullptr;
+        bool owned = false;
+        rc = stage(c, src, count, where, const_cast<double **>(&d_theta), &owned);
+        if (rc) return rc;
+        CUDA_OR_FAIL(c, launch_phase_user(d_theta, c->n_orb, n_states, c->d_inv_sqrt_n,
+                                          c->H.orb_sample, c->d_psi_user, c->st));
+        if (owned) {
+            cudaStreamSynchronize(c->st);
+            cudaFree((void *)d_theta);
+        }
+    } else {
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_psi_user, src, count * sizeof(double2),
+                                        where == TBPM_HOST ? cudaMemcpyHostToDevice
+                                                           : cudaMemcpyDeviceToDevice,
+                                        c->st));
+    }
+    c->n_states = n_states;
+    c->err.clear();
+    return leave(c);
+}
+
+extern "C" int tbpm_set_states(tbpm_ctx *c, int n_states, const double *psi0, int where)
+{
+    return set_states_common(c, n_states, psi0, where, false);
+}
+
+extern "C" int tbpm_set_phase_states(tbpm_ctx *c, int n_states, const double *theta, int where)
+{
+    return set_states_common(c, n_states, theta, where, true);
+}
+
+extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group, int threads)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (precision != TBPM_FP64 && precision != TBPM_FP32)
+        return fail(c, TBPM_E_INVALID_ARG, "bad precision");
+    const int cap = precision == TBPM_FP64 ? 8 : 16;
+    if (max_group < 1 || max_group > cap || (max_group & (max_group - 1)))
+        return fail(c, TBPM_E_INVALID_ARG, "group width must be a power of two within the cap");
+    if (threads < 64 || threads > 1024 || (threads & (threads - 1)))
+        return fail(c, TBPM_E_INVALID_ARG, "threads must be a power of two in 64..1024");
+    if (c->max_group[precision] != max_group || c->threads[precision] != threads) free_groups(c);
+    c->max_group[precision] = max_group;
+    c->threads[precision] = threads;
+    return TBPM_OK;
+}
+
+// Allocate the state groups for `prec`, splitting n_states into power-of-two
+// widths no wider than the cap (e.g. 3 -> 2 + 1).
+static int ensure_groups(tbpm_ctx *c, int prec)
+{
+    if (c->prec == prec && !c->groups.empty()) return TBPM_OK;
+    free_groups(c);
+    const size_t cs = prec == TBPM_FP64 ? 16 : 8;
+    int left = c->n_states, s0 = 0;
+    while (left > 0) {
+        int B = 1;
+        while (B * 2 <= left && B * 2 <= c->max_group[prec]) B *= 2;
+        Group g;
+        g.B = B;
+        g.s0 = s0;
+        c->groups.push_back(g);
+        left -= B;
+        s0 += B;
+    }
+    if ((int)c->groups.size() > kMaxGroups) {
+        free_groups(c);
+        return fail(c, TBPM_E_UNSUPPORTED, "too many state groups");
+    }
+    for (auto &g : c->groups) {
+        const size_t bytes = (size_t)c->H.n_rows * g.B * cs;
+        int rc = dalloc(c, (char **)&g.psi0, bytes);
+        for (int k = 0; k < 3 && !rc; ++k) rc = dalloc(c, (char **)&g.buf[k], bytes);
+        if (!rc && prec == TBPM_FP32) rc = dalloc(c, &g.scale, (size_t)c->n_samples * g.B);
+        if (rc) { free_groups(c); return rc; }
+        for (int k = 0; k < 3; ++k) cudaMemsetAsync(g.buf[k], 0, bytes, c->st);
+        cudaMemsetAsync(g.psi0, 0, bytes, c->st);
+    }
+    int maxB = 1;
+    for (auto &g : c->groups) maxB = std::max(maxB, g.B);
+    const int64_t need = c->H.n_rows / kChunkRows * maxB * 3;
+    if (need > c->partial_len) {
+        cudaFree(c->d_partial);
+        c->d_partial = nullptr;
+        int rc = dalloc(c, &c->d_partial, need);
+        if (rc) { free_groups(c); return rc; }
+        c->partial_len = need;
+    }
+    c->prec = prec;
+    return TBPM_OK;
+}
+
+namespace {
+
+struct Slot {
+    int buf;      // buffer index holding the stored part, or -1
+    double beta;  // plus beta * psi
+};
+
+struct Launch {
+    bool final_term;
+    int x, z, out;   // buffer indices; x == -1 means psi
+    double c, gamma;
+    bool interior;   // full term: gathered buffer x, z present
+};
+
+// Clenshaw schedule of one step for M coefficients a[0..M-1], given the
+// buffer `cur` that holds psi.  b_{M-1} = a_{M-1} psi is never stored.
+std::vector<Launch> schedule(const std::vector<double> &a, int cur, int *next_cur)
+{
+    const int M = (int)a.size();
+    std::vector<Slot> b(M + 2, Slot{-1, 0.0});
+    b[M - 1] = Slot{-1, a[M - 1]};
+    int scratch[2], ns = 0;
+    for (int k = 0; k < 3; ++k)
+        if (k != cur) scratch[ns++] = k;
+    std::vector<Launch> out;
+    for (int m = M - 2; m >= 0; --m) {
+        const Slot x = b[m + 1], zz = b[m + 2];
+        Launch L;
+        L.final_term = (m == 0);
+        const double g = L.final_term ? 1.0 : 2.0;
+        if (x.buf < 0) {
+            L.x = -1;
+            L.gamma = g * x.beta;
+        } else {
+            L.x = x.buf;
+            L.gamma = g;
+        }
+        L.c = a[m] + zz.beta;
+        L.z = zz.buf;
+        if (zz.buf >= 0)
+            L.out = zz.buf;
+        else
+            L.out = (scratch[0] != x.buf) ? scratch[0] : scratch[1];
+        L.interior = (x.buf >= 0 && zz.buf >= 0);
+        out.push_back(L);
+        b[m] = Slot{L.out, 0.0};
+    }
+    *next_cur = out.back().out;
+    return out;
+}
+
+void split_coeff(double c, int fp32, double *hi, double *lo)
+{
+    if (fp32) {
+        float h = (float)c;
+        *hi = (double)h;
+        *lo = (double)(float)(c - (double)h);
+    } else {
+        *hi = c;
+        *lo = 0.0;
+    }
+}
+
+}  // namespace
+
+static int get_events(tbpm_ctx *c, size_t n)
+{
+    while (c->events.size() < n) {
+        cudaEvent_t e;
+        CUDA_OR_FAIL(c, cudaEventCreate(&e));
+        c->events.push_back(e);
+    }
+    return TBPM_OK;
+}
+
+extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
+                              double *corr_out, int where_out, int flags)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->have_h || c->n_states < 1)
+        return fail(c, TBPM_E_STATE, "build the Hamiltonian and set states first");
+    if (precision != TBPM_FP64 && precision != TBPM_FP32)
+        return fail(c, TBPM_E_INVALID_ARG, "precision must be TBPM_FP64 or TBPM_FP32");
+    if (n_steps < 0) return fail(c, TBPM_E_INVALID_ARG, "n_steps < 0");
+    if (corr_out && where_out != TBPM_HOST && where_out != TBPM_DEVICE)
+        return fail(c, TBPM_E_INVALID_ARG, "bad where_out");
+    const int fp32 = precision == TBPM_FP32;
+    if ((fp32 && !c->H.val32) || (!fp32 && !c->H.val64))
+        return fail(c, TBPM_E_STATE, "the Hamiltonian was built without this precision");
+    const bool resume = (flags & TBPM_PROP_RESUME) != 0;
+    if (resume && (!c->have_run || c->prec != precision))
+        return fail(c, TBPM_E_STATE, "nothing to resume in this precision");
+    const bool profile = (flags & TBPM_PROP_PROFILE) != 0;
+    const bool graph = (flags & TBPM_PROP_GRAPH) != 0 && !profile;
+    if (flags & TBPM_PROP_PERSISTENT)
+        return fail(c, TBPM_E_UNSUPPORTED, "persistent mode is not built");
+
+    std::vector<double> J(kMaxTerms);
+    int M = 0;
+    if (bessel_miller(z, 1e-15, kMaxTerms, J.data(), &M) != TBPM_OK || M < 2)
+        return fail(c, TBPM_E_INVALID_ARG, "z out of range for the coefficient table");
+    std::vector<double> a(M);
+    a[0] = J[0];
+    for (int m = 1; m < M; ++m) a[m] = 2.0 * J[m];
+
+    int rc = enter(c);
+    if (rc) return rc;
+    rc = ensure_groups(c, precision);
+    if (rc) return rc;
+    if (c->corr_steps != n_steps) {
+        free_outputs(c);
+        const size_t cnt = (size_t)c->n_samples * c->n_states * (n_steps + 1);
+        rc = dalloc(c, &c->d_corr, cnt);
+        if (!rc) rc = dalloc(c, &c->d_norms, cnt);
+        if (rc) return rc;
+        c->corr_steps = n_steps;
+    }
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->st));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_renorm, 0, sizeof(unsigned long long), c->st));
+
+    const size_t cs = fp32 ? 8 : 16;
+    const int threads = c->threads[precision];
+    SellView Hv;
+    Hv.slice_ptr = c->H.slice_ptr;
+    Hv.col = c->H.col;
+    Hv.val = fp32 ? (const void *)c->H.val32 : (const void *)c->H.val64;
+    Hv.diag = fp32 ? (const void *)c->H.diag32 : (const void *)c->H.diag64;
+
+    const size_t ev_per_step = 5;
+    if (profile) {
+        rc = get_events(c, (size_t)(n_steps + 1) * ev_per_step * c->groups.size() + 2);
+        if (rc) return rc;
+    }
+    int64_t launches = 0;
+    size_t ev_used = 0;
+    cudaEvent_t ev_all0 = nullptr, ev_all1 = nullptr;
+    if (profile) {
+        ev_all0 = c->events[ev_used++];
+        ev_all1 = c->events[ev_used++];
+        CUDA_OR_FAIL(c, cudaEventRecord(ev_all0, c->st));
+    }
+    std::vector<size_t> step_ev;   // index of the first of 5 events per profiled step
+
+    for (auto &g : c->groups) {
+        const size_t bytes = (size_t)c->H.n_rows * g.B * cs;
+        if (!resume) {
+            CUDA_OR_FAIL(c, launch_set_states(c->d_psi_user, c->n_orb, c->n_states,
+                                              c->H.user_to_row, g.s0, g.B, fp32, g.psi0, c->st));
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(g.buf[0], g.psi0, bytes, cudaMemcpyDeviceToDevice, c->st));
+            g.cur = 0;
+            launches += 1;
+        }
+        for (int k = 0; k < 3; ++k)
+            if (g.graph[k]) { cudaGraphExecDestroy(g.graph[k]); g.graph[k] = nullptr; }
+        if (g.scale) {
+            std::vector<double> ones((size_t)c->n_samples * g.B, 1.0);
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(g.scale, ones.data(), ones.size() * sizeof(double),
+                                            cudaMemcpyHostToDevice, c->st));
+        }
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_step, 0, c->n_samples * sizeof(int), c->st));
+
+        TermArgs base;
+        memset(&base, 0, sizeof(base));
+        base.H = Hv;
+        base.chunk_sample = c->H.chunk_sample;
+        base.n_rows = c->H.n_rows;
+        base.psi0 = g.psi0;
+        base.partial = c->d_partial;
+        ReduceArgs ra;
+        ra.partial = c->d_partial;
+        ra.sample_chunk_off = c->d_sample_chunk_off;
+        ra.n_samples = c->n_samples;
+        ra.B = g.B;
+        ra.group_state0 = g.s0;
+        ra.n_states = c->n_states;
+        ra.n_steps = n_steps;
+        ra.step = c->d_step;
+        ra.corr = c->d_corr;
+        ra.norms = c->d_norms;
+        ra.renorm_bound = 1e-5;
+        ra.hard_bound = fp32 ? 1e-2 : 1e-6;
+        ra.renorm_count = c->d_renorm;
+        ra.error_flags = c->d_flags;
+
+        // C_0 = <psi0|phi(0)>
+        {
+            TermArgs t0 = base;
+            t0.H.col = nullptr;
+            t0.out = g.buf[g.cur];
+            CUDA_OR_FAIL(c, launch_final(t0, fp32, g.B, threads, c->st));
+            ra.scale = nullptr;
+            CUDA_OR_FAIL(c, launch_reduce(ra, c->st));
+            launches += 2;
+        }
+        ra.scale = g.scale;
+
+        auto run_step = [&](int cur, int *next_cur, bool timed) -> int {
+            std::vector<Launch> sch = schedule(a, cur, next_cur);
+            size_t e0 = 0;
+            if (timed) {
+                e0 = ev_used;
+                ev_used += ev_per_step;
+                step_ev.push_back(e0);
+                CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0], c->st));
+            }
+            bool started_interior = false, ended_interior = false;
+            for (size_t k = 0; k < sch.size(); ++k) {
+                const Launch &L = sch[k];
+                if (timed && L.interior && !started_interior) {
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 1], c->st));
+                    started_interior = true;
+                }
+                if (timed && started_interior && !ended_interior && !L.interior) {
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 2], c->st));
+                    ended_interior = true;
+                }
+                TermArgs t = base;
+                t.x = L.x < 0 ? g.buf[cur] : g.buf[L.x];
+                t.x_is_psi = L.x < 0;
+                t.psi = g.buf[cur];
+                t.z = L.z < 0 ? nullptr : g.buf[L.z];
+                t.out = g.buf[L.out];
+                split_coeff(L.c, fp32, &t.c_hi, &t.c_lo);
+                t.gamma = L.gamma;
+                t.scale = g.scale;
+                cudaError_t e = L.final_term ? launch_final(t, fp32, g.B, threads, c->st)
+                                             : launch_term(t, fp32, g.B, threads, c->st);
+                if (e != cudaSuccess)
+                    return fail(c, TBPM_E_CUDA, std::string("term kernel: ") + cudaGetErrorString(e));
+            }
+            if (timed) {
+                if (!started_interior) {
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 1], c->st));
+                }
+                if (!ended_interior) {
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 2], c->st));
+                }
+                CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 3], c->st));
+            }
+            CUDA_OR_FAIL(c, launch_reduce(ra, c->st));
+            if (timed) CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 4], c->st));
+            return TBPM_OK;
+        };
+
+        for (int n = 0; n < n_steps; ++n) {
+            int nxt = 0;
+            if (graph) {
+                if (!g.graph[g.cur]) {
+                    cudaGraph_t gr;
+                    CUDA_OR_FAIL(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+                    int rc2 = run_step(g.cur, &nxt, false);
+                    cudaError_t e = cudaStreamEndCapture(c->st, &gr);
+                    if (rc2) return rc2;
+                    if (e != cudaSuccess)
+                        return fail(c, TBPM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+                    e = cudaGraphInstantiate(&g.graph[g.cur], gr, 0);
+                    cudaGraphDestroy(gr);
+                    if (e != cudaSuccess)
+                        return fail(c, TBPM_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+                } else {
+                    schedule(a, g.cur, &nxt);
+                }
+                CUDA_OR_FAIL(c, cudaGraphLaunch(g.graph[g.cur], c->st));
+            } else {
+                rc = run_step(g.cur, &nxt, profile);
+                if (rc) return rc;
+            }
+            g.cur = nxt;
+            launches += M;   // M-1 term kernels + one reduction
+        }
+    }
+    if (profile) CUDA_OR_FAIL(c, cudaEventRecord(ev_all1, c->st));
+
+    // results and checks
+    int h_flags[4];
+    unsigned long long h_renorm = 0;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(h_flags, c->d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(&h_renorm, c->d_renorm, sizeof(h_renorm), cudaMemcpyDeviceToHost, c->st));
+    const size_t cnt = (size_t)c->n_samples * c->n_states * (n_steps + 1);
+    std::vector<double> norms(cnt);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(norms.data(), c->d_norms, cnt * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->st));
+    if (corr_out)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(corr_out, c->d_corr, cnt * sizeof(double2),
+                                        where_out == TBPM_HOST ? cudaMemcpyDeviceToHost
+                                                               : cudaMemcpyDeviceToDevice,
+                                        c->st));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));
+    c->have_run = true;
+
+    tbpm_stats &S = c->stats;
+    S.n_terms = M;
+    S.n_steps = n_steps;
+    S.n_groups = (int)c->groups.size();
+    for (int k = 0; k < 8; ++k) S.group_width[k] = k < S.n_groups ? c->groups[k].B : 0;
+    S.renormalisations = (int64_t)h_renorm;
+    S.kernel_launches = launches;
+    double md = 0.0;
+    for (double v : norms) md = std::max(md, fabs(v - 1.0));
+    S.max_norm_drift = md;
+    S.ms_total = S.ms_term_avg = S.ms_final_avg = S.ms_reduce_avg = 0.0;
+    S.term_launches = 0;
+    {
+        // algorithmic bytes of one interior term launch over all groups' mean width
+        double vb = 0.0;
+        for (auto &g : c->groups) vb += (double)c->n_orb * 4.0 * g.B * cs;
+        vb /= c->groups.size();
+        const double valb = fp32 ? 4.0 : 8.0;
+        S.bytes_term = vb + (double)c->H.nnz_true * (4.0 + valb) + (double)c->n_orb * valb;
+    }
+    if (profile) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev_all0, ev_all1);
+        S.ms_total = ms;
+        double t_int = 0, t_fin = 0, t_red = 0;
+        const int n_int = std::max(0, M - 4);
+        for (size_t e0 : step_ev) {
+            float a1 = 0, a2 = 0, a3 = 0;
+            cudaEventElapsedTime(&a1, c->events[e0 + 1], c->events[e0 + 2]);
+            cudaEventElapsedTime(&a2, c->events[e0 + 2], c->events[e0 + 3]);
+            cudaEventElapsedTime(&a3, c->events[e0 + 3], c->events[e0 + 4]);
+            t_int += a1;
+            t_fin += a2;
+            t_red += a3;
+        }
+        S.term_launches = (int64_t)step_ev.size() * n_int;
+        if (S.term_launches) S.ms_term_avg = t_int / S.term_launches;
+        if (!step_ev.empty()) {
+            S.ms_final_avg = t_fin / step_ev.size();
+            S.ms_reduce_avg = t_red / step_ev.size();
+        }
+    }
+    rc = leave(c);
+    if (rc) return rc;
+    if (h_flags[0] & 2) return fail(c, TBPM_E_NONFINITE, "non-finite value in a state or correlation");
+    if (h_flags[0] & 1) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "norm drift %.3g above the hard bound: s = %.6g eV is likely below the "
+                 "spectral radius of H (Gershgorin %.6g eV)", md, c->s, c->H.gershgorin * c->s);
+        return fail(c, TBPM_E_NORM_DRIFT, buf);
+    }
+    c->err.clear();
+    return TBPM_OK;
+}
+
+extern "C" int tbpm_correlation(tbpm_ctx *c, double *out, int where_out)
+{
+    if (!c || !out) return fail(c, TBPM_E_INVALID_ARG, "NULL argument");
+    if (!c->have_run) return fail(c, TBPM_E_STATE, "no propagation yet");
+    const int n1 = c->corr_steps + 1;
+    const size_t cnt = (size_t)c->n_samples * c->n_states * n1;
+    std::vector<double2> all(cnt);
+    CUDA_OR_FAIL(c, cudaMemcpy(all.data(), c->d_corr, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+    std::vector<double> avg((size_t)c->n_samples * n1 * 2, 0.0);
+    for (int s = 0; s < c->n_samples; ++s)
+        for (int n = 0; n < n1; ++n) {
+            double re = 0, im = 0;
+            for (int p = 0; p < c->n_states; ++p) {
+                const double2 v = all[((size_t)s * c->n_states + p) * n1 + n];
+                re += v.x;
+                im += v.y;
+            }
+            avg[((size_t)s * n1 + n) * 2] = re / c->n_states;
+            avg[((size_t)s * n1 + n) * 2 + 1] = im / c->n_states;
+        }
+    if (where_out == TBPM_DEVICE)
+        CUDA_OR_FAIL(c, cudaMemcpy(out, avg.data(), avg.size() * sizeof(double), cudaMemcpyHostToDevice));
+    else
+        memcpy(out, avg.data(), avg.size() * sizeof(double));
+    return TBPM_OK;
+}
+
+extern "C" int tbpm_get_states(tbpm_ctx *c, double *phi_out, int where_out)
+{
+    if (!c || !phi_out) return fail(c, TBPM_E_INVALID_ARG, "NULL argument");
+    if (!c->have_run) return fail(c, TBPM_E_STATE, "no propagation yet");
+    int rc = enter(c);
+    if (rc) return rc;
+    const size_t count = (size_t)c->n_states * c->n_orb;
+    double2 *d = nullptr;
+    if (where_out == TBPM_DEVICE) {
+        d = (double2 *)phi_out;
+    } else {
+        rc = dalloc(c, &d, count);
+        if (rc) return rc;
+    }
+    for (auto &g : c->groups)
+        CUDA_OR_FAIL(c, launch_get_states(g.buf[g.cur], c->n_orb, c->n_states, c->H.user_to_row,
+                                          g.s0, g.B, c->prec == TBPM_FP32, d, c->st));
+    if (where_out != TBPM_DEVICE) {
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(phi_out, d, count * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));
+        cudaFree(d);
+    }
+    return leave(c);
+}
+
+extern "C" int tbpm_get_norms(tbpm_ctx *c, double *out)
+{
+    if (!c || !out) return fail(c, TBPM_E_INVALID_ARG, "NULL argument");
+    if (!c->have_run) return fail(c, TBPM_E_STATE, "no propagation yet");
+    const size_t cnt = (size_t)c->n_samples * c->n_states * (c->corr_steps + 1);
+    CUDA_OR_FAIL(c, cudaMemcpy(out, c->d_norms, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    return TBPM_OK;
+}
+
+extern "C" int tbpm_get_stats(tbpm_ctx *c, tbpm_stats *out)
+{
+    if (!c || !out) return fail(c, TBPM_E_INVALID_ARG, "NULL argument");
+    *out = c->stats;
+    return TBPM_OK;
+}

@@ -1,0 +1,368 @@
+// a1: bond list -> sliced-ELLPACK H~ = H / s on the GPU.
+//
+// The Hamiltonian of Sec. 2.1 (Eq. ham_mat_finite, hopping convention of
+// Sec. 4.1) has H_ij = t and H_ji = conj(t) = t (real hoppings) for a bond
+// (i, j, t) and H_ii = eps_i.  The off-diagonal part is stored as sliced
+// ELLPACK with 32-row slices: slice q holds width_q entries per row, entry k
+// of local row r at slice_ptr[q] + 32 k + r.  Rows shorter than the slice
+// width are padded with (col = own row, value 0), so every load stays in
+// bounds and needs no predicate beyond the slice width.  The diagonal is a
+// separate dense array.  Each sample occupies a block of rows padded to a
+// multiple of kChunkRows; padding rows are empty.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tbpm_internal.cuh"
+
+namespace tbpm {
+namespace {
+
+#define CK(call)                                                              \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            msg = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+            return e_ == cudaErrorMemoryAllocation ? TBPM_E_OOM : TBPM_E_CUDA; \
+        }                                                                     \
+    } while (0)
+
+__device__ __forceinline__ int find_sample(const int64_t *off, int n_samples, int64_t u)
+{
+    int lo = 0, hi = n_samples - 1;
+    while (lo < hi) {                       // last k with off[k] <= u
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_map_orbitals(int64_t n_orb, int n_samples, const int64_t *sample_off,
+                               const int64_t *row_off, const int32_t *perm,
+                               int32_t *user_to_row, int32_t *orb_sample)
+{
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n_orb) return;
+    int s = find_sample(sample_off, n_samples, u);
+    int64_t local = perm ? (int64_t)perm[u] : u - sample_off[s];
+    user_to_row[u] = (int32_t)(row_off[s] + local);
+    orb_sample[u] = s;
+}
+
+// error bits: 1 index out of range, 2 self bond, 4 bond across samples,
+// 8 non-finite value
+__global__ void k_count(int64_t n_hop, int64_t n_orb, const int64_t *hi, const int64_t *hj,
+                        const double *hv, const int32_t *user_to_row,
+                        const int32_t *orb_sample, int32_t *deg, int *err)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n_hop) return;
+    int64_t i = hi[b], j = hj[b];
+    if (i < 0 || j < 0 || i >= n_orb || j >= n_orb) { atomicOr(err, 1); return; }
+    if (i == j) { atomicOr(err, 2); return; }
+    if (orb_sample[i] != orb_sample[j]) { atomicOr(err, 4); return; }
+    double v = hv[b];
+    if (!(v == v) || v - v != 0.0) { atomicOr(err, 8); return; }
+    atomicAdd(&deg[user_to_row[i]], 1);
+    atomicAdd(&deg[user_to_row[j]], 1);
+}
+
+__global__ void k_slice_width(int64_t n_slices, const int32_t *deg, int64_t *entries,
+                              int *max_width)
+{
+    int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (q >= n_slices) return;
+    int d = deg[q * kSliceRows + lane];
+    for (int o = 16; o > 0; o >>= 1) d = max(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if (lane == 0) {
+        entries[q] = (int64_t)d * kSliceRows;
+        atomicMax(max_width, d);
+    }
+}
+
+// ---- exclusive scan of int64 (three phases, recursive over block sums) ----
+constexpr int kScanBlock = 1024;
+
+__global__ void k_scan_block(const int64_t *in, int64_t *out, int64_t n, int64_t *block_sums)
+{
+    __shared__ int64_t warp_tot[32];
+    int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    int64_t v = i < n ? in[i] : 0;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int64_t before = (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+    if (i < n) out[i] = before;
+    if (threadIdx.x == kScanBlock - 1) block_sums[blockIdx.x] = before + v;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *block_off)
+{
+    int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    if (i < n) out[i] += block_off[blockIdx.x];
+}
+
+// out[0 .. n] = exclusive scan of in[0 .. n-1]; out[n] = total.
+int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st,
+                   std::string &msg)
+{
+    int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    int64_t *sums = nullptr, *sums_scan = nullptr;
+    CK(cudaMalloc(&sums, (nb + 1) * sizeof(int64_t)));
+    CK(cudaMalloc(&sums_scan, (nb + 1) * sizeof(int64_t)));
+    k_scan_block<<<(unsigned)nb, kScanBlock, 0, st>>>(in, out, n, sums);
+    CK(cudaGetLastError());
+    int rc = TBPM_OK;
+    if (nb > 1) {
+        rc = scan_exclusive(sums, sums_scan, nb, st, msg);
+        if (rc == TBPM_OK) {
+            k_scan_add<<<(unsigned)nb, kScanBlock, 0, st>>>(out, n, sums_scan);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(out + n, sums_scan + nb, sizeof(int64_t),
+                               cudaMemcpyDeviceToDevice, st));
+        }
+    } else {
+        CK(cudaMemcpyAsync(out + n, sums, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    cudaFree(sums);
+    cudaFree(sums_scan);
+    return rc;
+}
+
+__global__ void k_pad_fill(int64_t n_rows, const int64_t *slice_ptr, int32_t *col,
+                           double *val)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    int64_t q = r / kSliceRows;
+    int lr = (int)(r % kSliceRows);
+    int64_t base = slice_ptr[q];
+    int w = (int)((slice_ptr[q + 1] - base) / kSliceRows);
+    for (int k = 0; k < w; ++k) {
+        col[base + (int64_t)k * kSliceRows + lr] = (int32_t)r;
+        val[base + (int64_t)k * kSliceRows + lr] = 0.0;
+    }
+}
+
+__global__ void k_fill(int64_t n_hop, const int64_t *hi, const int64_t *hj, const double *hv,
+                       double inv_s, const int32_t *user_to_row, const int64_t *slice_ptr,
+                       int32_t *fill, int32_t *col, double *val)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n_hop) return;
+    int32_t ri = user_to_row[hi[b]], rj = user_to_row[hj[b]];
+    double v = hv[b] * inv_s;
+    int pi = atomicAdd(&fill[ri], 1);
+    int64_t ei = slice_ptr[ri / kSliceRows] + (int64_t)pi * kSliceRows + ri % kSliceRows;
+    col[ei] = rj;
+    val[ei] = v;
+    int pj = atomicAdd(&fill[rj], 1);
+    int64_t ej = slice_ptr[rj / kSliceRows] + (int64_t)pj * kSliceRows + rj % kSliceRows;
+    col[ej] = ri;
+    val[ej] = v;                 // conj(t) = t for real hoppings
+}
+
+__global__ void k_diag(int64_t n_orb, const double *onsite, double inv_s,
+                       const int32_t *user_to_row, double *diag)
+{
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n_orb) return;
+    diag[user_to_row[u]] = onsite ? onsite[u] * inv_s : 0.0;
+}
+
+// Per row: insertion sort of the filled entries by (col, value) so the
+// product's summation order is independent of the fill order; then the
+// Gershgorin row bound |d_r| + sum |H~_rc|, max-reduced as the bit pattern of
+// a non-negative double (which orders like an unsigned integer).
+__global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int32_t *deg,
+                            const double *diag, int32_t *col, double *val,
+                            unsigned long long *gersh_bits)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    int64_t base = slice_ptr[r / kSliceRows] + r % kSliceRows;
+    int d = deg[r];
+    for (int a = 1; a < d; ++a) {
+        int32_t c = col[base + (int64_t)a * kSliceRows];
+        double v = val[base + (int64_t)a * kSliceRows];
+        int b = a - 1;
+        while (b >= 0) {
+            int32_t cb = col[base + (int64_t)b * kSliceRows];
+            double vb = val[base + (int64_t)b * kSliceRows];
+            if (cb < c || (cb == c && vb <= v)) break;
+            col[base + (int64_t)(b + 1) * kSliceRows] = cb;
+            val[base + (int64_t)(b + 1) * kSliceRows] = vb;
+            --b;
+        }
+        col[base + (int64_t)(b + 1) * kSliceRows] = c;
+        val[base + (int64_t)(b + 1) * kSliceRows] = v;
+    }
+    double g = fabs(diag[r]);
+    for (int a = 0; a < d; ++a) g += fabs(val[base + (int64_t)a * kSliceRows]);
+    atomicMax(gersh_bits, (unsigned long long)__double_as_longlong(g));
+}
+
+__global__ void k_to_f32(int64_t n, const double *src, float *dst)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void free_build(BuildOutput &b)
+{
+    cudaFree(b.user_to_row);
+    cudaFree(b.orb_sample);
+    cudaFree(b.slice_ptr);
+    cudaFree(b.col);
+    cudaFree(b.val64);
+    cudaFree(b.val32);
+    cudaFree(b.diag64);
+    cudaFree(b.diag32);
+    cudaFree(b.chunk_sample);
+    b = BuildOutput();
+}
+
+int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
+               cudaStream_t st, std::string &msg)
+{
+    const int T = 256;
+    std::vector<int64_t> row_off(in.n_samples + 1);
+    CK(cudaMemcpyAsync(row_off.data(), in.d_sample_row_off,
+                       (in.n_samples + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int64_t n_rows = row_off[in.n_samples];
+    const int64_t n_slices = n_rows / kSliceRows;
+    out.n_rows = n_rows;
+    out.n_slices = n_slices;
+
+    CK(cudaMalloc(&out.user_to_row, in.n_orb * sizeof(int32_t)));
+    CK(cudaMalloc(&out.orb_sample, in.n_orb * sizeof(int32_t)));
+    k_map_orbitals<<<blocks_for(in.n_orb, T), T, 0, st>>>(
+        in.n_orb, in.n_samples, in.d_sample_off, in.d_sample_row_off, in.d_perm,
+        out.user_to_row, out.orb_sample);
+    CK(cudaGetLastError());
+
+    int32_t *deg = nullptr, *fill = nullptr;
+    int64_t *entries = nullptr;
+    int *err = nullptr;           // [0] error bits, [1] max width
+    unsigned long long *gbits = nullptr;
+    CK(cudaMalloc(&deg, n_rows * sizeof(int32_t)));
+    CK(cudaMalloc(&fill, n_rows * sizeof(int32_t)));
+    CK(cudaMalloc(&entries, (n_slices + 1) * sizeof(int64_t)));
+    CK(cudaMalloc(&err, 2 * sizeof(int)));
+    CK(cudaMalloc(&gbits, sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(deg, 0, n_rows * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(fill, 0, n_rows * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(err, 0, 2 * sizeof(int), st));
+    CK(cudaMemsetAsync(gbits, 0, sizeof(unsigned long long), st));
+
+    if (in.n_hop > 0) {
+        k_count<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.n_orb, in.hop_i, in.hop_j,
+                                                       in.hop_v, out.user_to_row,
+                                                       out.orb_sample, deg, err);
+        CK(cudaGetLastError());
+    }
+    int h_err[2] = {0, 0};
+    CK(cudaMemcpyAsync(h_err, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    auto cleanup = [&]() {
+        cudaFree(deg); cudaFree(fill); cudaFree(entries); cudaFree(err); cudaFree(gbits);
+    };
+    if (h_err[0]) {
+        msg = "invalid bond list:";
+        if (h_err[0] & 1) msg += " index out of range;";
+        if (h_err[0] & 2) msg += " bond from an orbital to itself;";
+        if (h_err[0] & 4) msg += " bond joins two samples;";
+        if (h_err[0] & 8) msg += " non-finite hopping;";
+        cleanup();
+        return TBPM_E_INVALID_ARG;
+    }
+    k_slice_width<<<blocks_for(n_slices * 32, T), T, 0, st>>>(n_slices, deg, entries, err + 1);
+    CK(cudaGetLastError());
+    CK(cudaMalloc(&out.slice_ptr, (n_slices + 1) * sizeof(int64_t)));
+    int rc = scan_exclusive(entries, out.slice_ptr, n_slices, st, msg);
+    if (rc) { cleanup(); return rc; }
+    CK(cudaMemcpyAsync(&out.nnz_pad, out.slice_ptr + n_slices, sizeof(int64_t),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&out.max_width, err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out.nnz_true = 2 * in.n_hop;
+    if (out.nnz_pad > (int64_t)1 << 40) { msg = "matrix too large"; cleanup(); return TBPM_E_OOM; }
+
+    int64_t nnz_alloc = out.nnz_pad > 0 ? out.nnz_pad : 1;
+    CK(cudaMalloc(&out.col, nnz_alloc * sizeof(int32_t)));
+    CK(cudaMalloc(&out.val64, nnz_alloc * sizeof(double)));
+    CK(cudaMalloc(&out.diag64, n_rows * sizeof(double)));
+    CK(cudaMemsetAsync(out.diag64, 0, n_rows * sizeof(double), st));
+    k_pad_fill<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, out.val64);
+    CK(cudaGetLastError());
+    if (in.n_hop > 0) {
+        k_fill<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j, in.hop_v,
+                                                      in.inv_s, out.user_to_row,
+                                                      out.slice_ptr, fill, out.col, out.val64);
+        CK(cudaGetLastError());
+    }
+    k_diag<<<blocks_for(in.n_orb, T), T, 0, st>>>(in.n_orb, in.onsite, in.inv_s,
+                                                  out.user_to_row, out.diag64);
+    CK(cudaGetLastError());
+    k_sort_rows<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, deg, out.diag64,
+                                                     out.col, out.val64, gbits);
+    CK(cudaGetLastError());
+    unsigned long long hg = 0;
+    CK(cudaMemcpyAsync(&hg, gbits, sizeof(hg), cudaMemcpyDeviceToHost, st));
+
+    // chunk -> sample table
+    int64_t n_chunks = n_rows / kChunkRows;
+    std::vector<int32_t> cs(n_chunks > 0 ? n_chunks : 1);
+    for (int s = 0; s < in.n_samples; ++s)
+        for (int64_t c = row_off[s] / kChunkRows; c < row_off[s + 1] / kChunkRows; ++c)
+            cs[c] = s;
+    CK(cudaMalloc(&out.chunk_sample, cs.size() * sizeof(int32_t)));
+    CK(cudaMemcpyAsync(out.chunk_sample, cs.data(), cs.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, st));
+
+    if (keep32) {
+        CK(cudaMalloc(&out.val32, nnz_alloc * sizeof(float)));
+        CK(cudaMalloc(&out.diag32, n_rows * sizeof(float)));
+        if (out.nnz_pad > 0)
+            k_to_f32<<<blocks_for(out.nnz_pad, T), T, 0, st>>>(out.nnz_pad, out.val64, out.val32);
+        k_to_f32<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.diag64, out.diag32);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(st));
+    double g;
+    memcpy(&g, &hg, sizeof(g));
+    out.gershgorin = g;
+    if (!keep64) {
+        cudaFree(out.val64);
+        cudaFree(out.diag64);
+        out.val64 = nullptr;
+        out.diag64 = nullptr;
+    }
+    cleanup();
+    return TBPM_OK;
+}
+
+}  // namespace tbpm

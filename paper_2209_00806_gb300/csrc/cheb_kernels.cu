@@ -1,0 +1,437 @@
+// a3-a5: the fused Chebyshev term kernels and the correlation reduction.
+//
+// One time step evaluates psi(t + tau) = sum_{m<M} a_m T^_m(H~) psi(t)
+// (Sec. 2.2, Eq. psi_t: a_0 = J_0(z), a_m = 2 J_m(z), modified polynomials
+// T^_{m+1} = -2i H~ T^_m + T^_{m-1}).  The paper sums forward; this library
+// evaluates the same sum by Clenshaw's backward recurrence,
+//   b_m = a_m psi + (-2i H~) b_{m+1} + b_{m+2},   b_M = b_{M+1} = 0,
+//   psi(t + tau) = a_0 psi + (-i H~) b_1 + b_2,
+// which needs one sparse product per term like the forward sum but moves
+// four vectors per term instead of five (no accumulator read-modify-write).
+// Every term is one kernel:
+//   out = c psi + gamma (-i) (H~ x) + z
+// with x gathered through the sparse rows, psi, z and out at the thread's
+// own row.  The closing term (gamma = 1) also reduces <psi0|out> and
+// <out|out> in FP64 per state.
+//
+// Vectors hold B states per orbital, interleaved: element (row r, state b)
+// is complex number r * B + b.  A row is served by L lanes; each lane moves
+// 16 bytes (one complex128, or two complex64) so a warp reads 512
+// contiguous bytes of the own-row vectors, and every gathered row is one or
+// more full 32-byte sectors.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tbpm_internal.cuh"
+
+namespace tbpm {
+namespace {
+
+template <typename V, int SPL> struct LaneT;
+template <> struct LaneT<double, 1> { typedef double2 type; };
+template <> struct LaneT<float, 1> { typedef float2 type; };
+template <> struct LaneT<float, 2> { typedef float4 type; };
+
+template <typename V, int SPL> struct Cv {
+    V re[SPL], im[SPL];
+};
+
+__device__ __forceinline__ void unpack(const double2 &v, Cv<double, 1> &o) { o.re[0] = v.x; o.im[0] = v.y; }
+__device__ __forceinline__ void unpack(const float2 &v, Cv<float, 1> &o) { o.re[0] = v.x; o.im[0] = v.y; }
+__device__ __forceinline__ void unpack(const float4 &v, Cv<float, 2> &o)
+{
+    o.re[0] = v.x; o.im[0] = v.y; o.re[1] = v.z; o.im[1] = v.w;
+}
+__device__ __forceinline__ double2 pack(const Cv<double, 1> &o) { return make_double2(o.re[0], o.im[0]); }
+__device__ __forceinline__ float2 pack(const Cv<float, 1> &o) { return make_float2(o.re[0], o.im[0]); }
+__device__ __forceinline__ float4 pack(const Cv<float, 2> &o)
+{
+    return make_float4(o.re[0], o.im[0], o.re[1], o.im[1]);
+}
+
+// Load the lane data of row `r` through the read-only path.
+template <typename V, int L, int SPL>
+__device__ __forceinline__ Cv<V, SPL> ld_ro(const void *base, int64_t r, int l)
+{
+    typedef typename LaneT<V, SPL>::type Lane;
+    Cv<V, SPL> o;
+    unpack(__ldg(reinterpret_cast<const Lane *>(base) + r * L + l), o);
+    return o;
+}
+template <typename V, int L, int SPL>
+__device__ __forceinline__ Cv<V, SPL> ld(const void *base, int64_t r, int l)
+{
+    typedef typename LaneT<V, SPL>::type Lane;
+    Cv<V, SPL> o;
+    unpack(reinterpret_cast<const Lane *>(base)[r * L + l], o);
+    return o;
+}
+template <typename V, int L, int SPL>
+__device__ __forceinline__ void st(void *base, int64_t r, int l, const Cv<V, SPL> &v)
+{
+    typedef typename LaneT<V, SPL>::type Lane;
+    reinterpret_cast<Lane *>(base)[r * L + l] = pack(v);
+}
+
+// out = c psi + gamma (-i) (H~ x) + z for lane l of row r.
+template <typename V, int L, int SPL>
+__device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int l,
+                                               const double *sc)
+{
+    const int64_t q = r / kSliceRows;
+    const int lr = (int)(r % kSliceRows);
+    const int64_t base = __ldg(a.H.slice_ptr + q);
+    const int w = (int)((__ldg(a.H.slice_ptr + q + 1) - base) / kSliceRows);
+    const int32_t *colp = a.H.col + base + lr;
+    const V *valp = reinterpret_cast<const V *>(a.H.val) + base + lr;
+
+    // y = H~ x: diagonal first, then the row's entries in stored order,
+    // four at a time so that the gathers are in flight together.
+    const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+    Cv<V, SPL> y = ld_ro<V, L, SPL>(a.x, r, l);
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
+    for (int k = 0; k < w; k += 4) {
+        int32_t c[4];
+        V h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = k + u < w;
+            c[u] = ok ? __ldg(colp + (int64_t)(k + u) * kSliceRows) : (int32_t)r;
+            h[u] = ok ? __ldg(valp + (int64_t)(k + u) * kSliceRows) : (V)0;
+        }
+        Cv<V, SPL> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_ro<V, L, SPL>(a.x, c[u], l);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
+                y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+            }
+        }
+    }
+    Cv<V, SPL> p = ld_ro<V, L, SPL>(a.psi, r, l);
+    if (sc) {               // FP32 norm carry: psi -> psi * scale (per state)
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const V s = (V)sc[l * SPL + j];
+            p.re[j] *= s;
+            p.im[j] *= s;
+            if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
+        }
+    }
+    Cv<V, SPL> zz;
+    if (a.z) {
+        zz = ld<V, L, SPL>(a.z, r, l);
+    } else {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
+    }
+    const V g = (V)a.gamma, ch = (V)a.c_hi, cl = (V)a.c_lo;
+    Cv<V, SPL> o;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+        // (-i)(y_re + i y_im) = y_im - i y_re
+        V re = fma(g, y.im[j], zz.re[j]);
+        V im = fma(-g, y.re[j], zz.im[j]);
+        if (sizeof(V) == 4) {           // coefficient carried as hi + lo in FP32
+            re = fma(cl, p.re[j], re);
+            im = fma(cl, p.im[j], im);
+        }
+        o.re[j] = fma(ch, p.re[j], re);
+        o.im[j] = fma(ch, p.im[j], im);
+    }
+    return o;
+}
+
+template <typename V, int L, int SPL>
+__global__ void __launch_bounds__(1024) k_term(TermArgs a)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = t / L;
+    const int l = (int)(t % L);
+    if (r >= a.n_rows) return;
+    const double *sc = nullptr;
+    if (a.scale) sc = a.scale + (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
+    Cv<V, SPL> o = term_row<V, L, SPL>(a, r, l, sc);
+    st<V, L, SPL>(a.out, r, l, o);
+}
+
+// Closing term over one chunk of kChunkRows rows per block, with the FP64
+// partial sums of <psi0|out> and <out|out> per state.  Deterministic: fixed
+// thread-to-row mapping, shuffle tree, then a fixed-order sum over warps.
+template <typename V, int L, int SPL, bool COMPUTE>
+__global__ void __launch_bounds__(1024) k_final(TermArgs a)
+{
+    constexpr int B = L * SPL;
+    __shared__ double red[32][B][3];
+    const int64_t chunk = blockIdx.x;
+    const int rows_per_pass = blockDim.x / L;
+    const int l = threadIdx.x % L;
+    const double *sc = nullptr;
+    if (a.scale) sc = a.scale + (int64_t)a.chunk_sample[chunk] * B;
+    double dre[SPL], dim[SPL], nrm[SPL];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) { dre[j] = 0; dim[j] = 0; nrm[j] = 0; }
+    for (int64_t r = chunk * kChunkRows + threadIdx.x / L; r < (chunk + 1) * kChunkRows;
+         r += rows_per_pass) {
+        Cv<V, SPL> o;
+        if (COMPUTE) {
+            o = term_row<V, L, SPL>(a, r, l, sc);
+            st<V, L, SPL>(a.out, r, l, o);
+        } else {
+            o = ld<V, L, SPL>(a.out, r, l);
+        }
+        Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const double orr = o.re[j], oi = o.im[j], pr = p0.re[j], pi = p0.im[j];
+            dre[j] = fma(pr, orr, fma(pi, oi, dre[j]));
+            dim[j] = fma(pr, oi, fma(-pi, orr, dim[j]));
+            nrm[j] = fma(orr, orr, fma(oi, oi, nrm[j]));
+        }
+    }
+    // sum over the rows held by one warp (lanes with equal l)
+#pragma unroll
+    for (int off = L; off < 32; off <<= 1) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            dre[j] += __shfl_xor_sync(0xffffffffu, dre[j], off);
+            dim[j] += __shfl_xor_sync(0xffffffffu, dim[j], off);
+            nrm[j] += __shfl_xor_sync(0xffffffffu, nrm[j], off);
+        }
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane < L) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            red[warp][lane * SPL + j][0] = dre[j];
+            red[warp][lane * SPL + j][1] = dim[j];
+            red[warp][lane * SPL + j][2] = nrm[j];
+        }
+    }
+    __syncthreads();
+    const int nw = blockDim.x / 32;
+    if (threadIdx.x < B * 3) {
+        const int b = threadIdx.x / 3, q = threadIdx.x % 3;
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w][b][q];
+        a.partial[chunk * (B * 3) + threadIdx.x] = s;
+    }
+}
+
+// One block per sample: fixed-order sum of the chunk partials, then the
+// correlation entry, the squared norm, the drift checks and (FP32) the
+// scale of the next step's starting state.
+__global__ void __launch_bounds__(256) k_reduce(ReduceArgs a)
+{
+    __shared__ double part[256];
+    const int s = blockIdx.x;
+    const int B3 = a.B * 3;
+    const int G = blockDim.x / B3;
+    const int t = threadIdx.x;
+    const int64_t c0 = a.sample_chunk_off[s], c1 = a.sample_chunk_off[s + 1];
+    if (t < G * B3) {
+        const int g = t / B3, comp = t % B3;
+        double acc = 0.0;
+        for (int64_t c = c0 + g; c < c1; c += G) acc += a.partial[c * B3 + comp];
+        part[t] = acc;
+    }
+    __syncthreads();
+    const int step = a.step[s];
+    if (t < a.B) {
+        double v[3];
+        for (int q = 0; q < 3; ++q) {
+            double acc = 0.0;
+            for (int g = 0; g < G; ++g) acc += part[g * B3 + t * 3 + q];
+            v[q] = acc;
+        }
+        const int state = a.group_state0 + t;
+        const int64_t idx = ((int64_t)s * a.n_states + state) * (a.n_steps + 1) + step;
+        a.corr[idx] = make_double2(v[0], v[1]);
+        a.norms[idx] = v[2];
+        const double drift = fabs(v[2] - 1.0);
+        if (!(v[2] == v[2]) || !(v[0] == v[0]) || !(v[1] == v[1]) || v[2] - v[2] != 0.0) {
+            atomicOr(a.error_flags, 2);
+        } else if (drift > a.hard_bound) {
+            atomicOr(a.error_flags, 1);
+        }
+        if (a.scale) {
+            double sc = 1.0;
+            if (drift > a.renorm_bound && v[2] > 0.0 && v[2] - v[2] == 0.0) {
+                sc = 1.0 / sqrt(v[2]);
+                atomicAdd(a.renorm_count, 1ull);
+            }
+            a.scale[(int64_t)s * a.B + t] = sc;
+        }
+    }
+    __syncthreads();
+    if (t == 0) a.step[s] = step + 1;
+}
+
+template <typename V, int SPL> struct StoreC;
+template <> struct StoreC<double, 1> {
+    __device__ static void put(void *psi, int64_t idx, double re, double im)
+    {
+        reinterpret_cast<double2 *>(psi)[idx] = make_double2(re, im);
+    }
+    __device__ static double2 get(const void *psi, int64_t idx)
+    {
+        return reinterpret_cast<const double2 *>(psi)[idx];
+    }
+};
+template <> struct StoreC<float, 1> {
+    __device__ static void put(void *psi, int64_t idx, double re, double im)
+    {
+        reinterpret_cast<float2 *>(psi)[idx] = make_float2((float)re, (float)im);
+    }
+    __device__ static double2 get(const void *psi, int64_t idx)
+    {
+        float2 v = reinterpret_cast<const float2 *>(psi)[idx];
+        return make_double2(v.x, v.y);
+    }
+};
+
+// psi0_u = exp(i theta_u) / sqrt(N_k) in caller order (complex128).
+__global__ void k_phase_user(const double *theta, int64_t n_orb, int n_states,
+                             const double *inv_sqrt_n, const int32_t *orb_sample,
+                             double2 *psi_user)
+{
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n_orb) return;
+    const double a = inv_sqrt_n[orb_sample[u]];
+    for (int p = 0; p < n_states; ++p) {
+        double sn, cs;
+        sincos(theta[(int64_t)p * n_orb + u], &sn, &cs);
+        psi_user[(int64_t)p * n_orb + u] = make_double2(a * cs, a * sn);
+    }
+}
+
+template <typename V>
+__global__ void k_set_states(const double2 *src, int64_t n_orb, const int32_t *user_to_row,
+                             int g0, int B, void *psi)
+{
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n_orb) return;
+    const int64_t r = user_to_row[u];
+    for (int b = 0; b < B; ++b) {
+        double2 v = src[(int64_t)(g0 + b) * n_orb + u];
+        StoreC<V, 1>::put(psi, r * B + b, v.x, v.y);
+    }
+}
+
+template <typename V>
+__global__ void k_get_states(const void *psi, int64_t n_orb, const int32_t *user_to_row,
+                             int g0, int B, double2 *dst)
+{
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= n_orb) return;
+    const int64_t r = user_to_row[u];
+    for (int b = 0; b < B; ++b)
+        dst[(int64_t)(g0 + b) * n_orb + u] = StoreC<V, 1>::get(psi, r * B + b);
+}
+
+template <typename V, int L, int SPL>
+cudaError_t launch_term_t(const TermArgs &a, int threads, cudaStream_t st)
+{
+    const int64_t n_threads = a.n_rows * L;
+    const unsigned blocks = (unsigned)((n_threads + threads - 1) / threads);
+    k_term<V, L, SPL><<<blocks, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename V, int L, int SPL>
+cudaError_t launch_final_t(const TermArgs &a, int threads, bool compute, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)(a.n_rows / kChunkRows);
+    if (compute)
+        k_final<V, L, SPL, true><<<blocks, threads, 0, st>>>(a);
+    else
+        k_final<V, L, SPL, false><<<blocks, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool FINAL>
+cudaError_t dispatch(const TermArgs &a, int fp32, int B, int threads, bool compute,
+                     cudaStream_t st)
+{
+#define TBPM_CASE(V, L, SPL)                                              \
+    return FINAL ? launch_final_t<V, L, SPL>(a, threads, compute, st)    \
+                 : launch_term_t<V, L, SPL>(a, threads, st)
+    if (!fp32) {
+        switch (B) {
+        case 1: TBPM_CASE(double, 1, 1);
+        case 2: TBPM_CASE(double, 2, 1);
+        case 4: TBPM_CASE(double, 4, 1);
+        case 8: TBPM_CASE(double, 8, 1);
+        }
+    } else {
+        switch (B) {
+        case 1: TBPM_CASE(float, 1, 1);
+        case 2: TBPM_CASE(float, 1, 2);
+        case 4: TBPM_CASE(float, 2, 2);
+        case 8: TBPM_CASE(float, 4, 2);
+        case 16: TBPM_CASE(float, 8, 2);
+        }
+    }
+#undef TBPM_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
+{
+    return dispatch<false>(a, fp32, B, threads, true, st);
+}
+
+cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
+{
+    return dispatch<true>(a, fp32, B, threads, a.H.col != nullptr, st);
+}
+
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st)
+{
+    k_reduce<<<a.n_samples, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_user(const double *theta, int64_t n_orb, int n_states,
+                              const double *inv_sqrt_n, const int32_t *orb_sample,
+                              double2 *psi_user, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((n_orb + 255) / 256);
+    k_phase_user<<<blocks, 256, 0, st>>>(theta, n_orb, n_states, inv_sqrt_n, orb_sample,
+                                         psi_user);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_states(const double2 *psi_user, int64_t n_orb, int n_states,
+                              const int32_t *user_to_row, int g0, int B, int fp32, void *psi,
+                              cudaStream_t st)
+{
+    (void)n_states;
+    const unsigned blocks = (unsigned)((n_orb + 255) / 256);
+    if (fp32)
+        k_set_states<float><<<blocks, 256, 0, st>>>(psi_user, n_orb, user_to_row, g0, B, psi);
+    else
+        k_set_states<double><<<blocks, 256, 0, st>>>(psi_user, n_orb, user_to_row, g0, B, psi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_states(const void *psi, int64_t n_orb, int n_states,
+                              const int32_t *user_to_row, int g0, int B, int fp32,
+                              double2 *out_user, cudaStream_t st)
+{
+    (void)n_states;
+    const unsigned blocks = (unsigned)((n_orb + 255) / 256);
+    if (fp32)
+        k_get_states<float><<<blocks, 256, 0, st>>>(psi, n_orb, user_to_row, g0, B, out_user);
+    else
+        k_get_states<double><<<blocks, 256, 0, st>>>(psi, n_orb, user_to_row, g0, B, out_user);
+    return cudaGetLastError();
+}
+
+}  // namespace tbpm

@@ -1,0 +1,124 @@
+// Internal declarations of the TBPM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tbpm.h"
+
+namespace tbpm {
+
+// Rows of one sliced-ELLPACK slice.  Entry k of local row r of slice q sits
+// at slice_ptr[q] + k * kSliceRows + r, so the rows of a warp read
+// consecutive words for each k.
+constexpr int kSliceRows = 32;
+// Samples are padded to a multiple of this many rows; it is also the row
+// chunk that one partial of the correlation reduction covers.
+constexpr int kChunkRows = 1024;
+constexpr int kMaxStates = 64;
+constexpr int kMaxTerms = 128;
+constexpr int kMaxGroups = 8;
+
+// Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
+// diagonal, one copy per value precision.
+struct SellView {
+    const int64_t *slice_ptr;  // [n_slices + 1]
+    const int32_t *col;        // [nnz_pad]
+    const void *val;           // double or float [nnz_pad]
+    const void *diag;          // double or float [n_rows]
+};
+
+// One Clenshaw term: out = c * psi + gamma * (-i) * H~ x + z, optionally
+// with psi scaled per state (FP32 norm carry).
+struct TermArgs {
+    SellView H;
+    const void *x;        // gathered vector
+    const void *psi;      // current state (own row only)
+    const void *z;        // b_{m+2} (own row) or nullptr
+    void *out;            // may alias z
+    double c_hi, c_lo;    // coefficient of psi as an unevaluated sum (FP32)
+    double gamma;
+    int x_is_psi;         // apply the state scale to x as well
+    const double *scale;  // [n_samples * B] or nullptr
+    const int32_t *chunk_sample;  // [n_rows / kChunkRows]
+    int64_t n_rows;
+    // closing term only (H.col == nullptr: reduce `out` without computing it)
+    const void *psi0;
+    double *partial;      // [n_chunks][B][3]
+};
+
+struct ReduceArgs {
+    const double *partial;           // [n_chunks][B][3]
+    const int64_t *sample_chunk_off; // [n_samples + 1]
+    int n_samples;
+    int B;
+    int group_state0;                // first state of this group
+    int n_states;
+    int n_steps;
+    int *step;                       // device step counter (index of the new C)
+    double2 *corr;                   // [n_samples][n_states][n_steps + 1]
+    double *norms;                   // [n_samples][n_states][n_steps + 1]
+    double *scale;                   // [n_samples * B] next-step scale (FP32) or nullptr
+    double renorm_bound;             // |<phi|phi> - 1| above which to renormalise
+    double hard_bound;               // above which to flag NORM_DRIFT
+    unsigned long long *renorm_count;
+    int *error_flags;                // bit 0 drift, bit 1 non-finite
+};
+
+// Kernel launchers (cheb_kernels.cu).  `fp32` selects the value precision,
+// B the states per row (a group).  Return cudaError_t of the launch.
+cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
+cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
+cudaError_t launch_phase_user(const double *theta, int64_t n_orb, int n_states,
+                              const double *inv_sqrt_n, const int32_t *orb_sample,
+                              double2 *psi_user, cudaStream_t st);
+cudaError_t launch_set_states(const double2 *psi_user, int64_t n_orb, int n_states,
+                              const int32_t *user_to_row, int group_state0, int B,
+                              int fp32, void *psi, cudaStream_t st);
+cudaError_t launch_get_states(const void *psi, int64_t n_orb, int n_states,
+                              const int32_t *user_to_row, int group_state0, int B,
+                              int fp32, double2 *out_user, cudaStream_t st);
+
+// Builder (build_kernels.cu).
+struct BuildInput {
+    int64_t n_orb;
+    const double *onsite;   // device or nullptr
+    int64_t n_hop;
+    const int64_t *hop_i, *hop_j;
+    const double *hop_v;    // device
+    double inv_s;
+    int n_samples;
+    const int64_t *d_sample_off;      // device [n_samples + 1] (caller order)
+    const int64_t *d_sample_row_off;  // device [n_samples + 1] (padded rows)
+    const int32_t *d_perm;            // device [n_orb] caller -> position in sample, or nullptr
+};
+
+struct BuildOutput {
+    int64_t n_rows = 0, n_slices = 0, nnz_pad = 0, nnz_true = 0;
+    int32_t *user_to_row = nullptr;  // [n_orb]
+    int32_t *orb_sample = nullptr;   // [n_orb]
+    int64_t *slice_ptr = nullptr;    // [n_slices + 1]
+    int32_t *col = nullptr;
+    double *val64 = nullptr;
+    float *val32 = nullptr;
+    double *diag64 = nullptr;
+    float *diag32 = nullptr;
+    int32_t *chunk_sample = nullptr; // [n_rows / kChunkRows]
+    double gershgorin = 0.0;
+    int max_width = 0;
+};
+
+// Returns TBPM status; fills msg on failure.  Allocations in `out` are owned
+// by the caller afterwards (freed with free_build).
+int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
+               cudaStream_t st, std::string &msg);
+void free_build(BuildOutput &b);
+
+// Host math (host_math.cpp).
+int bessel_miller(double z, double tol, int max_terms, double *J, int *n_terms);
+
+}  // namespace tbpm

@@ -1,0 +1,111 @@
+"""Object wrapper over the C ABI: one context, one Hamiltonian, its states.
+
+Marshalling only -- every step runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native as N
+
+
+class Propagator:
+    """Owns a library context on ``device`` (ordered after ``stream``, a raw
+    cudaStream_t address such as ``torch.cuda.current_stream().cuda_stream``)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.ctx = N.tbpm_create(device, stream)
+        self.n_samples = 1
+        self.n_states = 0
+        self.n_orb = 0
+        self.s = None
+
+    def close(self):
+        if self.ctx is not None:
+            N.tbpm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # a1
+    def build(self, n_orb, onsite, hop_i, hop_j, hop_v, s, sample_offsets=None, flags=0):
+        """Arrays are numpy (host) or torch CUDA tensors (device), all alike."""
+        n_samples = 1 if sample_offsets is None else len(sample_offsets) - 1
+        N.tbpm_build_hamiltonian(self.ctx, int(n_orb), onsite, int(hop_i.shape[0]), hop_i,
+                                 hop_j, hop_v, float(s), n_samples, sample_offsets,
+                                 N.where_of(hop_i), flags)
+        self.n_samples = n_samples
+        self.n_orb = int(n_orb)
+        self.s = float(s)
+        return self
+
+    def build_sample(self, sample, s, sample_offsets=None, flags=0):
+        return self.build(sample.n_orb, _c64(sample.onsite), _ci64(sample.hop_i),
+                          _ci64(sample.hop_j), _c64(sample.hop_v), s, sample_offsets, flags)
+
+    def set_phase_states(self, theta):
+        self.n_states = int(theta.shape[0])
+        N.tbpm_set_phase_states(self.ctx, self.n_states, theta)
+        return self
+
+    def set_states(self, psi0):
+        self.n_states = int(psi0.shape[0])
+        N.tbpm_set_states(self.ctx, self.n_states, psi0)
+        return self
+
+    def launch_config(self, precision, max_group, threads):
+        N.tbpm_set_launch_config(self.ctx, precision, max_group, threads)
+        return self
+
+    # a2-a6
+    def propagate(self, z, n_steps, precision=N.TBPM_FP64, out=None, flags=0):
+        """C [n_samples, n_states, n_steps + 1] complex128 (numpy unless ``out``)."""
+        if out is None:
+            out = np.empty((self.n_samples, self.n_states, n_steps + 1), dtype=np.complex128)
+        N.tbpm_propagate(self.ctx, float(z), int(n_steps), precision, out, None, flags)
+        return out
+
+    def correlation(self):
+        out = np.empty((self.n_samples, self.stats()["n_steps"] + 1), dtype=np.complex128)
+        N.tbpm_correlation(self.ctx, out)
+        return out
+
+    def states(self):
+        out = np.empty((self.n_states, self.n_orb), dtype=np.complex128)
+        N.tbpm_get_states(self.ctx, out)
+        return out
+
+    def norms(self):
+        out = np.empty((self.n_samples, self.n_states, self.stats()["n_steps"] + 1))
+        N.tbpm_get_norms(self.ctx, out)
+        return out
+
+    def stats(self) -> dict:
+        return N.tbpm_get_stats(self.ctx)
+
+
+def dos(corr_avg, tau, e_min, e_max, n_e, window=N.TBPM_WINDOW_HANN):
+    """(energies, D) from one averaged correlation C_0 .. C_N (host FP64)."""
+    c = np.ascontiguousarray(corr_avg, dtype=np.complex128)
+    en = np.empty(n_e)
+    d = np.empty(n_e)
+    N.tbpm_dos(c, c.shape[0] - 1, tau, window, e_min, e_max, n_e, en, d)
+    return en, d
+
+
+def _c64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ci64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)

@@ -1,0 +1,94 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports
+every entry point ``include/tbpm.h`` declares, and its pure-host functions
+(Bessel table, DOS transform) agree with the oracle and SciPy.  No GPU."""
+import math
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+import scipy.special
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2209_00806_gb300 import build_native
+    build_native.build()
+    from paper_2209_00806_gb300 import _native
+    return _native
+
+
+def declared_functions():
+    text = (ROOT / "include" / "tbpm.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tbpm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(native):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(native.lib, n), n
+    bound = {s[0] for s in native.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_library_is_built_for_sm103a(native):
+    import subprocess
+    out = subprocess.run(["cuobjdump", "--list-elf", str(native._LIB_PATH)],
+                         capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_no_device_gives_a_status_not_a_crash(native):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(native.TbpmError) as e:
+        native.tbpm_create(0)
+    assert e.value.code == native.TBPM_E_CUDA
+
+
+@pytest.mark.parametrize("z", [0.3, math.pi / 2, math.pi, 7.5, 40.0, 300.0])
+def test_bessel_table_vs_scipy(native, z):
+    J = native.tbpm_bessel_coefficients(z, max_terms=int(z) + 100)
+    M = len(J)
+    ref = scipy.special.jv(np.arange(M + 1), z)
+    assert np.max(np.abs(J - ref[:M])) < 1e-15 * max(1.0, math.sqrt(z))
+    assert M > z and abs(ref[M]) < 1e-15
+    assert all(not (m > z and abs(ref[m]) < 1e-15) for m in range(M))
+
+
+def test_bessel_table_matches_oracle_term_count(native):
+    import oracle
+    for z in (0.5, math.pi / 2, math.pi, 3.9):
+        assert len(native.tbpm_bessel_coefficients(z)) == oracle.n_terms(z)
+    assert len(native.tbpm_bessel_coefficients(math.pi / 2)) == 16
+
+
+def test_bessel_table_rejects_bad_z(native):
+    for z in (0.0, -1.0, float("nan"), 2000.0):
+        with pytest.raises(native.TbpmError):
+            native.tbpm_bessel_coefficients(z)
+
+
+def test_dos_transform_vs_oracle(native):
+    import oracle
+    from paper_2209_00806_gb300 import dos
+    gen = np.random.default_rng(1)
+    n = 300
+    E = gen.uniform(-3, 3, 40)
+    w = gen.uniform(0, 1, 40)
+    w /= w.sum()
+    tau = 0.15
+    c = np.exp(-1j * np.outer(np.arange(n + 1) * tau, E)) @ w
+    en, d = dos(c, tau, -4.0, 4.0, 777)
+    en2, d2 = oracle.dos(c, tau, -4.0, 4.0, 777)
+    assert np.array_equal(en, en2)
+    assert np.max(np.abs(d - d2)) < 1e-12
+    with pytest.raises(native.TbpmError):
+        dos(c, tau, 1.0, -1.0, 10)

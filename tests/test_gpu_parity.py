@@ -1,0 +1,219 @@
+"""GPU parity of the CUDA path against the CPU FP64 oracle, element by
+element on the same seeded inputs, through the C ABI.
+
+Tolerances: FP64 C(t) within 1e-10 absolute (C_0 = 1 sets the scale); FP32
+states give a DOS whose L1 distance sum_k |D_k - D_k^oracle| dE is within
+1e-4 (D integrates to 1)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tbpm_inputs import lattice, rng, workloads
+
+from . import exact
+
+pytestmark = pytest.mark.gpu
+
+Z = math.pi / 2
+
+
+@pytest.fixture(scope="module")
+def tb():
+    import paper_2209_00806_gb300 as tb
+    return tb
+
+
+def run_gpu(tb, smp, s, theta, n_steps, precision=0, offsets=None, flags=0, bflags=0,
+            cfg=None):
+    with tb.Propagator() as p:
+        p.build_sample(smp, s, sample_offsets=offsets, flags=bflags)
+        if cfg:
+            p.launch_config(precision, *cfg)
+        p.set_phase_states(np.ascontiguousarray(theta))
+        c = p.propagate(Z, n_steps, precision, flags=flags)
+        return c, p.stats(), p.states(), p.norms()
+
+
+def run_oracle(smp, s, theta, n_steps, want_psi=False):
+    psi0 = oracle.phase_states(theta)
+    return oracle.propagate(smp, s, Z, n_steps, psi0, want_psi=want_psi, want_norms=want_psi)
+
+
+def test_gpu_fp64_disordered_vacancies_several_groups(tb):
+    smp = lattice.graphene(24, 20, pbc=True, seed=5, onsite_w=1.0, vacancy_frac=0.02)
+    th = rng.phases(9, 7, smp.n_orb)       # 7 states -> groups 4 + 2 + 1
+    c, st, phi, nrm = run_gpu(tb, smp, 9.5, th, 200)
+    ref, onrm, psi = run_oracle(smp, 9.5, th, 200, want_psi=True)
+    assert st["group_width"] == [4, 2, 1] and st["n_terms"] == 16
+    assert np.max(np.abs(c[0] - ref)) < 1e-10
+    assert np.max(np.abs(phi - psi)) < 1e-10
+    assert np.max(np.abs(nrm[0] - onrm)) < 1e-10
+
+
+@pytest.mark.parametrize("cfg", [(1, 64), (2, 128), (8, 1024)])
+def test_gpu_fp64_ragged_rows_launch_shapes(tb, cfg):
+    smp = lattice.random_graph(3001, 9000, seed=3, onsite_w=2.0)   # degrees 0 .. ~15
+    H = exact.dense_h(smp)
+    s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(H)))
+    th = rng.phases(4, 5, smp.n_orb)
+    c, st, _, _ = run_gpu(tb, smp, s, th, 60, cfg=cfg)
+    ref = run_oracle(smp, s, th, 60)
+    assert np.max(np.abs(c[0] - ref)) < 1e-10
+
+
+def test_gpu_fp64_graphene_dos_full_workload(tb):
+    """64x64 pristine periodic graphene, 1024 steps: oracle and Bloch exact."""
+    w = workloads.graphene_dos()
+    th = w.thetas()[0]
+    c, st, _, _ = run_gpu(tb, w.sample, w.s, th, w.n_steps)
+    ref = run_oracle(w.sample, w.s, th, w.n_steps)
+    assert np.max(np.abs(c[0, 0] - ref[0])) < 1e-10
+    times = w.tau * np.arange(w.n_steps + 1)
+    bloch = exact.graphene_bloch_corr(64, 64, lattice.T_NN, oracle.phase_states(th)[0], times)
+    assert np.max(np.abs(c[0, 0] - bloch)) < 1e-10
+    en, d = tb.dos(c[0].mean(axis=0), w.tau, *w.e_range, w.n_energies)
+    en2, d2 = oracle.dos(ref.mean(axis=0), w.tau, *w.e_range, w.n_energies)
+    assert np.max(np.abs(d - d2)) < 1e-9
+
+
+def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
+    parts = [lattice.graphene(L, L, pbc=True, seed=10 + L, onsite_w=0.3 * L % 2)
+             for L in (5, 9, 23)]
+    smp, offs = lattice.concat(parts)
+    th_parts = [rng.phases(40 + k, 3, p.n_orb) for k, p in enumerate(parts)]
+    th = np.concatenate(th_parts, axis=1)
+    c64, _, _, _ = run_gpu(tb, smp, 9.5, th, 120, offsets=offs)
+    c32, st32, _, _ = run_gpu(tb, smp, 9.5, th, 120, precision=1, offsets=offs)
+    for k, p in enumerate(parts):
+        ref = run_oracle(p, 9.5, th_parts[k], 120)
+        assert np.max(np.abs(c64[k] - ref)) < 1e-10
+        assert np.max(np.abs(c32[k] - ref)) < 2e-5
+
+
+def test_gpu_fp32_dos_l1(tb):
+    w = workloads.disordered_graphene(L=96, n_steps=1024, n_energies=2048)
+    th = w.thetas()[0]
+    c32, st, _, _ = run_gpu(tb, w.sample, w.s, th, w.n_steps, precision=1)
+    ref = run_oracle(w.sample, w.s, th, w.n_steps)
+    en, d32 = tb.dos(c32[0].mean(axis=0), w.tau, *w.e_range, w.n_energies)
+    _, d64 = oracle.dos(ref.mean(axis=0), w.tau, *w.e_range, w.n_energies)
+    l1 = np.sum(np.abs(d32 - d64)) * (en[1] - en[0])
+    assert l1 < 1e-4, l1
+    assert st["max_norm_drift"] < 1e-3
+
+
+def test_gpu_rcm_reorder_and_permuted_input(tb):
+    smp = lattice.graphene(16, 16, pbc=True, seed=2, onsite_w=1.0, vacancy_frac=0.02)
+    perm = np.random.default_rng(7).permutation(smp.n_orb)
+    shuffled = lattice.permute(smp, perm)
+    th = rng.phases(5, 2, smp.n_orb)
+    th_sh = np.empty_like(th)
+    th_sh[:, perm] = th
+    c0, _, _, _ = run_gpu(tb, smp, 9.5, th, 100)
+    c1, _, phi1, _ = run_gpu(tb, shuffled, 9.5, th_sh, 100, bflags=8)
+    _, _, phi0, _ = run_gpu(tb, smp, 9.5, th, 100)
+    assert np.max(np.abs(c0 - c1)) < 1e-12
+    assert np.max(np.abs(phi1[:, perm] - phi0)) < 1e-12
+
+
+def test_gpu_device_inputs_match_host_inputs(tb):
+    import torch
+    smp = lattice.graphene(12, 12, pbc=True, seed=1, onsite_w=1.0, vacancy_frac=0.03)
+    th = rng.phases(3, 2, smp.n_orb)
+    ch, _, _, _ = run_gpu(tb, smp, 9.5, th, 80)
+    d = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    with tb.Propagator() as p:
+        p.build(smp.n_orb, d(smp.onsite, torch.float64), d(smp.hop_i, torch.int64),
+                d(smp.hop_j, torch.int64), d(smp.hop_v, torch.float64), 9.5)
+        p.set_phase_states(d(th, torch.float64))
+        out = torch.empty((1, 2, 81), dtype=torch.complex128, device="cuda")
+        p.propagate(Z, 80, 0, out=out)
+        cd = out.cpu().numpy()
+    assert np.max(np.abs(cd - ch)) < 1e-15
+
+
+def test_gpu_graph_mode_and_determinism(tb):
+    smp = lattice.graphene(20, 20, pbc=True, seed=8, onsite_w=1.0, vacancy_frac=0.01)
+    th = rng.phases(6, 4, smp.n_orb)
+    for prec in (0, 1):
+        a, _, _, _ = run_gpu(tb, smp, 9.5, th, 50, precision=prec)
+        b, _, _, _ = run_gpu(tb, smp, 9.5, th, 50, precision=prec)
+        g, _, _, _ = run_gpu(tb, smp, 9.5, th, 50, precision=prec, flags=2)
+        pr, stp, _, _ = run_gpu(tb, smp, 9.5, th, 50, precision=prec, flags=1)
+        assert np.array_equal(a, b) and np.array_equal(a, g) and np.array_equal(a, pr)
+        assert stp["ms_term_avg"] > 0 and stp["term_launches"] == 50 * 12
+
+
+def test_gpu_resume_continues_the_propagation(tb):
+    smp = lattice.graphene(10, 10, pbc=True, seed=3, onsite_w=0.5)
+    th = rng.phases(2, 3, smp.n_orb)
+    with tb.Propagator() as p:
+        p.build_sample(smp, 9.0)
+        p.set_phase_states(th)
+        full = p.propagate(Z, 60, 0)
+        phi_full = p.states()
+        p.propagate(Z, 25, 0)
+        p.propagate(Z, 35, 0, flags=4)
+        assert np.max(np.abs(p.states() - phi_full)) < 1e-12
+
+
+def test_gpu_errors_are_statuses(tb):
+    N = tb._native
+    smp = lattice.graphene(6, 6, pbc=True)
+    p = tb.Propagator()
+    with pytest.raises(N.TbpmError) as e:
+        p.propagate(Z, 3)
+    assert e.value.code == N.TBPM_E_STATE
+    bad = lattice.Sample(4, None, np.array([0, 2]), np.array([1, 2]), np.array([1.0, 1.0]))
+    with pytest.raises(N.TbpmError) as e:
+        p.build_sample(bad, 3.0)
+    assert e.value.code == N.TBPM_E_INVALID_ARG and "itself" in str(e.value)
+    out = lattice.Sample(4, None, np.array([0, 2]), np.array([1, 7]), np.array([1.0, 1.0]))
+    with pytest.raises(N.TbpmError) as e:
+        p.build_sample(out, 3.0)
+    assert e.value.code == N.TBPM_E_INVALID_ARG
+    with pytest.raises(N.TbpmError) as e:
+        p.build_sample(smp, 5.0, flags=N.TBPM_BUILD_STRICT_BOUND)
+    assert e.value.code == N.TBPM_E_SPECTRAL_BOUND
+    # s well below the spectral radius: the Chebyshev series diverges
+    p.build_sample(smp, 3.0)
+    p.set_phase_states(rng.phases(1, 1, smp.n_orb))
+    with pytest.raises(N.TbpmError) as e:
+        p.propagate(Z, 40)
+    assert e.value.code in (N.TBPM_E_NORM_DRIFT, N.TBPM_E_NONFINITE)
+    # NaN in the initial state
+    p.build_sample(smp, 9.0)
+    psi = oracle.phase_states(rng.phases(1, 1, smp.n_orb))
+    psi[0, 3] = np.nan
+    p.set_states(psi)
+    with pytest.raises(N.TbpmError) as e:
+        p.propagate(Z, 2)
+    assert e.value.code == N.TBPM_E_NONFINITE
+    # the context stays usable
+    p.set_phase_states(rng.phases(1, 1, smp.n_orb))
+    c = p.propagate(Z, 2)
+    assert abs(c[0, 0, 0] - 1) < 1e-14
+    p.close()
+
+
+def test_gpu_disordered_graphene_full_size_sampled(tb):
+    """2048x2048 disordered graphene with vacancies (8,304,722 orbitals), four
+    states, the launch shape the benchmark uses: the first steps against the
+    oracle on one state, and size-independent properties over 64 steps."""
+    w = workloads.disordered_graphene()
+    th = np.concatenate([t for t in w.thetas()], axis=1)
+    with tb.Propagator() as p:
+        p.build_sample(w.sample, w.s)
+        p.set_phase_states(th)
+        c64 = p.propagate(w.z, 64, 0)
+        n64 = p.norms()
+        c32 = p.propagate(w.z, 64, 1)
+        n32 = p.norms()
+    ref = run_oracle(w.sample, w.s, th[:1], 3)
+    assert np.max(np.abs(c64[0, 0, :4] - ref[0])) < 1e-12
+    assert np.max(np.abs(c32[0, 0, :4] - ref[0])) < 1e-6
+    assert np.max(np.abs(n64 - 1)) < 1e-12 and np.max(np.abs(n32 - 1)) < 1e-4
+    assert np.all(np.abs(c64) <= 1 + 1e-12)
+    assert np.max(np.abs(c64 - c32)) < 1e-4
