@@ -58,6 +58,8 @@ def _load():
         lib.oracle_propagate.argtypes = [i64, P, i64, P, P, P, P, f64, f64, i32, i32,
                                          P, P, P, P]
         lib.oracle_dos.argtypes = [P, i32, f64, f64, f64, i32, P, P]
+        lib.oracle_gradient.argtypes = [i64, P, i64, P, P, P, f64, f64, i32, i32, P, P, P, P]
+        lib.oracle_dos_adjoint.argtypes = [P, i32, f64, f64, f64, i32, P]
         _lib = lib
     return _lib
 
@@ -152,3 +154,34 @@ def dos(corr_avg: np.ndarray, tau: float, e_min: float, e_max: float, n_e: int):
     if rc != 0:
         raise ValueError("bad DOS arguments")
     return en, d
+
+
+def gradient(sample, s: float, z: float, n_steps: int, psi0: np.ndarray, gbar: np.ndarray):
+    """(dL/dt_b [n_hop], dL/deps_i [n_orb]) for a loss with
+    gbar[p, n] = dL/dRe C_n^(p) + i dL/dIm C_n^(p).  Real hoppings only."""
+    psi0 = np.ascontiguousarray(np.atleast_2d(psi0), dtype=np.complex128)
+    gbar = np.ascontiguousarray(np.atleast_2d(gbar), dtype=np.complex128)
+    S, n = psi0.shape
+    if gbar.shape != (S, n_steps + 1):
+        raise ValueError("gbar must be [n_states, n_steps + 1]")
+    if np.iscomplexobj(sample.hop_v):
+        raise ValueError("gradients need real hoppings")
+    hi, hj, re, _ = _hops(sample)
+    ons = _f64(sample.onsite)
+    gh = np.empty(sample.n_hop)
+    go = np.empty(n)
+    rc = _load().oracle_gradient(n, _p(ons), sample.n_hop, _p(hi), _p(hj), _p(re), s, z,
+                                 n_steps, S, _p(psi0), _p(gbar), _p(gh), _p(go))
+    if rc != 0:
+        raise RuntimeError(f"oracle_gradient failed ({rc})")
+    return gh, go
+
+
+def dos_adjoint(dl_dd: np.ndarray, n_steps: int, tau: float, e_min: float, e_max: float):
+    """gbar_n of the averaged correlation from dL/dD on the DOS grid."""
+    d = np.ascontiguousarray(dl_dd, dtype=np.float64)
+    out = np.empty(n_steps + 1, dtype=np.complex128)
+    rc = _load().oracle_dos_adjoint(_p(d), n_steps, tau, e_min, e_max, d.shape[0], _p(out))
+    if rc != 0:
+        raise ValueError("bad DOS adjoint arguments")
+    return out

@@ -224,3 +224,160 @@ int oracle_dos(const double complex *corr, int n_steps, double tau, double e_min
     }
     return ORACLE_OK;
 }
+
+/* ---- adjoint (gradients of a real loss of the correlations) -------------
+ *
+ * The loss L depends on the correlations C_n^(p) of every state p.  The
+ * caller supplies gbar[p][n] = dL/dRe C_n + i dL/dIm C_n, so that
+ * dL = sum Re(conj(gbar) dC).  Since C_n = <psi0|phi_n>, the adjoint source
+ * of phi_n is gbar_n psi0, and the adjoint of the whole trajectory obeys
+ *   Lambda_N = gbar_N psi0,  Lambda_n = gbar_n psi0 + P^dagger Lambda_{n+1},
+ * with P = sum_m c_m T^_m(H~) the one-step propagator of Sec. 2.2.  Within a
+ * step the paper's forward recurrence is differentiated in reverse order:
+ *   mu_{M-1} = c_{M-1} Lambda,  mu_{M-2} = c_{M-2} Lambda + 2i H~ mu_{M-1},
+ *   mu_m = c_m Lambda + 2i H~ mu_{m+1} + mu_{m+2}          (1 <= m <= M-3),
+ *   mu_0 = c_0 Lambda + i H~ mu_1 + mu_2                     (= P^dagger Lambda),
+ * and each product T^_m = -2i H~ T^_{m-1} + ... (factor -i for m = 1)
+ * contributes, for a real symmetric change dH~ of entries (i, j) and (j, i),
+ *   dL += g_m Im(conj(mu_{m,i}) T^_{m-1,j} + conj(mu_{m,j}) T^_{m-1,i}) dH~_ij,
+ * g_m = 2 (m >= 2) or 1 (m = 1); a diagonal change gives
+ * g_m Im(conj(mu_{m,i}) T^_{m-1,i}).  With H~ = H / s: dL/dt_b and
+ * dL/deps_i carry a factor 1/s.  Real hoppings only.  Every phi_n is kept,
+ * so this is for small systems. */
+int oracle_gradient(int64_t n, const double *onsite, int64_t n_hop, const int64_t *hop_i,
+                    const int64_t *hop_j, const double *hop_re, double s, double z,
+                    int n_steps, int n_states, const double complex *psi0,
+                    const double complex *gbar, double *grad_hop, double *grad_onsite)
+{
+    if (n <= 0 || n_steps < 0 || n_states <= 0 || !(s > 0.0) || !psi0 || !gbar ||
+        !grad_hop || !grad_onsite)
+        return ORACLE_E_ARG;
+    int M = oracle_n_terms(z);
+    if (M < 2)
+        return ORACLE_E_RANGE;
+    double J[129], c[129];
+    oracle_bessel(z, M, J);
+    c[0] = J[0];
+    for (int m = 1; m < M; ++m)
+        c[m] = 2.0 * J[m];
+
+    size_t vec = (size_t)n * sizeof(double complex);
+    double complex *traj = malloc(vec * (size_t)(n_steps + 1));
+    double complex *T = malloc(vec * (size_t)M);
+    double complex *mu = malloc(vec * (size_t)(M + 2));
+    double complex *lam = malloc(vec);
+    double complex *tmp = malloc(vec);
+    if (!traj || !T || !mu || !lam || !tmp) {
+        free(traj); free(T); free(mu); free(lam); free(tmp);
+        return ORACLE_E_NOMEM;
+    }
+    for (int64_t b = 0; b < n_hop; ++b)
+        grad_hop[b] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        grad_onsite[i] = 0.0;
+
+    for (int p = 0; p < n_states; ++p) {
+        const double complex *a = psi0 + (size_t)p * n;
+        const double complex *g = gbar + (size_t)p * (n_steps + 1);
+        /* forward trajectory phi_0 .. phi_N */
+        memcpy(traj, a, vec);
+        for (int k = 0; k < n_steps; ++k) {
+            double complex *phi = traj + (size_t)k * n, *nxt = traj + (size_t)(k + 1) * n;
+            double complex *T0 = T, *T1 = T + n;
+            memcpy(T0, phi, vec);
+            oracle_apply_h(n, onsite, n_hop, hop_i, hop_j, hop_re, NULL, s, T0, T1);
+            for (int64_t i = 0; i < n; ++i) {
+                T1[i] *= -I;
+                nxt[i] = c[0] * T0[i] + c[1] * T1[i];
+            }
+            for (int m = 2; m < M; ++m) {
+                double complex *Tm = T + (size_t)m * n;
+                oracle_apply_h(n, onsite, n_hop, hop_i, hop_j, hop_re, NULL, s,
+                               T + (size_t)(m - 1) * n, Tm);
+                for (int64_t i = 0; i < n; ++i) {
+                    Tm[i] = -2.0 * I * Tm[i] + T[(size_t)(m - 2) * n + i];
+                    nxt[i] += c[m] * Tm[i];
+                }
+            }
+        }
+        /* backward */
+        for (int64_t i = 0; i < n; ++i)
+            lam[i] = g[n_steps] * a[i];
+        for (int k = n_steps - 1; k >= 0; --k) {
+            const double complex *phi = traj + (size_t)k * n;
+            /* the step's polynomials T^_0 .. T^_{M-1} */
+            memcpy(T, phi, vec);
+            oracle_apply_h(n, onsite, n_hop, hop_i, hop_j, hop_re, NULL, s, T, T + n);
+            for (int64_t i = 0; i < n; ++i)
+                T[n + i] *= -I;
+            for (int m = 2; m < M; ++m) {
+                double complex *Tm = T + (size_t)m * n;
+                oracle_apply_h(n, onsite, n_hop, hop_i, hop_j, hop_re, NULL, s,
+                               T + (size_t)(m - 1) * n, Tm);
+                for (int64_t i = 0; i < n; ++i)
+                    Tm[i] = -2.0 * I * Tm[i] + T[(size_t)(m - 2) * n + i];
+            }
+            /* mu_{M+1} = mu_M = 0, then the reverse recurrence */
+            memset(mu + (size_t)M * n, 0, 2 * vec);
+            for (int m = M - 1; m >= 0; --m) {
+                double complex *mm = mu + (size_t)m * n;
+                if (m == M - 1) {
+                    for (int64_t i = 0; i < n; ++i)
+                        mm[i] = c[m] * lam[i];
+                    continue;
+                }
+                oracle_apply_h(n, onsite, n_hop, hop_i, hop_j, hop_re, NULL, s,
+                               mu + (size_t)(m + 1) * n, tmp);
+                double complex f = (m == 0) ? I : 2.0 * I;
+                for (int64_t i = 0; i < n; ++i)
+                    mm[i] = c[m] * lam[i] + f * tmp[i] + mu[(size_t)(m + 2) * n + i];
+            }
+            /* gradient contributions of T^_m = (-i g_m H~) T^_{m-1} + ... */
+            for (int m = 1; m < M; ++m) {
+                double gm = (m == 1) ? 1.0 : 2.0;
+                const double complex *um = mu + (size_t)m * n;
+                const double complex *tv = T + (size_t)(m - 1) * n;
+                for (int64_t b = 0; b < n_hop; ++b) {
+                    int64_t i = hop_i[b], j = hop_j[b];
+                    grad_hop[b] += gm * cimag(conj(um[i]) * tv[j] + conj(um[j]) * tv[i]) / s;
+                }
+                for (int64_t i = 0; i < n; ++i)
+                    grad_onsite[i] += gm * cimag(conj(um[i]) * tv[i]) / s;
+            }
+            /* Lambda_k = gbar_k psi0 + P^dagger Lambda_{k+1} */
+            for (int64_t i = 0; i < n; ++i)
+                lam[i] = g[k] * a[i] + mu[i];
+        }
+    }
+    free(traj); free(T); free(mu); free(lam); free(tmp);
+    return ORACLE_OK;
+}
+
+/* Adjoint of oracle_dos: given dL/dD_k for each energy bin, return
+ * gbar_n = dL/dRe C_n + i dL/dIm C_n of the averaged correlation.  From
+ * D_k = (tau/pi)[Re C_0 / 2 + sum_{n=1}^{N-1} w_n Re(e^{i E_k n tau} C_n)]:
+ *   gbar_0 = (tau / 2 pi) sum_k dL/dD_k,
+ *   gbar_n = (tau / pi) w_n sum_k dL/dD_k e^{-i E_k n tau}   (1 <= n < N),
+ *   gbar_N = 0. */
+int oracle_dos_adjoint(const double *dl_dd, int n_steps, double tau, double e_min,
+                       double e_max, int n_e, double complex *gbar)
+{
+    if (n_steps < 1 || n_e < 1 || !(tau > 0.0) || !(e_max > e_min))
+        return ORACLE_E_ARG;
+    double de = (e_max - e_min) / n_e;
+    double s0 = 0.0;
+    for (int k = 0; k < n_e; ++k)
+        s0 += dl_dd[k];
+    gbar[0] = tau / (2.0 * M_PI) * s0;
+    for (int n = 1; n < n_steps; ++n) {
+        double w = 0.5 * (1.0 + cos(M_PI * n / n_steps));
+        double complex acc = 0.0;
+        for (int k = 0; k < n_e; ++k) {
+            double ph = (e_min + (k + 0.5) * de) * n * tau;
+            acc += dl_dd[k] * (cos(ph) - I * sin(ph));
+        }
+        gbar[n] = tau / M_PI * w * acc;
+    }
+    gbar[n_steps] = 0.0;
+    return ORACLE_OK;
+}

@@ -14,8 +14,8 @@ ROOT = Path(__file__).resolve().parents[1]
 
 @pytest.fixture(scope="module")
 def native():
-    from paper_2209_00806_gb300 import build_native
-    build_native.build()
+    import __graft_entry__
+    __graft_entry__._build_module().build()
     from paper_2209_00806_gb300 import _native
     return _native
 
