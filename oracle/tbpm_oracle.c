@@ -64,6 +64,25 @@ int oracle_bessel(double z, int m_max, double *J)
     return ORACLE_OK;
 }
 
+/* Compensated (Neumaier) running sum: the inner products below add up
+ * millions of terms of equal size, where a plain running sum drifts by
+ * ~1e-10; this keeps the sum exact to about one rounding. */
+typedef struct {
+    double s, c;
+} oracle_sum;
+
+static void sum_add(oracle_sum *k, double x)
+{
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x))
+        k->c += (k->s - t) + x;
+    else
+        k->c += (x - t) + k->s;
+    k->s = t;
+}
+
+static double sum_value(const oracle_sum *k) { return k->s + k->c; }
+
 /* Number of Chebyshev coefficients M: the series keeps m = 0 .. M-1, where
  * M is the first m > z with |J_m(z)| < 1e-15. */
 int oracle_n_terms(double z)
@@ -182,15 +201,18 @@ int oracle_propagate(int64_t n, const double *onsite, int64_t n_hop, const int64
                 }
                 memcpy(phi, acc, (size_t)n * sizeof(double complex));
             }
-            double complex c = 0.0;
-            double nn = 0.0;
+            /* C_k = sum_i conj(psi0_i) phi_i and <phi|phi>, each summed with
+             * compensation */
+            oracle_sum cre = {0, 0}, cim = {0, 0}, nn = {0, 0};
             for (int64_t i = 0; i < n; ++i) {
-                c += conj(a[i]) * phi[i];
-                nn += creal(phi[i]) * creal(phi[i]) + cimag(phi[i]) * cimag(phi[i]);
+                double complex v = conj(a[i]) * phi[i];
+                sum_add(&cre, creal(v));
+                sum_add(&cim, cimag(v));
+                sum_add(&nn, creal(phi[i]) * creal(phi[i]) + cimag(phi[i]) * cimag(phi[i]));
             }
-            corr[(size_t)p * (n_steps + 1) + k] = c;
+            corr[(size_t)p * (n_steps + 1) + k] = sum_value(&cre) + I * sum_value(&cim);
             if (norms)
-                norms[(size_t)p * (n_steps + 1) + k] = nn;
+                norms[(size_t)p * (n_steps + 1) + k] = sum_value(&nn);
         }
         if (psi_out)
             memcpy(psi_out + (size_t)p * n, phi, (size_t)n * sizeof(double complex));

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <string>
 #include <vector>
 
@@ -220,6 +222,15 @@ __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int3
     atomicMax(gersh_bits, (unsigned long long)__double_as_longlong(g));
 }
 
+__global__ void k_bond_rows(int64_t n_hop, const int64_t *hi, const int64_t *hj,
+                            const int32_t *user_to_row, int32_t *rows)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n_hop) return;
+    rows[2 * b] = user_to_row[hi[b]];
+    rows[2 * b + 1] = user_to_row[hj[b]];
+}
+
 __global__ void k_to_f32(int64_t n, const double *src, float *dst)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -241,6 +252,7 @@ void free_build(BuildOutput &b)
     cudaFree(b.diag64);
     cudaFree(b.diag32);
     cudaFree(b.chunk_sample);
+    cudaFree(b.bond_rows);
     b = BuildOutput();
 }
 
@@ -343,6 +355,13 @@ int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
     CK(cudaMemcpyAsync(out.chunk_sample, cs.data(), cs.size() * sizeof(int32_t),
                        cudaMemcpyHostToDevice, st));
 
+    out.n_hop = in.n_hop;
+    if (keep64 && in.n_hop > 0) {      // bond -> rows, for the adjoint's parameter gradients
+        CK(cudaMalloc(&out.bond_rows, 2 * in.n_hop * sizeof(int32_t)));
+        k_bond_rows<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j,
+                                                           out.user_to_row, out.bond_rows);
+        CK(cudaGetLastError());
+    }
     if (keep32) {
         CK(cudaMalloc(&out.val32, nnz_alloc * sizeof(float)));
         CK(cudaMalloc(&out.diag32, n_rows * sizeof(float)));

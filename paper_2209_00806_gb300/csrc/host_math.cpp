@@ -52,6 +52,44 @@ int bessel_miller(double z, double tol, int max_terms, double *J, int *n_terms)
     return TBPM_OK;
 }
 
+// Adjoint of the DOS transform: for dL/dD_k on the bin centres, the
+// derivative of L with respect to the averaged correlation,
+//   gbar_n = dL/dRe C_n + i dL/dIm C_n,
+//   gbar_0 = (tau / 2 pi) sum_k dL/dD_k,
+//   gbar_n = (tau / pi) w_n sum_k dL/dD_k exp(-i E_k n tau),  0 < n < N,
+//   gbar_N = 0.
+// The phase exp(-i E_k n tau) advances by one rotation per n and is
+// re-anchored from cos/sin every 64 steps.
+int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_min,
+                double e_max, double *gbar_out)
+{
+    typedef std::complex<double> cd;
+    const double de = (e_max - e_min) / n_e;
+    std::vector<cd> acc(n_steps + 1, cd(0.0, 0.0));
+    double s0 = 0.0;
+    for (int k = 0; k < n_e; ++k) s0 += dl_dd[k];
+    for (int k = 0; k < n_e; ++k) {
+        const double E = e_min + (k + 0.5) * de;
+        const cd step(cos(E * tau), -sin(E * tau));
+        cd ph(1.0, 0.0);
+        for (int n = 1; n < n_steps; ++n) {
+            if (n % 64 == 0) ph = cd(cos(E * tau * n), -sin(E * tau * n));
+            else ph *= step;
+            acc[n] += dl_dd[k] * ph;
+        }
+    }
+    gbar_out[0] = tau / (2.0 * M_PI) * s0;
+    gbar_out[1] = 0.0;
+    for (int n = 1; n < n_steps; ++n) {
+        const double w = 0.5 * (1.0 + cos(M_PI * (double)n / (double)n_steps));
+        gbar_out[2 * n] = tau / M_PI * w * acc[n].real();
+        gbar_out[2 * n + 1] = tau / M_PI * w * acc[n].imag();
+    }
+    gbar_out[2 * n_steps] = 0.0;
+    gbar_out[2 * n_steps + 1] = 0.0;
+    return TBPM_OK;
+}
+
 }  // namespace tbpm
 
 // ---- C ABI: host functions --------------------------------------------------
@@ -91,4 +129,13 @@ extern "C" int tbpm_dos(const double *corr, int n_steps, double tau, int window,
         dos_out[k] = tau / M_PI * (c0 + s.real());
     }
     return TBPM_OK;
+}
+
+extern "C" int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau,
+                                int window, double e_min, double e_max, double *gbar_out)
+{
+    if (!dl_dd || n_e < 1 || n_steps < 1 || !(tau > 0.0) || !(e_max > e_min) || !gbar_out)
+        return TBPM_E_INVALID_ARG;
+    if (window != TBPM_WINDOW_HANN) return TBPM_E_UNSUPPORTED;
+    return tbpm::dos_adjoint(dl_dd, n_e, n_steps, tau, e_min, e_max, gbar_out);
 }

@@ -68,6 +68,22 @@ struct ReduceArgs {
     int *error_flags;                // bit 0 drift, bit 1 non-finite
 };
 
+// One backward (adjoint) term with gradient accumulation, FP64:
+//   out = c psi + gamma (-i) (H~ x) + z [+ gbar_step psi0],
+//   G_rc += gfac Im(conj(x_c) T_r) for every stored entry, Gdiag_r likewise.
+struct AdjArgs {
+    SellView H;
+    const void *x, *psi, *z, *T_own;
+    void *out;
+    double c, gamma, gfac;
+    double *G, *Gdiag;
+    const double2 *gbar;   // [n_samples][n_states][n_steps + 1] or nullptr
+    const void *psi0;
+    int n_states, state0, n_steps, step;
+    const int32_t *chunk_sample;
+    int64_t n_rows;
+};
+
 // Kernel launchers (cheb_kernels.cu).  `fp32` selects the value precision,
 // B the states per row (a group).  Return cudaError_t of the launch.
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
@@ -82,6 +98,16 @@ cudaError_t launch_set_states(const double2 *psi_user, int64_t n_orb, int n_stat
 cudaError_t launch_get_states(const void *psi, int64_t n_orb, int n_states,
                               const int32_t *user_to_row, int group_state0, int B,
                               int fp32, double2 *out_user, cudaStream_t st);
+
+// Adjoint kernels (adjoint_kernels.cu).
+cudaError_t launch_adj_term(const AdjArgs &a, int B, int threads, cudaStream_t st);
+cudaError_t launch_source_init(int64_t n_rows, int B, const int32_t *chunk_sample,
+                               const double2 *gbar, int n_states, int state0, int n_steps,
+                               int step, const void *psi0, void *out, cudaStream_t st);
+cudaError_t launch_param_grads(int64_t n_hop, const int32_t *bond_rows, const int64_t *slice_ptr,
+                               const int32_t *col, const double *G, const double *Gd,
+                               int64_t n_orb, const int32_t *user_to_row, double inv_s,
+                               double *grad_hop, double *grad_onsite, cudaStream_t st);
 
 // Builder (build_kernels.cu).
 struct BuildInput {
@@ -108,6 +134,8 @@ struct BuildOutput {
     double *diag64 = nullptr;
     float *diag32 = nullptr;
     int32_t *chunk_sample = nullptr; // [n_rows / kChunkRows]
+    int32_t *bond_rows = nullptr;    // [2 n_hop] rows of each bond (kept with FP64 values)
+    int64_t n_hop = 0;
     double gershgorin = 0.0;
     int max_width = 0;
 };
@@ -120,5 +148,7 @@ void free_build(BuildOutput &b);
 
 // Host math (host_math.cpp).
 int bessel_miller(double z, double tol, int max_terms, double *J, int *n_terms);
+int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_min,
+                double e_max, double *gbar_out);
 
 }  // namespace tbpm
