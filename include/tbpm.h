@@ -197,6 +197,30 @@ int tbpm_get_norms(tbpm_ctx *ctx, double *norms_out);
 int tbpm_dos(const double *corr, int n_steps, double tau, int window, double e_min,
              double e_max, int n_e, double *energies_out, double *dos_out);
 
+/* a8. Adjoint of the propagation (FP64): gradients of a real loss L of the
+ * correlations with respect to every hopping t_b and onsite energy eps_i.
+ *   gbar       complex128 [n_samples][n_states][n_steps + 1] (host or device,
+ *              `where`): dL/dRe C_n + i dL/dIm C_n of each state's C_n, as
+ *              tbpm_propagate defines C_n for the states currently set
+ *   K          checkpoint interval (states kept every K steps, recomputed
+ *              in between; memory ~ (N/K + K + M) state vectors)
+ *   grad_hop   double [n_hop] dL/dt_b, bonds in the order given to
+ *              tbpm_build_hamiltonian (host or device, `where_out`)
+ *   grad_onsite double [n_orb] dL/deps_i
+ * H~ is Hermitian, so the backward pass is the same Chebyshev series with +i
+ * in place of -i (the adjoint of the propagator of Sec. 2.2); no counterpart
+ * in the paper, which has no gradients.  Needs the FP64 Hamiltonian and real
+ * hoppings.  Overwrites the propagation state of the context.
+ * Errors: STATE, INVALID_ARG, OOM, CUDA. */
+int tbpm_propagate_adjoint(tbpm_ctx *ctx, double z, int n_steps, const double *gbar, int where,
+                           int K, double *grad_hop, double *grad_onsite, int where_out);
+
+/* Adjoint of tbpm_dos (host, FP64): from dL/dD_k on the n_e bins, the
+ * derivative gbar_n = dL/dRe C_n + i dL/dIm C_n of the averaged correlation,
+ * complex128 [n_steps + 1]. */
+int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int window,
+                     double e_min, double e_max, double *gbar_out);
+
 /* Launch shape of the propagation kernels for one precision: states are
  * split into groups of power-of-two width <= max_group (FP64 <= 8,
  * FP32 <= 16), each group propagated as one blocked sparse product per term;

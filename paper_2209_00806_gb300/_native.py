@@ -87,6 +87,8 @@ SIGNATURES = [
     ("tbpm_get_states", _I32, [P, P, _I32]),
     ("tbpm_get_norms", _I32, [P, P]),
     ("tbpm_dos", _I32, [P, _I32, _F64, _I32, _F64, _F64, _I32, P, P]),
+    ("tbpm_propagate_adjoint", _I32, [P, _F64, _I32, P, _I32, _I32, P, P, _I32]),
+    ("tbpm_dos_adjoint", _I32, [P, _I32, _I32, _F64, _I32, _F64, _F64, P]),
     ("tbpm_set_launch_config", _I32, [P, _I32, _I32, _I32]),
     ("tbpm_get_stats", _I32, [P, ctypes.POINTER(tbpm_stats)]),
 ]
@@ -211,6 +213,19 @@ def tbpm_get_norms(ctx, out):
 def tbpm_dos(corr, n_steps, tau, window, e_min, e_max, n_e, energies_out, dos_out):
     return check(None, lib.tbpm_dos(ptr(corr), n_steps, tau, window, e_min, e_max, n_e,
                                     ptr(energies_out), ptr(dos_out)))
+
+
+def tbpm_propagate_adjoint(ctx, z, n_steps, gbar, where, K, grad_hop, grad_onsite,
+                           where_out=None):
+    if where_out is None:
+        where_out = where_of(grad_hop)
+    return check(ctx, lib.tbpm_propagate_adjoint(ctx, z, n_steps, ptr(gbar), where, K,
+                                                 ptr(grad_hop), ptr(grad_onsite), where_out))
+
+
+def tbpm_dos_adjoint(dl_dd, n_e, n_steps, tau, window, e_min, e_max, gbar_out):
+    return check(None, lib.tbpm_dos_adjoint(ptr(dl_dd), n_e, n_steps, tau, window, e_min,
+                                            e_max, ptr(gbar_out)))
 
 
 def tbpm_set_launch_config(ctx, precision, max_group, threads):

@@ -953,3 +953,215 @@ extern "C" int tbpm_get_stats(tbpm_ctx *c, tbpm_stats *out)
     *out = c->stats;
     return TBPM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// a8: adjoint propagation with checkpoints every K steps.
+//
+// Forward: phi_0 .. phi_{N-1} are produced step by step; phi_{jK} is kept.
+// Backward, segment by segment from the last: the segment's states are
+// recomputed from its checkpoint, then for each step n (descending) the
+// forward polynomials T^_1 .. T^_{M-2} of phi_n are recomputed by the plain
+// recurrence and the conjugate Clenshaw schedule runs with gradient
+// accumulation (see adjoint_kernels.cu), ending in
+// Lambda_n = gbar_n psi0 + P^dagger Lambda_{n+1}.
+extern "C" int tbpm_propagate_adjoint(tbpm_ctx *c, double z, int n_steps, const double *gbar,
+                                      int where, int K, double *grad_hop, double *grad_onsite,
+                                      int where_out)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->have_h || c->n_states < 1)
+        return fail(c, TBPM_E_STATE, "build the Hamiltonian and set states first");
+    if (!c->H.val64 || (c->H.n_hop > 0 && !c->H.bond_rows))
+        return fail(c, TBPM_E_STATE, "the adjoint needs the FP64 Hamiltonian");
+    if (n_steps < 1 || K < 1 || !gbar || !grad_hop || !grad_onsite)
+        return fail(c, TBPM_E_INVALID_ARG, "bad adjoint arguments");
+    if ((where != TBPM_HOST && where != TBPM_DEVICE) ||
+        (where_out != TBPM_HOST && where_out != TBPM_DEVICE))
+        return fail(c, TBPM_E_INVALID_ARG, "where must be TBPM_HOST or TBPM_DEVICE");
+    if (K > n_steps) K = n_steps;
+    std::vector<double> J(kMaxTerms);
+    int M = 0;
+    if (bessel_miller(z, 1e-15, kMaxTerms, J.data(), &M) != TBPM_OK || M < 2)
+        return fail(c, TBPM_E_INVALID_ARG, "z out of range for the coefficient table");
+    std::vector<double> a(M);
+    a[0] = J[0];
+    for (int m = 1; m < M; ++m) a[m] = 2.0 * J[m];
+
+    int rc = enter(c);
+    if (rc) return rc;
+    rc = ensure_groups(c, TBPM_FP64);
+    if (rc) return rc;
+    c->have_run = false;      // the group buffers are reused as scratch below
+
+    const size_t n_g = (size_t)c->n_samples * c->n_states * (n_steps + 1);
+    double2 *d_gbar = nullptr;
+    bool gbar_owned = false;
+    rc = stage(c, reinterpret_cast<const double2 *>(gbar), n_g, where, &d_gbar, &gbar_owned);
+    if (rc) return rc;
+
+    int maxB = 1;
+    for (auto &g : c->groups) maxB = std::max(maxB, g.B);
+    const size_t vec = (size_t)c->H.n_rows * maxB * sizeof(double2);
+    const int nseg = (n_steps + K - 1) / K;
+    std::vector<void *> ckpt(nseg, nullptr), traj(K, nullptr), stash(M - 1, nullptr);
+    double *G = nullptr, *Gd = nullptr, *d_gh = nullptr, *d_go = nullptr;
+    auto release = [&]() {
+        for (void *p : ckpt) cudaFree(p);
+        for (void *p : traj) cudaFree(p);
+        for (void *p : stash) cudaFree(p);
+        cudaFree(G);
+        cudaFree(Gd);
+        if (where_out == TBPM_HOST) { cudaFree(d_gh); cudaFree(d_go); }
+        if (gbar_owned) cudaFree(d_gbar);
+    };
+    for (auto &p : ckpt) if (!rc) rc = dalloc(c, (char **)&p, vec);
+    for (size_t k = 1; k < traj.size() && !rc; ++k) rc = dalloc(c, (char **)&traj[k], vec);
+    for (auto &p : stash) if (!rc) rc = dalloc(c, (char **)&p, vec);
+    if (!rc) rc = dalloc(c, &G, (size_t)std::max<int64_t>(c->H.nnz_pad, 1));
+    if (!rc) rc = dalloc(c, &Gd, (size_t)c->H.n_rows);
+    if (!rc && where_out == TBPM_HOST) {
+        rc = dalloc(c, &d_gh, (size_t)std::max<int64_t>(c->H.n_hop, 1));
+        if (!rc) rc = dalloc(c, &d_go, (size_t)c->n_orb);
+    } else if (!rc) {
+        d_gh = grad_hop;
+        d_go = grad_onsite;
+    }
+    if (rc) { release(); return rc; }
+    cudaMemsetAsync(G, 0, std::max<int64_t>(c->H.nnz_pad, 1) * sizeof(double), c->st);
+    cudaMemsetAsync(Gd, 0, c->H.n_rows * sizeof(double), c->st);
+
+    SellView Hv;
+    Hv.slice_ptr = c->H.slice_ptr;
+    Hv.col = c->H.col;
+    Hv.val = c->H.val64;
+    Hv.diag = c->H.diag64;
+    const int threads = c->threads[TBPM_FP64];
+    int64_t launches = 0;
+    int fin = 0;
+    schedule(a, 0, &fin);
+
+    for (auto &g : c->groups) {
+        const int B = g.B;
+        TermArgs base;
+        memset(&base, 0, sizeof(base));
+        base.H = Hv;
+        base.chunk_sample = c->H.chunk_sample;
+        base.n_rows = c->H.n_rows;
+        auto term = [&](const void *x, const void *psi, const void *zz, void *out, double cc,
+                        double gamma) -> int {
+            TermArgs t = base;
+            t.x = x;
+            t.psi = psi;
+            t.z = zz;
+            t.out = out;
+            t.c_hi = cc;
+            t.gamma = gamma;
+            ++launches;
+            CUDA_OR_FAIL(c, launch_term(t, 0, B, threads, c->st));
+            return TBPM_OK;
+        };
+        // one forward Clenshaw step src -> dst (tmp: scratch)
+        auto step_into = [&](void *src, void *dst, void *tmp) -> int {
+            void *bufs[3];
+            bufs[0] = src;
+            bufs[fin] = dst;
+            bufs[3 - fin] = tmp;
+            int nx = 0;
+            for (const Launch &L : schedule(a, 0, &nx)) {
+                int r2 = term(L.x < 0 ? src : bufs[L.x], src, L.z < 0 ? nullptr : bufs[L.z],
+                              bufs[L.out], L.c, L.gamma);
+                if (r2) return r2;
+            }
+            return TBPM_OK;
+        };
+        CUDA_OR_FAIL(c, launch_set_states(c->d_psi_user, c->n_orb, c->n_states, c->H.user_to_row,
+                                          g.s0, B, 0, g.psi0, c->st));
+        const size_t gvec = (size_t)c->H.n_rows * B * sizeof(double2);
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(ckpt[0], g.psi0, gvec, cudaMemcpyDeviceToDevice, c->st));
+        // forward pass: checkpoints phi_{jK}
+        void *src = ckpt[0];
+        for (int n = 0; n + 1 < n_steps; ++n) {
+            void *dst = g.buf[n % 2];
+            if ((rc = step_into(src, dst, g.buf[2]))) { release(); return rc; }
+            src = dst;
+            if ((n + 1) % K == 0)
+                CUDA_OR_FAIL(c, cudaMemcpyAsync(ckpt[(n + 1) / K], dst, gvec,
+                                                cudaMemcpyDeviceToDevice, c->st));
+        }
+        // backward pass
+        int lc = 0;
+        CUDA_OR_FAIL(c, launch_source_init(c->H.n_rows, B, c->H.chunk_sample, d_gbar, c->n_states,
+                                           g.s0, n_steps, n_steps, g.psi0, g.buf[0], c->st));
+        for (int seg = nseg - 1; seg >= 0; --seg) {
+            const int n0 = seg * K, n1 = std::min(n_steps, n0 + K);
+            std::vector<void *> tp(n1 - n0);
+            tp[0] = ckpt[seg];
+            for (int k = 1; k < n1 - n0; ++k) {
+                tp[k] = traj[k];
+                if ((rc = step_into(tp[k - 1], tp[k], stash[0]))) { release(); return rc; }
+            }
+            for (int n = n1 - 1; n >= n0; --n) {
+                void *phi = tp[n - n0];
+                if (M - 2 >= 1 && (rc = term(phi, phi, nullptr, stash[1], 0.0, 1.0))) {
+                    release(); return rc;
+                }
+                for (int m = 2; m <= M - 2; ++m)
+                    if ((rc = term(stash[m - 1], stash[m - 1], m == 2 ? phi : stash[m - 2],
+                                   stash[m], 0.0, 2.0))) {
+                        release(); return rc;
+                    }
+                int nx = 0;
+                std::vector<Launch> sch = schedule(a, lc, &nx);
+                for (size_t k = 0; k < sch.size(); ++k) {
+                    const Launch &L = sch[k];
+                    const int m = M - 2 - (int)k;
+                    AdjArgs aa;
+                    memset(&aa, 0, sizeof(aa));
+                    aa.H = Hv;
+                    aa.x = L.x < 0 ? g.buf[lc] : g.buf[L.x];
+                    aa.psi = g.buf[lc];
+                    aa.z = L.z < 0 ? nullptr : g.buf[L.z];
+                    aa.out = g.buf[L.out];
+                    aa.T_own = m == 0 ? phi : stash[m];
+                    aa.c = L.c;
+                    aa.gamma = -L.gamma;
+                    aa.gfac = L.gamma;
+                    aa.G = G;
+                    aa.Gdiag = Gd;
+                    aa.gbar = m == 0 ? d_gbar : nullptr;
+                    aa.psi0 = g.psi0;
+                    aa.n_states = c->n_states;
+                    aa.state0 = g.s0;
+                    aa.n_steps = n_steps;
+                    aa.step = n;
+                    aa.chunk_sample = c->H.chunk_sample;
+                    aa.n_rows = c->H.n_rows;
+                    ++launches;
+                    cudaError_t e = launch_adj_term(aa, B, threads, c->st);
+                    if (e != cudaSuccess) {
+                        release();
+                        return fail(c, TBPM_E_CUDA, std::string("adjoint kernel: ") + cudaGetErrorString(e));
+                    }
+                }
+                lc = nx;
+            }
+        }
+    }
+    cudaError_t e = launch_param_grads(c->H.n_hop, c->H.bond_rows, c->H.slice_ptr, c->H.col, G, Gd,
+                                       c->n_orb, c->H.user_to_row, 1.0 / c->s, d_gh, d_go, c->st);
+    if (e == cudaSuccess && where_out == TBPM_HOST) {
+        if (c->H.n_hop > 0)
+            e = cudaMemcpyAsync(grad_hop, d_gh, c->H.n_hop * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(grad_onsite, d_go, c->n_orb * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    release();
+    if (e != cudaSuccess)
+        return fail(c, TBPM_E_CUDA, std::string("adjoint: ") + cudaGetErrorString(e));
+    c->stats.kernel_launches = launches;
+    c->stats.n_terms = M;
+    c->stats.n_steps = n_steps;
+    c->err.clear();
+    return leave(c);
+}

@@ -45,6 +45,7 @@ class Propagator:
                                  hop_j, hop_v, float(s), n_samples, sample_offsets,
                                  N.where_of(hop_i), flags)
         self.n_samples = n_samples
+        self.n_hop = int(hop_i.shape[0])
         self.n_orb = int(n_orb)
         self.s = float(s)
         return self
@@ -90,6 +91,24 @@ class Propagator:
         N.tbpm_get_norms(self.ctx, out)
         return out
 
+    # a8
+    def adjoint(self, z, n_steps, gbar, K=64, n_hop=None):
+        """(dL/dt_b, dL/deps_i) for gbar [n_samples, n_states, n_steps + 1]
+        = dL/dRe C + i dL/dIm C (numpy or CUDA tensor)."""
+        if n_hop is None:
+            n_hop = self.n_hop
+        if N.where_of(gbar) == N.TBPM_DEVICE:
+            import torch
+            gh = torch.empty(n_hop, dtype=torch.float64, device=gbar.device)
+            go = torch.empty(self.n_orb, dtype=torch.float64, device=gbar.device)
+        else:
+            gbar = np.ascontiguousarray(gbar, dtype=np.complex128)
+            gh = np.empty(n_hop)
+            go = np.empty(self.n_orb)
+        N.tbpm_propagate_adjoint(self.ctx, float(z), int(n_steps), gbar, N.where_of(gbar),
+                                 int(K), gh, go)
+        return gh, go
+
     def stats(self) -> dict:
         return N.tbpm_get_stats(self.ctx)
 
@@ -101,6 +120,14 @@ def dos(corr_avg, tau, e_min, e_max, n_e, window=N.TBPM_WINDOW_HANN):
     d = np.empty(n_e)
     N.tbpm_dos(c, c.shape[0] - 1, tau, window, e_min, e_max, n_e, en, d)
     return en, d
+
+
+def dos_adjoint(dl_dd, n_steps, tau, e_min, e_max, window=N.TBPM_WINDOW_HANN):
+    """gbar_n [n_steps + 1] of the averaged correlation from dL/dD (host FP64)."""
+    d = np.ascontiguousarray(dl_dd, dtype=np.float64)
+    out = np.empty(n_steps + 1, dtype=np.complex128)
+    N.tbpm_dos_adjoint(d, d.shape[0], n_steps, tau, window, e_min, e_max, out)
+    return out
 
 
 def _c64(a):

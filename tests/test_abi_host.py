@@ -92,3 +92,14 @@ def test_dos_transform_vs_oracle(native):
     assert np.max(np.abs(d - d2)) < 1e-12
     with pytest.raises(native.TbpmError):
         dos(c, tau, 1.0, -1.0, 10)
+
+
+def test_dos_adjoint_vs_oracle(native):
+    import oracle
+    from paper_2209_00806_gb300 import dos_adjoint
+    gen = np.random.default_rng(3)
+    dl = gen.normal(size=513)
+    for n in (10, 200, 1024):
+        g = dos_adjoint(dl, n, 0.165, -9.5, 9.5)
+        ref = oracle.dos_adjoint(dl, n, 0.165, -9.5, 9.5)
+        assert np.max(np.abs(g - ref)) < 1e-11 * max(1.0, np.max(np.abs(ref)))
