@@ -56,6 +56,9 @@ struct tbpm_ctx {
     std::vector<Group> groups;
     double *d_partial = nullptr;
     int64_t partial_len = 0;
+    double *d_block_partial = nullptr;
+    int64_t block_partial_len = 0;
+    int *d_chunk_count = nullptr;
     int *d_step = nullptr;       // [n_samples]
     int *d_flags = nullptr;      // [0] error bits
     unsigned long long *d_renorm = nullptr;
@@ -132,7 +135,12 @@ void free_hamiltonian(tbpm_ctx *c)
     cudaFree(c->d_inv_sqrt_n);
     cudaFree(c->d_psi_user);
     cudaFree(c->d_partial);
+    cudaFree(c->d_block_partial);
+    cudaFree(c->d_chunk_count);
     cudaFree(c->d_step);
+    c->d_block_partial = nullptr;
+    c->d_chunk_count = nullptr;
+    c->block_partial_len = 0;
     c->d_sample_chunk_off = nullptr;
     c->d_inv_sqrt_n = nullptr;
     c->d_psi_user = nullptr;
@@ -536,6 +544,24 @@ static int ensure_groups(tbpm_ctx *c, int prec)
         if (rc) { free_groups(c); return rc; }
         c->partial_len = need;
     }
+    // block partials of the closing term: one per block of the launch shape
+    int64_t need_b = 0;
+    for (auto &g : c->groups) {
+        const int L = prec == TBPM_FP64 ? g.B : std::max(1, g.B / 2);
+        need_b = std::max<int64_t>(need_b, c->H.n_rows * L / c->threads[prec] * g.B * 3);
+    }
+    if (need_b > c->block_partial_len) {
+        cudaFree(c->d_block_partial);
+        c->d_block_partial = nullptr;
+        int rc = dalloc(c, &c->d_block_partial, need_b);
+        if (rc) { free_groups(c); return rc; }
+        c->block_partial_len = need_b;
+    }
+    if (!c->d_chunk_count) {
+        int rc = dalloc(c, &c->d_chunk_count, c->H.n_rows / kChunkRows);
+        if (rc) { free_groups(c); return rc; }
+        cudaMemsetAsync(c->d_chunk_count, 0, c->H.n_rows / kChunkRows * sizeof(int), c->st);
+    }
     c->prec = prec;
     return TBPM_OK;
 }
@@ -708,6 +734,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         base.n_rows = c->H.n_rows;
         base.psi0 = g.psi0;
         base.partial = c->d_partial;
+        base.block_partial = c->d_block_partial;
+        base.chunk_count = c->d_chunk_count;
         ReduceArgs ra;
         ra.partial = c->d_partial;
         ra.sample_chunk_off = c->d_sample_chunk_off;

@@ -159,41 +159,39 @@ __global__ void __launch_bounds__(1024) k_term(TermArgs a)
     st<V, L, SPL>(a.out, r, l, o);
 }
 
-// Closing term over one chunk of kChunkRows rows per block, with the FP64
-// partial sums of <psi0|out> and <out|out> per state.  Deterministic: fixed
-// thread-to-row mapping, shuffle tree, then a fixed-order sum over warps.
+// Closing term, one row per thread like k_term, with the FP64 sums of
+// <psi0|out> and <out|out> per state: shuffle tree over the rows of a warp,
+// fixed-order sum over the warps into a per-block partial, then the last
+// block of each kChunkRows chunk (atomic ticket after a fence) adds the
+// chunk's block partials in block order.  Every sum has a fixed order, so the
+// result does not depend on which block finishes last.
 template <typename V, int L, int SPL, bool COMPUTE>
 __global__ void __launch_bounds__(1024) k_final(TermArgs a)
 {
     constexpr int B = L * SPL;
     __shared__ double red[32][B][3];
-    const int64_t chunk = blockIdx.x;
-    const int rows_per_pass = blockDim.x / L;
-    const int l = threadIdx.x % L;
+    __shared__ int last;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = t / L;
+    const int l = (int)(t % L);
     const double *sc = nullptr;
-    if (a.scale) sc = a.scale + (int64_t)a.chunk_sample[chunk] * B;
+    if (a.scale) sc = a.scale + (int64_t)a.chunk_sample[r / kChunkRows] * B;
+    Cv<V, SPL> o;
+    if (COMPUTE) {
+        o = term_row<V, L, SPL>(a, r, l, sc);
+        st<V, L, SPL>(a.out, r, l, o);
+    } else {
+        o = ld<V, L, SPL>(a.out, r, l);
+    }
+    const Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
     double dre[SPL], dim[SPL], nrm[SPL];
 #pragma unroll
-    for (int j = 0; j < SPL; ++j) { dre[j] = 0; dim[j] = 0; nrm[j] = 0; }
-    for (int64_t r = chunk * kChunkRows + threadIdx.x / L; r < (chunk + 1) * kChunkRows;
-         r += rows_per_pass) {
-        Cv<V, SPL> o;
-        if (COMPUTE) {
-            o = term_row<V, L, SPL>(a, r, l, sc);
-            st<V, L, SPL>(a.out, r, l, o);
-        } else {
-            o = ld<V, L, SPL>(a.out, r, l);
-        }
-        Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-            const double orr = o.re[j], oi = o.im[j], pr = p0.re[j], pi = p0.im[j];
-            dre[j] = fma(pr, orr, fma(pi, oi, dre[j]));
-            dim[j] = fma(pr, oi, fma(-pi, orr, dim[j]));
-            nrm[j] = fma(orr, orr, fma(oi, oi, nrm[j]));
-        }
+    for (int j = 0; j < SPL; ++j) {
+        const double orr = o.re[j], oi = o.im[j], pr = p0.re[j], pi = p0.im[j];
+        dre[j] = fma(pr, orr, pi * oi);
+        dim[j] = fma(pr, oi, -pi * orr);
+        nrm[j] = fma(orr, orr, oi * oi);
     }
-    // sum over the rows held by one warp (lanes with equal l)
 #pragma unroll
     for (int off = L; off < 32; off <<= 1) {
 #pragma unroll
@@ -214,20 +212,40 @@ __global__ void __launch_bounds__(1024) k_final(TermArgs a)
     }
     __syncthreads();
     const int nw = blockDim.x / 32;
+    const int per_chunk = kChunkRows * L / blockDim.x;    // blocks per chunk
+    const int64_t chunk = blockIdx.x / per_chunk;
     if (threadIdx.x < B * 3) {
         const int b = threadIdx.x / 3, q = threadIdx.x % 3;
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += red[w][b][q];
-        a.partial[chunk * (B * 3) + threadIdx.x] = s;
+        a.block_partial[(int64_t)blockIdx.x * (B * 3) + threadIdx.x] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int ticket = atomicAdd(a.chunk_count + chunk, 1);
+        last = (ticket == per_chunk - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x < B * 3) {
+            double s = 0.0;
+            const int64_t b0 = chunk * per_chunk;
+            for (int k = 0; k < per_chunk; ++k)
+                s += __ldcg(a.block_partial + (b0 + k) * (B * 3) + threadIdx.x);
+            a.partial[chunk * (B * 3) + threadIdx.x] = s;
+        }
+        if (threadIdx.x == 0) a.chunk_count[chunk] = 0;     // ready for the next launch
     }
 }
 
 // One block per sample: fixed-order sum of the chunk partials, then the
 // correlation entry, the squared norm, the drift checks and (FP32) the
 // scale of the next step's starting state.
-__global__ void __launch_bounds__(256) k_reduce(ReduceArgs a)
+__global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a)
 {
-    __shared__ double part[256];
+    __shared__ double part[1024];
     const int s = blockIdx.x;
     const int B3 = a.B * 3;
     const int G = blockDim.x / B3;
@@ -236,6 +254,7 @@ __global__ void __launch_bounds__(256) k_reduce(ReduceArgs a)
     if (t < G * B3) {
         const int g = t / B3, comp = t % B3;
         double acc = 0.0;
+#pragma unroll 8
         for (int64_t c = c0 + g; c < c1; c += G) acc += a.partial[c * B3 + comp];
         part[t] = acc;
     }
@@ -345,7 +364,7 @@ cudaError_t launch_term_t(const TermArgs &a, int threads, cudaStream_t st)
 template <typename V, int L, int SPL>
 cudaError_t launch_final_t(const TermArgs &a, int threads, bool compute, cudaStream_t st)
 {
-    const unsigned blocks = (unsigned)(a.n_rows / kChunkRows);
+    const unsigned blocks = (unsigned)(a.n_rows * L / threads);
     if (compute)
         k_final<V, L, SPL, true><<<blocks, threads, 0, st>>>(a);
     else
@@ -394,7 +413,7 @@ cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaSt
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st)
 {
-    k_reduce<<<a.n_samples, 256, 0, st>>>(a);
+    k_reduce<<<a.n_samples, 1024, 0, st>>>(a);
     return cudaGetLastError();
 }
 

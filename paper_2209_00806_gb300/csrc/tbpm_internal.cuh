@@ -47,7 +47,9 @@ struct TermArgs {
     int64_t n_rows;
     // closing term only (H.col == nullptr: reduce `out` without computing it)
     const void *psi0;
-    double *partial;      // [n_chunks][B][3]
+    double *partial;        // [n_chunks][B][3]
+    double *block_partial;  // [n_blocks][B][3]
+    int *chunk_count;       // [n_chunks], zero between launches
 };
 
 struct ReduceArgs {
