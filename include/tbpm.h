@@ -228,6 +228,30 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
  * library's autotuner or by hand.  Drops the current propagation buffers. */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads);
 
+/* Allocation-free form of the correlation reduction, for callers that
+ * cannot allocate device memory (a host framework whose pool owns the whole
+ * device, a plugin that may only allocate at start-up, a latency-bound loop
+ * that cannot afford cudaMalloc/cudaFree).  The paper has no counterpart:
+ * this is an integration convenience of the library.
+ *   psi0, phi  device complex128 [n_states][n_orb], caller order (as
+ *              tbpm_get_states returns); caller-owned, read only
+ *   corr_out   device complex128 [n_states]: <psi0_s|phi_s>
+ *   norm_out   device double [n_states]: <phi_s|phi_s>
+ *   cuda_stream the stream to run on (cudaStream_t, may be NULL)
+ * Same FP64 sums as the closing reduction of tbpm_propagate.  Allocates
+ * nothing: its scratch is one fixed device array of 786,496 bytes
+ * (n_states <= 16), held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Calls share the array, so calls that overlap
+ * on the GPU race: serialise them.  Asynchronous on cuda_stream; the
+ * message of a failure is read with tbpm_last_error(NULL).
+ * Errors: INVALID_ARG (NULL pointer, n_orb < 1, n_states outside 1..16),
+ * CUDA. */
+int tbpm_correlation_noalloc(const double *psi0, const double *phi, int64_t n_orb,
+                             int n_states, double *corr_out, double *norm_out,
+                             void *cuda_stream);
+
 /* Statistics of the last call on ctx. */
 int tbpm_get_stats(tbpm_ctx *ctx, tbpm_stats *out);
 

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("tbpm_propagate_adjoint", _I32, [P, _F64, _I32, P, _I32, _I32, P, P, _I32]),
     ("tbpm_dos_adjoint", _I32, [P, _I32, _I32, _F64, _I32, _F64, _F64, P]),
     ("tbpm_set_launch_config", _I32, [P, _I32, _I32, _I32]),
+    ("tbpm_correlation_noalloc", _I32, [P, P, _I64, _I32, P, P, P]),
     ("tbpm_get_stats", _I32, [P, ctypes.POINTER(tbpm_stats)]),
 ]
 
@@ -226,6 +227,11 @@ def tbpm_propagate_adjoint(ctx, z, n_steps, gbar, where, K, grad_hop, grad_onsit
 def tbpm_dos_adjoint(dl_dd, n_e, n_steps, tau, window, e_min, e_max, gbar_out):
     return check(None, lib.tbpm_dos_adjoint(ptr(dl_dd), n_e, n_steps, tau, window, e_min,
                                             e_max, ptr(gbar_out)))
+
+
+def tbpm_correlation_noalloc(psi0, phi, n_orb, n_states, corr_out, norm_out, stream=None):
+    return check(None, lib.tbpm_correlation_noalloc(ptr(psi0), ptr(phi), n_orb, n_states,
+                                                    ptr(corr_out), ptr(norm_out), stream))
 
 
 def tbpm_set_launch_config(ctx, precision, max_group, threads):

@@ -230,6 +230,8 @@ void rcm_sample(int64_t lo, int64_t hi, const std::vector<int64_t> &adj_ptr,
 
 }  // namespace
 
+void tbpm::set_thread_error(const std::string &m) { g_last_error = m; }
+
 // ---------------------------------------------------------------------------
 
 extern "C" int tbpm_version(void) { return 10000; }

@@ -148,6 +148,9 @@ int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
                cudaStream_t st, std::string &msg);
 void free_build(BuildOutput &b);
 
+// Thread-local message returned by tbpm_last_error(NULL) (api.cu).
+void set_thread_error(const std::string &m);
+
 // Host math (host_math.cpp).
 int bessel_miller(double z, double tol, int max_terms, double *J, int *n_terms);
 int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_min,
