@@ -224,9 +224,25 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
 /* Launch shape of the propagation kernels for one precision: states are
  * split into groups of power-of-two width <= max_group (FP64 <= 8,
  * FP32 <= 16), each group propagated as one blocked sparse product per term;
- * threads per block is a power of two in 64..1024.  Chosen by the
- * library's autotuner or by hand.  Drops the current propagation buffers. */
-int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads);
+ * threads per block is a power of two in 64..1024; variant is a set of
+ * TBPM_VARIANT_* bits.  Chosen by tbpm_autotune or by hand.  Changing the
+ * width or block size drops the current propagation buffers. */
+#define TBPM_VARIANT_ZIGZAG 1        /* alternate the row traversal direction per term,
+                                        so each term starts on rows still in L2 */
+#define TBPM_VARIANT_STREAM_HINTS 2  /* evict-first loads of the own-row streams */
+int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
+                           int variant);
+
+/* Autotuner: for the current Hamiltonian and states, time probe_steps
+ * (1..64) steps of each candidate launch shape -- state-group width (the
+ * block width of the blocked sparse product), threads per block (128, 256,
+ * 512) and TBPM_VARIANT_* bits -- and keep the fastest as the context's
+ * configuration for `precision`.  The chosen values are written to the
+ * non-NULL out pointers.  The slice height is fixed at 32 rows (one warp's
+ * rows share a slice).  Leaves no propagation to resume.
+ * Errors: STATE, INVALID_ARG, OOM, CUDA. */
+int tbpm_autotune(tbpm_ctx *ctx, int precision, double z, int probe_steps, int *best_group,
+                  int *best_threads, int *best_variant, double *best_ms_per_step);
 
 /* Allocation-free form of the correlation reduction, for callers that
  * cannot allocate device memory (a host framework whose pool owns the whole

@@ -42,6 +42,8 @@ TBPM_PROP_PROFILE = 1
 TBPM_PROP_GRAPH = 2
 TBPM_PROP_RESUME = 4
 TBPM_PROP_PERSISTENT = 8
+TBPM_VARIANT_ZIGZAG = 1
+TBPM_VARIANT_STREAM_HINTS = 2
 
 
 class TbpmError(RuntimeError):
@@ -89,8 +91,10 @@ SIGNATURES = [
     ("tbpm_dos", _I32, [P, _I32, _F64, _I32, _F64, _F64, _I32, P, P]),
     ("tbpm_propagate_adjoint", _I32, [P, _F64, _I32, P, _I32, _I32, P, P, _I32]),
     ("tbpm_dos_adjoint", _I32, [P, _I32, _I32, _F64, _I32, _F64, _F64, P]),
-    ("tbpm_set_launch_config", _I32, [P, _I32, _I32, _I32]),
+    ("tbpm_set_launch_config", _I32, [P, _I32, _I32, _I32, _I32]),
     ("tbpm_correlation_noalloc", _I32, [P, P, _I64, _I32, P, P, P]),
+    ("tbpm_autotune", _I32, [P, _I32, _F64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                             ctypes.POINTER(_I32), ctypes.POINTER(_F64)]),
     ("tbpm_get_stats", _I32, [P, ctypes.POINTER(tbpm_stats)]),
 ]
 
@@ -229,13 +233,20 @@ def tbpm_dos_adjoint(dl_dd, n_e, n_steps, tau, window, e_min, e_max, gbar_out):
                                             e_max, ptr(gbar_out)))
 
 
+def tbpm_autotune(ctx, precision, z, probe_steps=4):
+    g, t, v, ms = _I32(), _I32(), _I32(), _F64()
+    check(ctx, lib.tbpm_autotune(ctx, precision, z, probe_steps, ctypes.byref(g),
+                                 ctypes.byref(t), ctypes.byref(v), ctypes.byref(ms)))
+    return dict(group=g.value, threads=t.value, variant=v.value, ms_per_step=ms.value)
+
+
 def tbpm_correlation_noalloc(psi0, phi, n_orb, n_states, corr_out, norm_out, stream=None):
     return check(None, lib.tbpm_correlation_noalloc(ptr(psi0), ptr(phi), n_orb, n_states,
                                                     ptr(corr_out), ptr(norm_out), stream))
 
 
-def tbpm_set_launch_config(ctx, precision, max_group, threads):
-    return check(ctx, lib.tbpm_set_launch_config(ctx, precision, max_group, threads))
+def tbpm_set_launch_config(ctx, precision, max_group, threads, variant=1):
+    return check(ctx, lib.tbpm_set_launch_config(ctx, precision, max_group, threads, variant))
 
 
 def tbpm_get_stats(ctx) -> dict:

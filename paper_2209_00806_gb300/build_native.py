@@ -1,6 +1,7 @@
 """Build the CUDA library libtbpm.so in-tree for sm_103a (nvcc + g++).
 
-Run as ``python -m paper_2209_00806_gb300.build_native`` or through
+Run as ``python paper_2209_00806_gb300/build_native.py`` (by path: importing the
+package needs the library this script builds) or through
 ``__graft_entry__.build()``.  Output: ``paper_2209_00806_gb300/_build/libtbpm.so``.
 """
 from __future__ import annotations

@@ -23,6 +23,7 @@ struct Group {
     void *psi0 = nullptr;        // internal layout, precision of the group
     void *buf[3] = {nullptr, nullptr, nullptr};
     double *scale = nullptr;     // [n_samples * B]
+    float *scale_f = nullptr;    // FP32 copy
     int cur = 0;                 // buffer holding the current state
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
 };
@@ -53,6 +54,7 @@ struct tbpm_ctx {
     int prec = -1;               // precision of the group buffers
     int max_group[2] = {8, 16};  // widest state group per precision
     int threads[2] = {256, 256}; // threads per block per precision
+    int variant[2] = {kVariantZigZag, kVariantZigZag};  // term-kernel launch variants
     std::vector<Group> groups;
     double *d_partial = nullptr;
     int64_t partial_len = 0;
@@ -111,6 +113,7 @@ void free_groups(tbpm_ctx *c)
             if (g.graph[k]) cudaGraphExecDestroy(g.graph[k]);
         }
         cudaFree(g.scale);
+        cudaFree(g.scale_f);
     }
     c->groups.clear();
     c->prec = -1;
@@ -489,7 +492,8 @@ extern "C" int tbpm_set_phase_states(tbpm_ctx *c, int n_states, const double *th
     return set_states_common(c, n_states, theta, where, true);
 }
 
-extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group, int threads)
+extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group, int threads,
+                                      int variant)
 {
     if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
     if (precision != TBPM_FP64 && precision != TBPM_FP32)
@@ -499,9 +503,12 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
         return fail(c, TBPM_E_INVALID_ARG, "group width must be a power of two within the cap");
     if (threads < 64 || threads > 1024 || (threads & (threads - 1)))
         return fail(c, TBPM_E_INVALID_ARG, "threads must be a power of two in 64..1024");
+    if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints))
+        return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
     if (c->max_group[precision] != max_group || c->threads[precision] != threads) free_groups(c);
     c->max_group[precision] = max_group;
     c->threads[precision] = threads;
+    c->variant[precision] = variant;
     return TBPM_OK;
 }
 
@@ -532,6 +539,7 @@ static int ensure_groups(tbpm_ctx *c, int prec)
         int rc = dalloc(c, (char **)&g.psi0, bytes);
         for (int k = 0; k < 3 && !rc; ++k) rc = dalloc(c, (char **)&g.buf[k], bytes);
         if (!rc && prec == TBPM_FP32) rc = dalloc(c, &g.scale, (size_t)c->n_samples * g.B);
+        if (!rc && prec == TBPM_FP32) rc = dalloc(c, &g.scale_f, (size_t)c->n_samples * g.B);
         if (rc) { free_groups(c); return rc; }
         for (int k = 0; k < 3; ++k) cudaMemsetAsync(g.buf[k], 0, bytes, c->st);
         cudaMemsetAsync(g.psi0, 0, bytes, c->st);
@@ -724,8 +732,12 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             if (g.graph[k]) { cudaGraphExecDestroy(g.graph[k]); g.graph[k] = nullptr; }
         if (g.scale) {
             std::vector<double> ones((size_t)c->n_samples * g.B, 1.0);
+            std::vector<float> ones_f((size_t)c->n_samples * g.B, 1.0f);
             CUDA_OR_FAIL(c, cudaMemcpyAsync(g.scale, ones.data(), ones.size() * sizeof(double),
                                             cudaMemcpyHostToDevice, c->st));
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(g.scale_f, ones_f.data(), ones_f.size() * sizeof(float),
+                                            cudaMemcpyHostToDevice, c->st));
+            CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));   // host vectors go out of scope
         }
         CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_step, 0, c->n_samples * sizeof(int), c->st));
 
@@ -761,10 +773,12 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             t0.out = g.buf[g.cur];
             CUDA_OR_FAIL(c, launch_final(t0, fp32, g.B, threads, c->st));
             ra.scale = nullptr;
+            ra.scale_f = nullptr;
             CUDA_OR_FAIL(c, launch_reduce(ra, c->st));
             launches += 2;
         }
         ra.scale = g.scale;
+        ra.scale_f = g.scale_f;
 
         auto run_step = [&](int cur, int *next_cur, bool timed) -> int {
             std::vector<Launch> sch = schedule(a, cur, next_cur);
@@ -787,6 +801,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                     ended_interior = true;
                 }
                 TermArgs t = base;
+                t.variant = c->variant[precision];
+                t.reverse = (t.variant & kVariantZigZag) ? (int)(k & 1) : 0;
                 t.x = L.x < 0 ? g.buf[cur] : g.buf[L.x];
                 t.x_is_psi = L.x < 0;
                 t.psi = g.buf[cur];
@@ -794,7 +810,11 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 t.out = g.buf[L.out];
                 split_coeff(L.c, fp32, &t.c_hi, &t.c_lo);
                 t.gamma = L.gamma;
+                t.c_hi_f = (float)t.c_hi;
+                t.c_lo_f = (float)t.c_lo;
+                t.gamma_f = (float)t.gamma;
                 t.scale = g.scale;
+                t.scale_f = g.scale_f;
                 cudaError_t e = L.final_term ? launch_final(t, fp32, g.B, threads, c->st)
                                              : launch_term(t, fp32, g.B, threads, c->st);
                 if (e != cudaSuccess)
@@ -1194,4 +1214,49 @@ extern "C" int tbpm_propagate_adjoint(tbpm_ctx *c, double z, int n_steps, const 
     c->stats.n_steps = n_steps;
     c->err.clear();
     return leave(c);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times a few steps of the current Hamiltonian and states for each
+// candidate (state-group width, threads per block, launch variant) and keeps
+// the fastest.  The states are restored: the next propagate starts from psi0.
+extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_steps,
+                             int *best_group, int *best_threads, int *best_variant,
+                             double *best_ms_per_step)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->have_h || c->n_states < 1)
+        return fail(c, TBPM_E_STATE, "build the Hamiltonian and set states first");
+    if (precision != TBPM_FP64 && precision != TBPM_FP32)
+        return fail(c, TBPM_E_INVALID_ARG, "bad precision");
+    if (probe_steps < 1 || probe_steps > 64)
+        return fail(c, TBPM_E_INVALID_ARG, "probe_steps must be 1..64");
+    const int cap = precision == TBPM_FP64 ? 8 : 16;
+    std::vector<int> widths;
+    for (int B = cap; B >= 1; B /= 2)
+        if (B <= c->n_states && (B >= 2 || c->n_states == 1)) widths.push_back(B);
+    if (widths.empty()) widths.push_back(1);
+    const int thread_opts[] = {128, 256, 512};
+    const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints};
+    double best = 1e300;
+    int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
+    for (int B : widths)
+        for (int T : thread_opts)
+            for (int V : variant_opts) {
+                int rc = tbpm_set_launch_config(c, precision, B, T, V);
+                if (rc) return rc;
+                rc = tbpm_propagate(c, z, probe_steps, precision, nullptr, TBPM_HOST,
+                                    TBPM_PROP_PROFILE);
+                if (rc) return rc;
+                const double ms = c->stats.ms_total / probe_steps;
+                if (ms < best) { best = ms; bg = B; bt = T; bv = V; }
+            }
+    int rc = tbpm_set_launch_config(c, precision, bg, bt, bv);
+    if (rc) return rc;
+    if (best_group) *best_group = bg;
+    if (best_threads) *best_threads = bt;
+    if (best_variant) *best_variant = bv;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    c->have_run = false;
+    return TBPM_OK;
 }

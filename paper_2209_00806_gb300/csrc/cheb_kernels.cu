@@ -66,6 +66,16 @@ __device__ __forceinline__ Cv<V, SPL> ld(const void *base, int64_t r, int l)
     unpack(reinterpret_cast<const Lane *>(base)[r * L + l], o);
     return o;
 }
+// Own-row stream read with an evict-first hint (kept out of the way of the
+// gathered vector in L2).
+template <typename V, int L, int SPL>
+__device__ __forceinline__ Cv<V, SPL> ld_cs(const void *base, int64_t r, int l)
+{
+    typedef typename LaneT<V, SPL>::type Lane;
+    Cv<V, SPL> o;
+    unpack(__ldcs(reinterpret_cast<const Lane *>(base) + r * L + l), o);
+    return o;
+}
 template <typename V, int L, int SPL>
 __device__ __forceinline__ void st(void *base, int64_t r, int l, const Cv<V, SPL> &v)
 {
@@ -73,11 +83,43 @@ __device__ __forceinline__ void st(void *base, int64_t r, int l, const Cv<V, SPL
     reinterpret_cast<Lane *>(base)[r * L + l] = pack(v);
 }
 
-// out = c psi + gamma (-i) (H~ x) + z for lane l of row r.
+// out = c psi + gamma (-i) (H~ x) + z for lane l of row r.  The own-row
+// streams (psi, z) are issued first so that they are in flight while the
+// dependent slice -> column -> gather chain resolves; padded slots of the
+// slice cost a load of the own row (always in bounds) but no arithmetic.
+// Coefficients in the kernel's own precision, read from the launch
+// arguments without any FP64 -> FP32 conversion on the device (GB300 runs
+// conversions involving FP64 at the FP64 rate).
+template <typename V> struct Coef;
+template <> struct Coef<double> {
+    __device__ static double g(const TermArgs &a) { return a.gamma; }
+    __device__ static double hi(const TermArgs &a) { return a.c_hi; }
+    __device__ static double lo(const TermArgs &a) { return a.c_lo; }
+    __device__ static const double *scale(const TermArgs &a) { return a.scale; }
+};
+template <> struct Coef<float> {
+    __device__ static float g(const TermArgs &a) { return a.gamma_f; }
+    __device__ static float hi(const TermArgs &a) { return a.c_hi_f; }
+    __device__ static float lo(const TermArgs &a) { return a.c_lo_f; }
+    __device__ static const float *scale(const TermArgs &a) { return a.scale_f; }
+};
+
 template <typename V, int L, int SPL>
 __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int l,
-                                               const double *sc)
+                                               const V *sc)
 {
+    Cv<V, SPL> p, zz;
+    if (a.variant & kVariantStreamHints) {
+        p = ld_cs<V, L, SPL>(a.psi, r, l);
+        if (a.z) zz = ld_cs<V, L, SPL>(a.z, r, l);
+    } else {
+        p = ld_ro<V, L, SPL>(a.psi, r, l);
+        if (a.z) zz = ld<V, L, SPL>(a.z, r, l);
+    }
+    if (!a.z) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
+    }
     const int64_t q = r / kSliceRows;
     const int lr = (int)(r % kSliceRows);
     const int64_t base = __ldg(a.H.slice_ptr + q);
@@ -105,31 +147,25 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
         for (int u = 0; u < 4; ++u) xv[u] = ld_ro<V, L, SPL>(a.x, c[u], l);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+            if (k + u < w) {
 #pragma unroll
-            for (int j = 0; j < SPL; ++j) {
-                y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
-                y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                for (int j = 0; j < SPL; ++j) {
+                    y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
+                    y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                }
             }
         }
     }
-    Cv<V, SPL> p = ld_ro<V, L, SPL>(a.psi, r, l);
     if (sc) {               // FP32 norm carry: psi -> psi * scale (per state)
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
-            const V s = (V)sc[l * SPL + j];
+            const V s = sc[l * SPL + j];
             p.re[j] *= s;
             p.im[j] *= s;
             if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
         }
     }
-    Cv<V, SPL> zz;
-    if (a.z) {
-        zz = ld<V, L, SPL>(a.z, r, l);
-    } else {
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
-    }
-    const V g = (V)a.gamma, ch = (V)a.c_hi, cl = (V)a.c_lo;
+    const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
     Cv<V, SPL> o;
 #pragma unroll
     for (int j = 0; j < SPL; ++j) {
@@ -146,15 +182,23 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
     return o;
 }
 
+// Block index in traversal order: with kVariantZigZag the term kernels walk
+// the rows from the end on odd launches, so they start on the rows the
+// previous launch wrote last (still in L2).
+__device__ __forceinline__ int64_t block_in_order(const TermArgs &a)
+{
+    return a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
+}
+
 template <typename V, int L, int SPL>
 __global__ void __launch_bounds__(1024) k_term(TermArgs a)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = block_in_order(a) * blockDim.x + threadIdx.x;
     const int64_t r = t / L;
     const int l = (int)(t % L);
     if (r >= a.n_rows) return;
-    const double *sc = nullptr;
-    if (a.scale) sc = a.scale + (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
+    const V *sc = Coef<V>::scale(a);
+    if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
     Cv<V, SPL> o = term_row<V, L, SPL>(a, r, l, sc);
     st<V, L, SPL>(a.out, r, l, o);
 }
@@ -171,11 +215,12 @@ __global__ void __launch_bounds__(1024) k_final(TermArgs a)
     constexpr int B = L * SPL;
     __shared__ double red[32][B][3];
     __shared__ int last;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t bid = block_in_order(a);
+    const int64_t t = bid * blockDim.x + threadIdx.x;
     const int64_t r = t / L;
     const int l = (int)(t % L);
-    const double *sc = nullptr;
-    if (a.scale) sc = a.scale + (int64_t)a.chunk_sample[r / kChunkRows] * B;
+    const V *sc = Coef<V>::scale(a);
+    if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * B;
     Cv<V, SPL> o;
     if (COMPUTE) {
         o = term_row<V, L, SPL>(a, r, l, sc);
@@ -213,12 +258,12 @@ __global__ void __launch_bounds__(1024) k_final(TermArgs a)
     __syncthreads();
     const int nw = blockDim.x / 32;
     const int per_chunk = kChunkRows * L / blockDim.x;    // blocks per chunk
-    const int64_t chunk = blockIdx.x / per_chunk;
+    const int64_t chunk = bid / per_chunk;
     if (threadIdx.x < B * 3) {
         const int b = threadIdx.x / 3, q = threadIdx.x % 3;
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += red[w][b][q];
-        a.block_partial[(int64_t)blockIdx.x * (B * 3) + threadIdx.x] = s;
+        a.block_partial[bid * (B * 3) + threadIdx.x] = s;
         __threadfence();
     }
     __syncthreads();
@@ -284,6 +329,7 @@ __global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a)
                 atomicAdd(a.renorm_count, 1ull);
             }
             a.scale[(int64_t)s * a.B + t] = sc;
+            if (a.scale_f) a.scale_f[(int64_t)s * a.B + t] = (float)sc;
         }
     }
     __syncthreads();

@@ -22,6 +22,10 @@ constexpr int kMaxStates = 64;
 constexpr int kMaxTerms = 128;
 constexpr int kMaxGroups = 8;
 
+// Launch variants of the term kernels (bits of TermArgs::variant).
+constexpr int kVariantZigZag = 1;       // alternate the traversal direction per launch
+constexpr int kVariantStreamHints = 2;  // evict-first loads of the own-row streams
+
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.
 struct SellView {
@@ -41,10 +45,14 @@ struct TermArgs {
     void *out;            // may alias z
     double c_hi, c_lo;    // coefficient of psi as an unevaluated sum (FP32)
     double gamma;
+    float c_hi_f, c_lo_f, gamma_f;  // the same in FP32 (no conversions on the device)
     int x_is_psi;         // apply the state scale to x as well
     const double *scale;  // [n_samples * B] or nullptr
+    const float *scale_f; // FP32 copy of scale (read by the FP32 kernels)
     const int32_t *chunk_sample;  // [n_rows / kChunkRows]
     int64_t n_rows;
+    int variant;          // kVariant* bits
+    int reverse;          // walk the blocks from the end (zig-zag order)
     // closing term only (H.col == nullptr: reduce `out` without computing it)
     const void *psi0;
     double *partial;        // [n_chunks][B][3]
@@ -64,6 +72,7 @@ struct ReduceArgs {
     double2 *corr;                   // [n_samples][n_states][n_steps + 1]
     double *norms;                   // [n_samples][n_states][n_steps + 1]
     double *scale;                   // [n_samples * B] next-step scale (FP32) or nullptr
+    float *scale_f;                  // its FP32 copy
     double renorm_bound;             // |<phi|phi> - 1| above which to renormalise
     double hard_bound;               // above which to flag NORM_DRIFT
     unsigned long long *renorm_count;

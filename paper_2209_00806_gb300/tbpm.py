@@ -64,9 +64,13 @@ class Propagator:
         N.tbpm_set_states(self.ctx, self.n_states, psi0)
         return self
 
-    def launch_config(self, precision, max_group, threads):
-        N.tbpm_set_launch_config(self.ctx, precision, max_group, threads)
+    def launch_config(self, precision, max_group, threads, variant=N.TBPM_VARIANT_ZIGZAG):
+        N.tbpm_set_launch_config(self.ctx, precision, max_group, threads, variant)
         return self
+
+    def autotune(self, z, precision=N.TBPM_FP64, probe_steps=4) -> dict:
+        """Pick the fastest launch shape for this Hamiltonian and these states."""
+        return N.tbpm_autotune(self.ctx, precision, float(z), probe_steps)
 
     # a2-a6
     def propagate(self, z, n_steps, precision=N.TBPM_FP64, out=None, flags=0):

@@ -52,7 +52,7 @@ def test_gpu_fp64_disordered_vacancies_several_groups(tb):
     assert np.max(np.abs(nrm[0] - onrm)) < 1e-10
 
 
-@pytest.mark.parametrize("cfg", [(1, 64), (2, 128), (8, 1024)])
+@pytest.mark.parametrize("cfg", [(1, 64, 0), (2, 128, 1), (8, 1024, 3), (4, 256, 2)])
 def test_gpu_fp64_ragged_rows_launch_shapes(tb, cfg):
     smp = lattice.random_graph(3001, 9000, seed=3, onsite_w=2.0)   # degrees 0 .. ~15
     H = exact.dense_h(smp)
@@ -90,6 +90,31 @@ def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
         ref = run_oracle(p, 9.5, th_parts[k], 120)
         assert np.max(np.abs(c64[k] - ref)) < 1e-10
         assert np.max(np.abs(c32[k] - ref)) < 2e-5
+
+
+@pytest.mark.parametrize("cfg", [(16, 128, 3), (4, 512, 1), (2, 64, 0)])
+def test_gpu_fp32_launch_shapes(tb, cfg):
+    smp = lattice.random_graph(2500, 7000, seed=9, onsite_w=2.0)
+    H = exact.dense_h(smp)
+    s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(H)))
+    th = rng.phases(8, 16, smp.n_orb)
+    c, st, _, _ = run_gpu(tb, smp, s, th, 40, precision=1, cfg=cfg)
+    ref = run_oracle(smp, s, th, 40)
+    assert np.max(np.abs(c[0] - ref)) < 2e-5
+
+
+def test_gpu_autotune_picks_a_valid_shape(tb):
+    smp = lattice.graphene(40, 40, pbc=True, seed=4, onsite_w=1.0, vacancy_frac=0.01)
+    th = rng.phases(3, 4, smp.n_orb)
+    with tb.Propagator() as p:
+        p.build_sample(smp, 9.5)
+        p.set_phase_states(th)
+        best = p.autotune(Z, precision=1, probe_steps=2)
+        assert best["group"] in (2, 4) and best["threads"] in (128, 256, 512)
+        assert best["variant"] in (0, 1, 3) and best["ms_per_step"] > 0
+        c = p.propagate(Z, 30, 1)
+    ref = run_oracle(smp, 9.5, th, 30)
+    assert np.max(np.abs(c[0] - ref)) < 2e-5
 
 
 def test_gpu_fp32_dos_l1(tb):
