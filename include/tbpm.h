@@ -41,7 +41,7 @@ extern "C" {
 #define TBPM_E_CUDA 4           /* a CUDA call failed; the message names it */
 #define TBPM_E_NORM_DRIFT 5     /* |<phi|phi> - 1| exceeded the hard bound */
 #define TBPM_E_NONFINITE 6      /* NaN or Inf met in a state or a reduction */
-#define TBPM_E_TIMEOUT 7        /* a bounded device-side wait gave up */
+#define TBPM_E_TIMEOUT 7        /* a bounded device-side wait gave up (TMA kernel) */
 #define TBPM_E_STATE 8          /* call order: e.g. propagate before build */
 #define TBPM_E_UNSUPPORTED 9    /* valid request this build does not provide */
 
@@ -230,6 +230,9 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
 #define TBPM_VARIANT_ZIGZAG 1        /* alternate the row traversal direction per term,
                                         so each term starts on rows still in L2 */
 #define TBPM_VARIANT_STREAM_HINTS 2  /* evict-first loads of the own-row streams */
+#define TBPM_VARIANT_TMA 4           /* persistent term kernel: each tile's row streams
+                                        and matrix slices staged in shared memory by
+                                        bulk asynchronous copies, 3 stages ahead */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
 

@@ -44,6 +44,7 @@ TBPM_PROP_RESUME = 4
 TBPM_PROP_PERSISTENT = 8
 TBPM_VARIANT_ZIGZAG = 1
 TBPM_VARIANT_STREAM_HINTS = 2
+TBPM_VARIANT_TMA = 4
 
 
 class TbpmError(RuntimeError):

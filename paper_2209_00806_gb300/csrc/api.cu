@@ -55,6 +55,7 @@ struct tbpm_ctx {
     int max_group[2] = {8, 16};  // widest state group per precision
     int threads[2] = {256, 256}; // threads per block per precision
     int variant[2] = {kVariantZigZag, kVariantZigZag};  // term-kernel launch variants
+    int num_sms = 0;
     std::vector<Group> groups;
     double *d_partial = nullptr;
     int64_t partial_len = 0;
@@ -259,6 +260,7 @@ extern "C" int tbpm_create(tbpm_ctx **out, int device, void *stream)
     c->user = (cudaStream_t)stream;
     memset(&c->stats, 0, sizeof(c->stats));
     e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_renorm, sizeof(unsigned long long));
@@ -503,7 +505,7 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
         return fail(c, TBPM_E_INVALID_ARG, "group width must be a power of two within the cap");
     if (threads < 64 || threads > 1024 || (threads & (threads - 1)))
         return fail(c, TBPM_E_INVALID_ARG, "threads must be a power of two in 64..1024");
-    if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints))
+    if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
     if (c->max_group[precision] != max_group || c->threads[precision] != threads) free_groups(c);
     c->max_group[precision] = max_group;
@@ -619,7 +621,7 @@ std::vector<Launch> schedule(const std::vector<double> &a, int cur, int *next_cu
             L.out = zz.buf;
         else
             L.out = (scratch[0] != x.buf) ? scratch[0] : scratch[1];
-        L.interior = (x.buf >= 0 && zz.buf >= 0);
+        L.interior = !L.final_term && x.buf >= 0 && zz.buf >= 0;
         out.push_back(L);
         b[m] = Slot{L.out, 0.0};
     }
@@ -815,8 +817,13 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 t.gamma_f = (float)t.gamma;
                 t.scale = g.scale;
                 t.scale_f = g.scale_f;
-                cudaError_t e = L.final_term ? launch_final(t, fp32, g.B, threads, c->st)
-                                             : launch_term(t, fp32, g.B, threads, c->st);
+                cudaError_t e;
+                if (L.final_term)
+                    e = launch_final(t, fp32, g.B, threads, c->st);
+                else if (t.variant & kVariantTma)
+                    e = launch_term_tma(t, fp32, g.B, c->H.max_width, c->d_flags, c->num_sms, c->st);
+                else
+                    e = launch_term(t, fp32, g.B, threads, c->st);
                 if (e != cudaSuccess)
                     return fail(c, TBPM_E_CUDA, std::string("term kernel: ") + cudaGetErrorString(e));
             }
@@ -924,6 +931,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
     }
     rc = leave(c);
     if (rc) return rc;
+    if (h_flags[0] & 4)
+        return fail(c, TBPM_E_TIMEOUT, "a bounded wait in the TMA term kernel expired");
     if (h_flags[0] & 2) return fail(c, TBPM_E_NONFINITE, "non-finite value in a state or correlation");
     if (h_flags[0] & 1) {
         char buf[200];
@@ -1237,7 +1246,8 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
         if (B <= c->n_states && (B >= 2 || c->n_states == 1)) widths.push_back(B);
     if (widths.empty()) widths.push_back(1);
     const int thread_opts[] = {128, 256, 512};
-    const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints};
+    const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints,
+                                kVariantTma, kVariantTma | kVariantZigZag};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
     for (int B : widths)

@@ -25,6 +25,7 @@ constexpr int kMaxGroups = 8;
 // Launch variants of the term kernels (bits of TermArgs::variant).
 constexpr int kVariantZigZag = 1;       // alternate the traversal direction per launch
 constexpr int kVariantStreamHints = 2;  // evict-first loads of the own-row streams
+constexpr int kVariantTma = 4;          // persistent TMA-staged term kernel
 
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.
@@ -109,6 +110,11 @@ cudaError_t launch_set_states(const double2 *psi_user, int64_t n_orb, int n_stat
 cudaError_t launch_get_states(const void *psi, int64_t n_orb, int n_states,
                               const int32_t *user_to_row, int group_state0, int B,
                               int fp32, double2 *out_user, cudaStream_t st);
+
+// Persistent TMA-staged term kernel (tma_kernels.cu); err bit 4 = bounded
+// wait expired.
+cudaError_t launch_term_tma(const TermArgs &a, int fp32, int B, int max_width, int *err,
+                            int num_sms, cudaStream_t st);
 
 // Adjoint kernels (adjoint_kernels.cu).
 cudaError_t launch_adj_term(const AdjArgs &a, int B, int threads, cudaStream_t st);

@@ -52,7 +52,8 @@ def test_gpu_fp64_disordered_vacancies_several_groups(tb):
     assert np.max(np.abs(nrm[0] - onrm)) < 1e-10
 
 
-@pytest.mark.parametrize("cfg", [(1, 64, 0), (2, 128, 1), (8, 1024, 3), (4, 256, 2)])
+@pytest.mark.parametrize("cfg", [(1, 64, 0), (2, 128, 1), (8, 1024, 3), (4, 256, 2), (4, 256, 4),
+                                 (8, 256, 5), (1, 256, 4)])
 def test_gpu_fp64_ragged_rows_launch_shapes(tb, cfg):
     smp = lattice.random_graph(3001, 9000, seed=3, onsite_w=2.0)   # degrees 0 .. ~15
     H = exact.dense_h(smp)
@@ -92,7 +93,8 @@ def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
         assert np.max(np.abs(c32[k] - ref)) < 2e-5
 
 
-@pytest.mark.parametrize("cfg", [(16, 128, 3), (4, 512, 1), (2, 64, 0)])
+@pytest.mark.parametrize("cfg", [(16, 128, 3), (4, 512, 1), (2, 64, 0), (16, 256, 4), (4, 256, 5),
+                                 (1, 256, 4)])
 def test_gpu_fp32_launch_shapes(tb, cfg):
     smp = lattice.random_graph(2500, 7000, seed=9, onsite_w=2.0)
     H = exact.dense_h(smp)
@@ -169,6 +171,20 @@ def test_gpu_graph_mode_and_determinism(tb):
         pr, stp, _, _ = run_gpu(tb, smp, 9.5, th, 50, precision=prec, flags=1)
         assert np.array_equal(a, b) and np.array_equal(a, g) and np.array_equal(a, pr)
         assert stp["ms_term_avg"] > 0 and stp["term_launches"] == 50 * 12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gpu_tma_kernel_is_bit_identical(tb, prec):
+    """The TMA-staged term kernel does the same arithmetic in the same order."""
+    smp = lattice.graphene(33, 31, pbc=True, seed=6, onsite_w=1.0, vacancy_frac=0.02)
+    th = rng.phases(12, 4, smp.n_orb)
+    outs = []
+    for variant in (0, 4, 5):
+        c, _, phi, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, cfg=(4, 256, variant),
+                               flags=2 if variant == 5 else 0)
+        outs.append((c, phi))
+    for c, phi in outs[1:]:
+        assert np.array_equal(c, outs[0][0]) and np.array_equal(phi, outs[0][1])
 
 
 def test_gpu_resume_continues_the_propagation(tb):
