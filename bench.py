@@ -39,7 +39,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--L", type=int, default=2048, help="lattice side (default: the full workload)")
+    ap.add_argument("--workload", default="disordered",
+                    choices=["disordered", "batched", "graphene_dos"],
+                    help="disordered: 2048^2 disordered graphene, 4 states, 1024 steps "
+                         "(default, the headline); batched: 32 uneven samples x 16 states, "
+                         "512 steps; graphene_dos: 64x64 pristine graphene, 1 state, 1024 steps")
+    ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -60,23 +65,43 @@ def n_cores():
         return os.cpu_count() or 1
 
 
-def workload_inputs(L, n_steps, rank):
+def workload_inputs(args, rank):
     from tbpm_inputs import rng, workloads
-    w = workloads.disordered_graphene(L=L, n_steps=n_steps)
-    # weak scaling: rank r propagates its own states (seed offset by the rank)
-    seed = w.sample_seeds[0] + 7919 * rank
-    theta = rng.phases(seed, w.n_states, w.sample.n_orb)
+    if args.workload == "batched":
+        w = workloads.batched_graphene()
+    elif args.workload == "graphene_dos":
+        w = workloads.graphene_dos(n_steps=args.time_steps)
+    else:
+        w = workloads.disordered_graphene(L=args.L, n_steps=args.time_steps)
+    # weak scaling: rank r propagates its own states (seeds offset by the rank)
+    parts = []
+    for k in range(w.n_samples):
+        n_k = int(w.offsets[k + 1] - w.offsets[k])
+        parts.append(rng.phases(w.sample_seeds[k] + 7919 * rank, w.n_states, n_k))
+    theta = np.ascontiguousarray(np.concatenate(parts, axis=1))
     return w, theta
 
 
 def config_dict(w, args, world):
-    return {"workload": f"disordered_graphene_{args.L}x{args.L}",
-            "n_orb": int(w.sample.n_orb), "n_bonds": int(w.sample.n_hop),
-            "states_per_gpu": w.n_states, "time_steps": w.n_steps, "z": "pi/2",
-            "s_eV": w.s, "chebyshev_products_per_step": None, "dos_bins": w.n_energies,
-            "onsite_disorder_eV": "U[-0.5,0.5]", "vacancies": "1%",
-            "l2": "inputs larger than L2 (state vectors 266 MB FP32 / 531 MB FP64)",
-            "parallelism": f"replicas x{world} (states sharded, no collective)"}
+    cs32 = 8 * w.n_states * w.sample.n_orb / 1e6
+    d = {"n_orb": int(w.sample.n_orb), "n_bonds": int(w.sample.n_hop),
+         "n_samples": w.n_samples, "states_per_sample": w.n_states, "time_steps": w.n_steps,
+         "z": "pi/2", "s_eV": w.s, "chebyshev_products_per_step": None,
+         "dos_bins": w.n_energies,
+         "parallelism": f"replicas x{world} (states sharded, no collective)"}
+    if args.workload == "batched":
+        d.update(workload="batched_graphene_32_samples", side_lengths=w.info["Ls"],
+                 onsite_disorder_eV="U[-W/2,W/2], W ~ U[0,2] per sample",
+                 l2=f"inputs larger than L2 (state vectors {cs32:.0f} MB FP32)")
+    elif args.workload == "graphene_dos":
+        d.update(workload="graphene_dos_64x64", onsite_disorder_eV="none",
+                 l2="working set inside L2 (latency-bound; no L2 flush)")
+    else:
+        d.update(workload=f"disordered_graphene_{args.L}x{args.L}",
+                 onsite_disorder_eV="U[-0.5,0.5]", vacancies="1%",
+                 l2=f"inputs larger than L2 (state vectors {cs32:.0f} MB FP32 / "
+                    f"{2 * cs32:.0f} MB FP64)")
+    return d
 
 
 # ---------------------------------------------------------------- clocks --
@@ -163,7 +188,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    w, theta = workload_inputs(args.L, args.time_steps, 0)
+    w, theta = workload_inputs(args, 0)
     M = 16
     per_step_budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     vals = []
@@ -205,6 +230,18 @@ def kernel_traffic():
     return d, d
 
 
+def sample_part(w, k):
+    """Sample k of a (possibly batched) workload as its own bond list."""
+    from tbpm_inputs import lattice
+    smp = w.sample
+    lo, hi = int(w.offsets[k]), int(w.offsets[k + 1])
+    if w.n_samples == 1:
+        return smp
+    m = (smp.hop_i >= lo) & (smp.hop_i < hi)
+    ons = None if smp.onsite is None else smp.onsite[lo:hi]
+    return lattice.Sample(hi - lo, ons, smp.hop_i[m] - lo, smp.hop_j[m] - lo, smp.hop_v[m])
+
+
 def run_gb300(args):
     import torch
     import torch.distributed as dist
@@ -217,51 +254,65 @@ def run_gb300(args):
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    w, theta = workload_inputs(args.L, args.time_steps, rank)
+    w, theta = workload_inputs(args, rank)
     smp = w.sample
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    d_on = torch.as_tensor(smp.onsite, device=dev)
+    onsite = smp.onsite if smp.onsite is not None else np.zeros(smp.n_orb)
+    d_on = torch.as_tensor(onsite, device=dev)
     d_hi = torch.as_tensor(smp.hop_i, device=dev)
     d_hj = torch.as_tensor(smp.hop_j, device=dev)
     d_hv = torch.as_tensor(smp.hop_v, device=dev)
     d_th = torch.as_tensor(theta, device=dev)
-    S, NT = w.n_states, w.n_steps
+    S, NT, NS = w.n_states, w.n_steps, w.n_samples
+    offsets = None if NS == 1 else w.offsets
     M = len(tb.tbpm_bessel_coefficients(w.z))
     units_per_step = smp.n_orb * S * NT * (M - 1)
     prop = tb.Propagator(local, stream.cuda_stream)
-    corr_d = torch.empty((1, S, NT + 1), dtype=torch.complex128, device=dev)
+    corr_d = torch.empty((NS, S, NT + 1), dtype=torch.complex128, device=dev)
+    # precisions measured per workload: the first one is the headline `value`
+    legs = {"disordered": [N.TBPM_FP32, N.TBPM_FP64], "batched": [N.TBPM_FP32],
+            "graphene_dos": [N.TBPM_FP64]}[args.workload]
+    graph = args.workload == "graphene_dos"     # launch-latency bound: replay step graphs
 
     def one_step(precision, flags):
-        prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s)
+        prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets)
         prop.set_phase_states(d_th)
         prop.propagate(w.z, NT, precision, out=corr_d, flags=flags)
-        c = corr_d.mean(dim=1)[0].cpu().numpy()
-        return tb.dos(c, w.tau, *w.e_range, w.n_energies)
+        c = corr_d.mean(dim=1).cpu().numpy()          # state average per sample
+        out = [tb.dos(c[k], w.tau, *w.e_range, w.n_energies) for k in range(NS)]
+        return out[0][0], np.stack([d for _, d in out])
 
     def barrier():
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
 
-    def timed(precision, flags):
+    # autotune the launch shape once per precision (outside the timed region)
+    tuned = {}
+    prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets)
+    prop.set_phase_states(d_th)
+    for prec in legs:
+        tuned[prec] = prop.autotune(w.z, precision=prec, probe_steps=3)
+
+    def timed(precision):
+        flags = N.TBPM_PROP_GRAPH if graph else N.TBPM_PROP_PROFILE
         for _ in range(args.warmup):
             one_step(precision, flags)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        st_acc = {"ms_term": 0.0, "n_term": 0, "ms_total": 0.0, "launches": 0, "renorm": 0,
-                  "drift": 0.0}
+        acc = {"ms_term": 0.0, "n_term": 0, "launches": 0, "renorm": 0, "drift": 0.0}
         with ClockSampler(local) as clk:
             e0.record(stream)
             for _ in range(args.steps):
                 res = one_step(precision, flags)
                 st = prop.stats()
-                st_acc["ms_term"] += st["ms_term_avg"] * st["term_launches"]
-                st_acc["n_term"] += st["term_launches"]
-                st_acc["launches"] += st["kernel_launches"] + 12   # + builder kernels
-                st_acc["renorm"] += st["renormalisations"]
-                st_acc["drift"] = max(st_acc["drift"], st["max_norm_drift"])
+                acc["ms_term"] += st["ms_term_avg"] * st["term_launches"]
+                acc["n_term"] += st["term_launches"]
+                acc["launches"] += st["kernel_launches"] + 13   # + builder kernels
+                acc["renorm"] += st["renormalisations"]
+                acc["drift"] = max(acc["drift"], st["max_norm_drift"])
             e1.record(stream)
             barrier()
         ms = e0.elapsed_time(e1)
@@ -269,14 +320,11 @@ def run_gb300(args):
             t = torch.tensor([ms], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        st = prop.stats()
-        ms_term = st_acc["ms_term"] / max(1, st_acc["n_term"])
-        return dict(ms=ms, res=res, stats=st, ms_term=ms_term, clocks=clk.summary(),
-                    launches=st_acc["launches"], renorm=st_acc["renorm"], drift=st_acc["drift"])
+        ms_term = acc["ms_term"] / acc["n_term"] if acc["n_term"] else None
+        return dict(ms=ms, res=res, stats=prop.stats(), ms_term=ms_term, clocks=clk.summary(),
+                    launches=acc["launches"], renorm=acc["renorm"], drift=acc["drift"])
 
-    PROFILE = N.TBPM_PROP_PROFILE
-    r32 = timed(N.TBPM_FP32, PROFILE)
-    r64 = timed(N.TBPM_FP64, PROFILE)
+    runs = {prec: timed(prec) for prec in legs}
 
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
         if (ROOT / "MEASURED_PEAKS.json").exists() else {}
@@ -285,42 +333,45 @@ def run_gb300(args):
     hbm = hbm or 6800.0
 
     def roofline(r, key):
+        if r["ms_term"] is None:
+            return None
         b = r["stats"]["bytes_term"]
         ach = b / (r["ms_term"] * 1e-3) / 1e9
-        tr, meta = kernel_traffic()
+        tr, _ = kernel_traffic()
         traffic = None
-        if tr is not None and key in tr:
+        if tr is not None and key in tr and args.workload == "disordered" and args.L == 2048:
             traffic = tr[key]["dram_bytes_per_launch_full_size"]
         return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": traffic, "peak_source": peak_note,
-                "kernel": "interior Clenshaw term (k_term)", "algorithmic_bytes_per_launch": b,
+                "kernel": "interior Clenshaw term", "algorithmic_bytes_per_launch": b,
                 "ms_per_launch": r["ms_term"]}
 
     total_units = units_per_step * args.steps * world
-    v32 = total_units / (r32["ms"] * 1e-3)
-    v64 = total_units / (r64["ms"] * 1e-3)
-    en, d32 = r32["res"]
-    _, d64 = r64["res"]
-    l1 = float(np.sum(np.abs(d32 - d64)) * (en[1] - en[0]))
+    vals = {prec: total_units / (r["ms"] * 1e-3) for prec, r in runs.items()}
+    head = legs[0]
+    r0 = runs[head]
+    name = {N.TBPM_FP32: "fp32", N.TBPM_FP64: "fp64"}
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
     if not args.no_e2e:
-        h_on = torch.from_numpy(np.ascontiguousarray(smp.onsite)).pin_memory()
+        h_on = torch.from_numpy(np.ascontiguousarray(onsite)).pin_memory()
         h_hi = torch.from_numpy(np.ascontiguousarray(smp.hop_i)).pin_memory()
         h_hj = torch.from_numpy(np.ascontiguousarray(smp.hop_j)).pin_memory()
         h_hv = torch.from_numpy(np.ascontiguousarray(smp.hop_v)).pin_memory()
         h_th = torch.from_numpy(np.ascontiguousarray(theta)).pin_memory()
-        h_c = torch.empty((1, S, NT + 1), dtype=torch.complex128).pin_memory()
+        h_c = torch.empty((NS, S, NT + 1), dtype=torch.complex128).pin_memory()
+        offs = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.int64)
 
         def host_step():
             N.tbpm_build_hamiltonian(prop.ctx, smp.n_orb, h_on.data_ptr(), smp.n_hop,
-                                     h_hi.data_ptr(), h_hj.data_ptr(), h_hv.data_ptr(), w.s, 1,
-                                     None, N.TBPM_HOST, 0)
+                                     h_hi.data_ptr(), h_hj.data_ptr(), h_hv.data_ptr(), w.s, NS,
+                                     offs, N.TBPM_HOST, 0)
             N.tbpm_set_phase_states(prop.ctx, S, h_th.data_ptr(), N.TBPM_HOST)
-            N.tbpm_propagate(prop.ctx, w.z, NT, N.TBPM_FP32, h_c.data_ptr(), N.TBPM_HOST, 0)
-            c = h_c.numpy().mean(axis=1)[0]
-            return tb.dos(c, w.tau, *w.e_range, w.n_energies)
+            N.tbpm_propagate(prop.ctx, w.z, NT, head, h_c.data_ptr(), N.TBPM_HOST,
+                             N.TBPM_PROP_GRAPH if graph else 0)
+            c = h_c.numpy().mean(axis=1)
+            return [tb.dos(c[k], w.tau, *w.e_range, w.n_energies) for k in range(NS)]
 
         for _ in range(args.warmup):
             host_step()
@@ -335,35 +386,48 @@ def run_gb300(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         h2d = sum(x.numel() * x.element_size() for x in (h_on, h_hi, h_hj, h_hv, h_th))
-        d2h = h_c.numel() * h_c.element_size() + S * (NT + 1) * 8   # correlations + norms
+        d2h = h_c.numel() * h_c.element_size() + NS * S * (NT + 1) * 8   # C + norms
         e2e = {"value": total_units / dt, "unit": "orbital-Chebyshev-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": 1e3 * dt / args.steps, "precision": "fp32"}
+               "ms_per_step": 1e3 * dt / args.steps, "precision": name[head]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = oracle_sample(w, theta, 15.0)
+        part = sample_part(w, 0)
+        from tbpm_inputs import workloads as _wl
+        wp = _wl.Workload(w.name, part, np.array([0, part.n_orb]), w.s, w.z, S, NT,
+                          w.n_energies, w.e_range, w.seed, [w.sample_seeds[0]])
+        cpu, _ = oracle_sample(wp, theta[:, :part.n_orb], 15.0)
 
     if rank == 0:
         cfg = config_dict(w, args, world)
         cfg["chebyshev_products_per_step"] = M - 1
-        cfg["state_groups"] = r32["stats"]["group_width"]
+        cfg["state_groups"] = r0["stats"]["group_width"]
+        cfg["launch"] = {name[p]: tuned[p] for p in legs}
         line = {
-            "metric": "orbital-Chebyshev-steps/s", "value": v32,
+            "metric": "orbital-Chebyshev-steps/s", "value": vals[head],
             "unit": "orbital-Chebyshev-steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps,
+            "warmup": args.warmup, "ms_per_step": r0["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "reductions": "f64", "data": "synthetic", "config": cfg,
-            "roofline": roofline(r32, "fp32"),
-            "fp64_form": {"value": v64, "ms_per_step": r64["ms"] / args.steps, "dtype": "f64",
-                          "roofline": roofline(r64, "fp64"), "clocks": r64["clocks"],
-                          "max_norm_drift": r64["drift"]},
-            "speedup_fp32_over_fp64": v32 / v64,
-            "dos_l1_fp32_vs_fp64": l1,
-            "fp32_renormalisations": r32["renorm"], "fp32_max_norm_drift": r32["drift"],
-            "e2e": e2e, "gpu_launches": int(r32["launches"]),
-            "clocks": r32["clocks"], "cpu_baseline": cpu,
+            "dtype": "f32" if head == N.TBPM_FP32 else "f64", "reductions": "f64",
+            "data": "synthetic", "config": cfg,
+            "roofline": roofline(r0, name[head]),
+            "e2e": e2e, "gpu_launches": int(r0["launches"]),
+            "clocks": r0["clocks"], "cpu_baseline": cpu,
         }
+        if head == N.TBPM_FP32:
+            line["fp32_renormalisations"] = r0["renorm"]
+            line["fp32_max_norm_drift"] = r0["drift"]
+        if N.TBPM_FP64 in runs and head != N.TBPM_FP64:
+            r64 = runs[N.TBPM_FP64]
+            en, d32 = r0["res"]
+            _, d64 = r64["res"]
+            line["fp64_form"] = {"value": vals[N.TBPM_FP64], "ms_per_step": r64["ms"] / args.steps,
+                                 "dtype": "f64", "roofline": roofline(r64, "fp64"),
+                                 "clocks": r64["clocks"], "max_norm_drift": r64["drift"]}
+            line["speedup_fp32_over_fp64"] = vals[head] / vals[N.TBPM_FP64]
+            line["dos_l1_fp32_vs_fp64"] = float(np.max(np.sum(np.abs(d32 - d64), axis=1)) *
+                                                (en[1] - en[0]))
         print(json.dumps(line), flush=True)
     prop.close()
     if world > 1:

@@ -62,6 +62,8 @@ struct tbpm_ctx {
     double *d_block_partial = nullptr;
     int64_t block_partial_len = 0;
     int *d_chunk_count = nullptr;
+    double *d_partial2 = nullptr;          // [n_samples][64][16][3]
+    unsigned int *d_sample_ticket = nullptr;
     int *d_step = nullptr;       // [n_samples]
     int *d_flags = nullptr;      // [0] error bits
     unsigned long long *d_renorm = nullptr;
@@ -141,6 +143,10 @@ void free_hamiltonian(tbpm_ctx *c)
     cudaFree(c->d_partial);
     cudaFree(c->d_block_partial);
     cudaFree(c->d_chunk_count);
+    cudaFree(c->d_partial2);
+    cudaFree(c->d_sample_ticket);
+    c->d_partial2 = nullptr;
+    c->d_sample_ticket = nullptr;
     cudaFree(c->d_step);
     c->d_block_partial = nullptr;
     c->d_chunk_count = nullptr;
@@ -560,7 +566,7 @@ static int ensure_groups(tbpm_ctx *c, int prec)
     int64_t need_b = 0;
     for (auto &g : c->groups) {
         const int L = prec == TBPM_FP64 ? g.B : std::max(1, g.B / 2);
-        need_b = std::max<int64_t>(need_b, c->H.n_rows * L / c->threads[prec] * g.B * 3);
+        need_b = std::max<int64_t>(need_b, c->H.n_rows * L / 512 * g.B * 3);   // closing-term blocks of 512
     }
     if (need_b > c->block_partial_len) {
         cudaFree(c->d_block_partial);
@@ -573,6 +579,12 @@ static int ensure_groups(tbpm_ctx *c, int prec)
         int rc = dalloc(c, &c->d_chunk_count, c->H.n_rows / kChunkRows);
         if (rc) { free_groups(c); return rc; }
         cudaMemsetAsync(c->d_chunk_count, 0, c->H.n_rows / kChunkRows * sizeof(int), c->st);
+    }
+    if (!c->d_partial2) {
+        int rc = dalloc(c, &c->d_partial2, (size_t)c->n_samples * 64 * 16 * 3);
+        if (!rc) rc = dalloc(c, &c->d_sample_ticket, (size_t)c->n_samples);
+        if (rc) { free_groups(c); return rc; }
+        cudaMemsetAsync(c->d_sample_ticket, 0, c->n_samples * sizeof(unsigned int), c->st);
     }
     c->prec = prec;
     return TBPM_OK;
@@ -754,6 +766,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         base.chunk_count = c->d_chunk_count;
         ReduceArgs ra;
         ra.partial = c->d_partial;
+        ra.partial2 = c->d_partial2;
+        ra.sample_ticket = c->d_sample_ticket;
         ra.sample_chunk_off = c->d_sample_chunk_off;
         ra.n_samples = c->n_samples;
         ra.B = g.B;

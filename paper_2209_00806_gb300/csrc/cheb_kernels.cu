@@ -203,20 +203,33 @@ __global__ void __launch_bounds__(1024) k_term(TermArgs a)
     st<V, L, SPL>(a.out, r, l, o);
 }
 
-// Closing term, one row per thread like k_term, with the FP64 sums of
-// <psi0|out> and <out|out> per state: shuffle tree over the rows of a warp,
-// fixed-order sum over the warps into a per-block partial, then the last
-// block of each kChunkRows chunk (atomic ticket after a fence) adds the
+// Closing term, one row per thread like k_term, with the sums of
+// <psi0|out> and <out|out> per state into one partial per block, then the
+// last block of each kChunkRows chunk (atomic ticket after a fence) adds the
 // chunk's block partials in block order.  Every sum has a fixed order, so the
 // result does not depend on which block finishes last.
+//
+// GB300 runs FP64 at 1/58 of the FP32 rate, so the reduction is shaped to
+// spend few FP64 operations: in the FP32 form the per-row products and the
+// sum over the rows of a warp are formed in FP32 (each warp partial covers
+// at most 32 rows; its rounding is far below that of the FP32 states
+// themselves) and everything from the warp partials up is FP64; in the FP64
+// form every product and sum is FP64, but rows are summed in a shared-memory
+// tree (one add per value) instead of a butterfly (one add per value and
+// level on every lane).
+constexpr int kFinalThreads = 512;
+
 template <typename V, int L, int SPL, bool COMPUTE>
-__global__ void __launch_bounds__(1024) k_final(TermArgs a)
+__global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
 {
     constexpr int B = L * SPL;
-    __shared__ double red[32][B][3];
+    constexpr int ROWS = kFinalThreads / L;          // rows per block
+    constexpr int NW = kFinalThreads / 32;
+    __shared__ double red[sizeof(V) == 8 ? ROWS * B * 3 : NW * B * 3];
+    __shared__ double grp[8][B * 3];
     __shared__ int last;
     const int64_t bid = block_in_order(a);
-    const int64_t t = bid * blockDim.x + threadIdx.x;
+    const int64_t t = bid * kFinalThreads + threadIdx.x;
     const int64_t r = t / L;
     const int l = (int)(t % L);
     const V *sc = Coef<V>::scale(a);
@@ -229,41 +242,69 @@ __global__ void __launch_bounds__(1024) k_final(TermArgs a)
         o = ld<V, L, SPL>(a.out, r, l);
     }
     const Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
-    double dre[SPL], dim[SPL], nrm[SPL];
+    V pre[SPL], pim[SPL], pnr[SPL];
 #pragma unroll
     for (int j = 0; j < SPL; ++j) {
-        const double orr = o.re[j], oi = o.im[j], pr = p0.re[j], pi = p0.im[j];
-        dre[j] = fma(pr, orr, pi * oi);
-        dim[j] = fma(pr, oi, -pi * orr);
-        nrm[j] = fma(orr, orr, oi * oi);
+        pre[j] = fma(p0.re[j], o.re[j], p0.im[j] * o.im[j]);
+        pim[j] = fma(p0.re[j], o.im[j], -(p0.im[j] * o.re[j]));
+        pnr[j] = fma(o.re[j], o.re[j], o.im[j] * o.im[j]);
     }
+    const int lrow = threadIdx.x / L;
+    if (sizeof(V) == 4) {
+        // FP32: butterfly over the rows of the warp, then FP64 per warp
 #pragma unroll
-    for (int off = L; off < 32; off <<= 1) {
+        for (int off = L; off < 32; off <<= 1) {
 #pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-            dre[j] += __shfl_xor_sync(0xffffffffu, dre[j], off);
-            dim[j] += __shfl_xor_sync(0xffffffffu, dim[j], off);
-            nrm[j] += __shfl_xor_sync(0xffffffffu, nrm[j], off);
+            for (int j = 0; j < SPL; ++j) {
+                pre[j] += __shfl_xor_sync(0xffffffffu, pre[j], off);
+                pim[j] += __shfl_xor_sync(0xffffffffu, pim[j], off);
+                pnr[j] += __shfl_xor_sync(0xffffffffu, pnr[j], off);
+            }
         }
-    }
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (lane < L) {
+        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+        if (lane < L) {
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                const int b = lane * SPL + j;
+                red[(warp * B + b) * 3 + 0] = (double)pre[j];
+                red[(warp * B + b) * 3 + 1] = (double)pim[j];
+                red[(warp * B + b) * 3 + 2] = (double)pnr[j];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < B * 3) {
+            double s = 0.0;
+            for (int w = 0; w < NW; ++w) s += red[w * B * 3 + threadIdx.x];
+            grp[0][threadIdx.x] = s;
+        }
+    } else {
+        // FP64: shared-memory tree, 8 groups of rows then the groups
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
-            red[warp][lane * SPL + j][0] = dre[j];
-            red[warp][lane * SPL + j][1] = dim[j];
-            red[warp][lane * SPL + j][2] = nrm[j];
+            const int b = l * SPL + j;
+            red[(lrow * B + b) * 3 + 0] = (double)pre[j];
+            red[(lrow * B + b) * 3 + 1] = (double)pim[j];
+            red[(lrow * B + b) * 3 + 2] = (double)pnr[j];
+        }
+        __syncthreads();
+        if (threadIdx.x < 8 * B * 3) {
+            const int gidx = threadIdx.x / (B * 3), v = threadIdx.x % (B * 3);
+            double s = 0.0;
+            for (int row = gidx; row < ROWS; row += 8) s += red[row * B * 3 + v];
+            grp[gidx][v] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x < B * 3) {
+            double s = 0.0;
+            for (int g2 = 0; g2 < 8; ++g2) s += grp[g2][threadIdx.x];
+            grp[0][threadIdx.x] = s;
         }
     }
     __syncthreads();
-    const int nw = blockDim.x / 32;
-    const int per_chunk = kChunkRows * L / blockDim.x;    // blocks per chunk
+    constexpr int per_chunk = kChunkRows / ROWS;     // blocks per chunk
     const int64_t chunk = bid / per_chunk;
     if (threadIdx.x < B * 3) {
-        const int b = threadIdx.x / 3, q = threadIdx.x % 3;
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += red[w][b][q];
-        a.block_partial[bid * (B * 3) + threadIdx.x] = s;
+        a.block_partial[bid * (B * 3) + threadIdx.x] = grp[0][threadIdx.x];
         __threadfence();
     }
     __syncthreads();
@@ -285,47 +326,60 @@ __global__ void __launch_bounds__(1024) k_final(TermArgs a)
     }
 }
 
-// One block per sample: fixed-order sum of the chunk partials, then the
-// correlation entry, the squared norm, the drift checks and (FP32) the
-// scale of the next step's starting state.
-__global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a)
+// Sum of the chunk partials of each sample, spread over kReduceSplit blocks
+// per sample (GB300's FP64 adder throughput per SM is small, so one block
+// per sample would take tens of microseconds): block (s, j) sums chunks
+// j, j + kReduceSplit, ... of sample s in order; the last of the sample's
+// blocks (ticket after a fence) adds the kReduceSplit sums in order and
+// writes the correlation entry, the squared norm, the drift checks and (FP32)
+// the scale of the next step's starting state.
+constexpr int kReduceSplit = 64;
+
+__global__ void __launch_bounds__(64) k_reduce(ReduceArgs a)
 {
-    __shared__ double part[1024];
-    const int s = blockIdx.x;
+    __shared__ int last;
+    const int s = blockIdx.x, j = blockIdx.y;
     const int B3 = a.B * 3;
-    const int G = blockDim.x / B3;
     const int t = threadIdx.x;
     const int64_t c0 = a.sample_chunk_off[s], c1 = a.sample_chunk_off[s + 1];
-    if (t < G * B3) {
-        const int g = t / B3, comp = t % B3;
+    double *mine = a.partial2 + ((int64_t)s * kReduceSplit + j) * B3;
+    if (t < B3) {
         double acc = 0.0;
-#pragma unroll 8
-        for (int64_t c = c0 + g; c < c1; c += G) acc += a.partial[c * B3 + comp];
-        part[t] = acc;
+#pragma unroll 4
+        for (int64_t c = c0 + j; c < c1; c += kReduceSplit) acc += a.partial[c * B3 + t];
+        mine[t] = acc;
+        __threadfence();
+    }
+    __syncthreads();
+    if (t == 0) last = (atomicAdd(a.sample_ticket + s, 1u) == kReduceSplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double v[48];
+    if (t < B3) {
+        double acc = 0.0;
+        const double *base = a.partial2 + (int64_t)s * kReduceSplit * B3;
+        for (int k = 0; k < kReduceSplit; ++k) acc += __ldcg(base + (int64_t)k * B3 + t);
+        v[t] = acc;
     }
     __syncthreads();
     const int step = a.step[s];
     if (t < a.B) {
-        double v[3];
-        for (int q = 0; q < 3; ++q) {
-            double acc = 0.0;
-            for (int g = 0; g < G; ++g) acc += part[g * B3 + t * 3 + q];
-            v[q] = acc;
-        }
+        const double re = v[t * 3], im = v[t * 3 + 1], nn = v[t * 3 + 2];
         const int state = a.group_state0 + t;
         const int64_t idx = ((int64_t)s * a.n_states + state) * (a.n_steps + 1) + step;
-        a.corr[idx] = make_double2(v[0], v[1]);
-        a.norms[idx] = v[2];
-        const double drift = fabs(v[2] - 1.0);
-        if (!(v[2] == v[2]) || !(v[0] == v[0]) || !(v[1] == v[1]) || v[2] - v[2] != 0.0) {
+        a.corr[idx] = make_double2(re, im);
+        a.norms[idx] = nn;
+        const double drift = fabs(nn - 1.0);
+        if (!(nn == nn) || !(re == re) || !(im == im) || nn - nn != 0.0) {
             atomicOr(a.error_flags, 2);
         } else if (drift > a.hard_bound) {
             atomicOr(a.error_flags, 1);
         }
         if (a.scale) {
             double sc = 1.0;
-            if (drift > a.renorm_bound && v[2] > 0.0 && v[2] - v[2] == 0.0) {
-                sc = 1.0 / sqrt(v[2]);
+            if (drift > a.renorm_bound && nn > 0.0 && nn - nn == 0.0) {
+                sc = 1.0 / sqrt(nn);
                 atomicAdd(a.renorm_count, 1ull);
             }
             a.scale[(int64_t)s * a.B + t] = sc;
@@ -333,7 +387,10 @@ __global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a)
         }
     }
     __syncthreads();
-    if (t == 0) a.step[s] = step + 1;
+    if (t == 0) {
+        a.step[s] = step + 1;
+        a.sample_ticket[s] = 0;          // ready for the next launch
+    }
 }
 
 template <typename V, int SPL> struct StoreC;
@@ -410,11 +467,12 @@ cudaError_t launch_term_t(const TermArgs &a, int threads, cudaStream_t st)
 template <typename V, int L, int SPL>
 cudaError_t launch_final_t(const TermArgs &a, int threads, bool compute, cudaStream_t st)
 {
-    const unsigned blocks = (unsigned)(a.n_rows * L / threads);
+    (void)threads;   // the closing term has its own block size
+    const unsigned blocks = (unsigned)(a.n_rows * L / kFinalThreads);
     if (compute)
-        k_final<V, L, SPL, true><<<blocks, threads, 0, st>>>(a);
+        k_final<V, L, SPL, true><<<blocks, kFinalThreads, 0, st>>>(a);
     else
-        k_final<V, L, SPL, false><<<blocks, threads, 0, st>>>(a);
+        k_final<V, L, SPL, false><<<blocks, kFinalThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -459,7 +517,7 @@ cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaSt
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st)
 {
-    k_reduce<<<a.n_samples, 1024, 0, st>>>(a);
+    k_reduce<<<dim3(a.n_samples, kReduceSplit), 64, 0, st>>>(a);
     return cudaGetLastError();
 }
 

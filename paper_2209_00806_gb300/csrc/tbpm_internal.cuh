@@ -20,7 +20,7 @@ constexpr int kSliceRows = 32;
 constexpr int kChunkRows = 1024;
 constexpr int kMaxStates = 64;
 constexpr int kMaxTerms = 128;
-constexpr int kMaxGroups = 8;
+constexpr int kMaxGroups = 64;
 
 // Launch variants of the term kernels (bits of TermArgs::variant).
 constexpr int kVariantZigZag = 1;       // alternate the traversal direction per launch
@@ -63,6 +63,8 @@ struct TermArgs {
 
 struct ReduceArgs {
     const double *partial;           // [n_chunks][B][3]
+    double *partial2;                // [n_samples][64][B][3]
+    unsigned int *sample_ticket;     // [n_samples], zero between launches
     const int64_t *sample_chunk_off; // [n_samples + 1]
     int n_samples;
     int B;

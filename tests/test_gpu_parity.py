@@ -94,7 +94,7 @@ def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
 
 
 @pytest.mark.parametrize("cfg", [(16, 128, 3), (4, 512, 1), (2, 64, 0), (16, 256, 4), (4, 256, 5),
-                                 (1, 256, 4)])
+                                 (2, 256, 4), (1, 256, 0)])
 def test_gpu_fp32_launch_shapes(tb, cfg):
     smp = lattice.random_graph(2500, 7000, seed=9, onsite_w=2.0)
     H = exact.dense_h(smp)
