@@ -64,6 +64,16 @@ struct tbpm_ctx {
     int *d_chunk_count = nullptr;
     double *d_partial2 = nullptr;          // [n_samples][64][16][3]
     unsigned int *d_sample_ticket = nullptr;
+    // wavefront-fused step
+    int32_t *d_items = nullptr;
+    int64_t items_len = 0;
+    int items_key[3] = {-1, -1, -1};       // (J, tile rows, radius) of the table
+    int *d_done = nullptr;
+    int64_t done_len = 0;
+    unsigned long long *d_fcounter = nullptr;
+    FusedTerm *d_fterms = nullptr;         // [3][kMaxTerms]
+    double *d_tile_partial = nullptr;
+    int64_t tile_partial_len = 0;
     int *d_step = nullptr;       // [n_samples]
     int *d_flags = nullptr;      // [0] error bits
     unsigned long long *d_renorm = nullptr;
@@ -147,6 +157,18 @@ void free_hamiltonian(tbpm_ctx *c)
     cudaFree(c->d_sample_ticket);
     c->d_partial2 = nullptr;
     c->d_sample_ticket = nullptr;
+    cudaFree(c->d_items);
+    cudaFree(c->d_done);
+    cudaFree(c->d_fcounter);
+    cudaFree(c->d_fterms);
+    cudaFree(c->d_tile_partial);
+    c->d_items = nullptr;
+    c->d_done = nullptr;
+    c->d_fcounter = nullptr;
+    c->d_fterms = nullptr;
+    c->d_tile_partial = nullptr;
+    c->items_len = c->done_len = c->tile_partial_len = 0;
+    c->items_key[0] = c->items_key[1] = c->items_key[2] = -1;
     cudaFree(c->d_step);
     c->d_block_partial = nullptr;
     c->d_chunk_count = nullptr;
@@ -511,7 +533,7 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
         return fail(c, TBPM_E_INVALID_ARG, "group width must be a power of two within the cap");
     if (threads < 64 || threads > 1024 || (threads & (threads - 1)))
         return fail(c, TBPM_E_INVALID_ARG, "threads must be a power of two in 64..1024");
-    if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma))
+    if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
     if (c->max_group[precision] != max_group || c->threads[precision] != threads) free_groups(c);
     c->max_group[precision] = max_group;
@@ -655,6 +677,56 @@ void split_coeff(double c, int fp32, double *hi, double *lo)
 
 }  // namespace
 
+// Item table of the wavefront-fused step: every (term j, tile t) ordered by
+// the key t + j (radius + 1), so each item's dependencies -- (j-1, t') for
+// |t' - t| <= radius -- come earlier; items of equal key are independent.
+static int ensure_fused(tbpm_ctx *c, int J, int R, int radius, int maxB)
+{
+    const int64_t T = c->H.n_rows / R;
+    if (T >= ((int64_t)1 << 25) || J >= 128)
+        return fail(c, TBPM_E_UNSUPPORTED, "fused step: too many tiles or terms");
+    if (c->items_key[0] != J || c->items_key[1] != R || c->items_key[2] != radius) {
+        std::vector<int32_t> items;
+        items.reserve((size_t)J * T);
+        const int64_t kmax = (T - 1) + (int64_t)(J - 1) * (radius + 1);
+        for (int64_t k = 0; k <= kmax; ++k)
+            for (int j = 0; j < J; ++j) {
+                const int64_t t = k - (int64_t)j * (radius + 1);
+                if (t >= 0 && t < T) items.push_back((int32_t)(((uint32_t)j << 25) | (uint32_t)t));
+            }
+        cudaFree(c->d_items);
+        c->d_items = nullptr;
+        int rc = dalloc(c, &c->d_items, items.size());
+        if (rc) return rc;
+        CUDA_OR_FAIL(c, cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice));
+        c->items_len = (int64_t)items.size();
+        c->items_key[0] = J;
+        c->items_key[1] = R;
+        c->items_key[2] = radius;
+    }
+    if (c->done_len < (int64_t)J * T) {
+        cudaFree(c->d_done);
+        c->d_done = nullptr;
+        int rc = dalloc(c, &c->d_done, (size_t)J * T);
+        if (rc) return rc;
+        c->done_len = (int64_t)J * T;
+    }
+    if (!c->d_fcounter) {
+        int rc = dalloc(c, &c->d_fcounter, 1);
+        if (!rc) rc = dalloc(c, &c->d_fterms, 3 * (size_t)kMaxTerms);
+        if (rc) return rc;
+    }
+    if (c->tile_partial_len < T * maxB * 3) {
+        cudaFree(c->d_tile_partial);
+        c->d_tile_partial = nullptr;
+        int rc = dalloc(c, &c->d_tile_partial, (size_t)T * maxB * 3);
+        if (rc) return rc;
+        c->tile_partial_len = T * maxB * 3;
+    }
+    return TBPM_OK;
+}
+
 static int get_events(tbpm_ctx *c, size_t n)
 {
     while (c->events.size() < n) {
@@ -684,6 +756,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         return fail(c, TBPM_E_STATE, "nothing to resume in this precision");
     const bool profile = (flags & TBPM_PROP_PROFILE) != 0;
     const bool graph = (flags & TBPM_PROP_GRAPH) != 0 && !profile;
+    const bool fused = (c->variant[precision] & kVariantFused) != 0;
     if (flags & TBPM_PROP_PERSISTENT)
         return fail(c, TBPM_E_UNSUPPORTED, "persistent mode is not built");
 
@@ -782,6 +855,59 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         ra.renorm_count = c->d_renorm;
         ra.error_flags = c->d_flags;
 
+        // wavefront-fused step: item table, flags and the term tables of the
+        // three buffer rotations
+        FusedArgs fa;
+        memset(&fa, 0, sizeof(fa));
+        if (fused) {
+            const int R = fused_tile_rows(fp32, g.B);
+            const int radius = (int)((c->H.bandwidth + R - 1) / R);
+            int maxB = 1;
+            for (auto &g2 : c->groups) maxB = std::max(maxB, g2.B);
+            rc = ensure_fused(c, M - 1, R, radius, maxB);
+            if (rc) return rc;
+            std::vector<FusedTerm> tabs(3 * (size_t)kMaxTerms);
+            for (int cur0 = 0; cur0 < 3; ++cur0) {
+                int nx = 0;
+                std::vector<Launch> sch = schedule(a, cur0, &nx);
+                for (size_t k = 0; k < sch.size(); ++k) {
+                    FusedTerm &ft = tabs[cur0 * kMaxTerms + k];
+                    ft.x = sch[k].x;
+                    ft.z = sch[k].z;
+                    ft.out = sch[k].out;
+                    ft.final_term = sch[k].final_term ? 1 : 0;
+                    split_coeff(sch[k].c, fp32, &ft.c_hi, &ft.c_lo);
+                    ft.gamma = sch[k].gamma;
+                    ft.c_hi_f = (float)ft.c_hi;
+                    ft.c_lo_f = (float)ft.c_lo;
+                    ft.gamma_f = (float)ft.gamma;
+                }
+            }
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_fterms, tabs.data(), tabs.size() * sizeof(FusedTerm),
+                                            cudaMemcpyHostToDevice, c->st));
+            CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_done, 0, (size_t)(M - 1) * (c->H.n_rows / R) * sizeof(int),
+                                            c->st));
+            CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));    // host table goes out of scope
+            fa.H = Hv;
+            fa.psi0 = g.psi0;
+            for (int k = 0; k < 3; ++k) fa.bufs[k] = g.buf[k];
+            fa.items = c->d_items;
+            fa.n_items = c->items_len;
+            fa.n_tiles = c->H.n_rows / R;
+            fa.tile_rows = R;
+            fa.radius = radius;
+            fa.done = c->d_done;
+            fa.counter = c->d_fcounter;
+            fa.epoch_ptr = c->d_step;
+            fa.err = c->d_flags;
+            fa.scale = g.scale;
+            fa.scale_f = g.scale_f;
+            fa.chunk_sample = c->H.chunk_sample;
+            fa.tile_partial = c->d_tile_partial;
+            fa.partial = c->d_partial;
+            fa.chunk_count = c->d_chunk_count;
+        }
+
         // C_0 = <psi0|phi(0)>
         {
             TermArgs t0 = base;
@@ -797,6 +923,31 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         ra.scale_f = g.scale_f;
 
         auto run_step = [&](int cur, int *next_cur, bool timed) -> int {
+            if (fused) {
+                schedule(a, cur, next_cur);
+                size_t e0 = 0;
+                if (timed) {
+                    e0 = ev_used;
+                    ev_used += ev_per_step;
+                    step_ev.push_back(e0);
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0], c->st));
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 1], c->st));
+                }
+                CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_fcounter, 0, sizeof(unsigned long long), c->st));
+                FusedArgs f = fa;
+                f.psi = g.buf[cur];
+                f.terms = c->d_fterms + (size_t)cur * kMaxTerms;
+                cudaError_t e = launch_step_fused(f, fp32, g.B, c->num_sms, c->st);
+                if (e != cudaSuccess)
+                    return fail(c, TBPM_E_CUDA, std::string("fused step: ") + cudaGetErrorString(e));
+                if (timed) {
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 2], c->st));
+                    CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 3], c->st));
+                }
+                CUDA_OR_FAIL(c, launch_reduce(ra, c->st));
+                if (timed) CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 4], c->st));
+                return TBPM_OK;
+            }
             std::vector<Launch> sch = schedule(a, cur, next_cur);
             size_t e0 = 0;
             if (timed) {
@@ -879,7 +1030,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 if (rc) return rc;
             }
             g.cur = nxt;
-            launches += M;   // M-1 term kernels + one reduction
+            launches += fused ? 2 : M;   // term kernels (or the fused step) + one reduction
         }
     }
     if (profile) CUDA_OR_FAIL(c, cudaEventRecord(ev_all1, c->st));
@@ -936,7 +1087,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             t_fin += a2;
             t_red += a3;
         }
-        S.term_launches = (int64_t)step_ev.size() * n_int;
+        // fused: the whole step is one launch; report its per-term share
+        S.term_launches = (int64_t)step_ev.size() * (fused ? (M - 1) : n_int);
         if (S.term_launches) S.ms_term_avg = t_int / S.term_launches;
         if (!step_ev.empty()) {
             S.ms_final_avg = t_fin / step_ev.size();
@@ -1261,7 +1413,7 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
     if (widths.empty()) widths.push_back(1);
     const int thread_opts[] = {128, 256, 512};
     const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints,
-                                kVariantTma, kVariantTma | kVariantZigZag};
+                                kVariantTma, kVariantTma | kVariantZigZag, kVariantFused};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
     for (int B : widths)

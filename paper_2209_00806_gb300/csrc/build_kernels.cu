@@ -196,7 +196,7 @@ __global__ void k_diag(int64_t n_orb, const double *onsite, double inv_s,
 // a non-negative double (which orders like an unsigned integer).
 __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int32_t *deg,
                             const double *diag, int32_t *col, double *val,
-                            unsigned long long *gersh_bits)
+                            unsigned long long *gersh_bits, unsigned long long *band)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_rows) return;
@@ -218,8 +218,14 @@ __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int3
         val[base + (int64_t)(b + 1) * kSliceRows] = v;
     }
     double g = fabs(diag[r]);
-    for (int a = 0; a < d; ++a) g += fabs(val[base + (int64_t)a * kSliceRows]);
+    long long bw = 0;
+    for (int a = 0; a < d; ++a) {
+        g += fabs(val[base + (int64_t)a * kSliceRows]);
+        const long long dist = (long long)col[base + (int64_t)a * kSliceRows] - (long long)r;
+        bw = max(bw, dist < 0 ? -dist : dist);
+    }
     atomicMax(gersh_bits, (unsigned long long)__double_as_longlong(g));
+    if (bw > 0) atomicMax(band, (unsigned long long)bw);
 }
 
 __global__ void k_bond_rows(int64_t n_hop, const int64_t *hi, const int64_t *hj,
@@ -279,16 +285,16 @@ int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
     int32_t *deg = nullptr, *fill = nullptr;
     int64_t *entries = nullptr;
     int *err = nullptr;           // [0] error bits, [1] max width
-    unsigned long long *gbits = nullptr;
+    unsigned long long *gbits = nullptr;   // [0] Gershgorin bits, [1] bandwidth
     CK(cudaMalloc(&deg, n_rows * sizeof(int32_t)));
     CK(cudaMalloc(&fill, n_rows * sizeof(int32_t)));
     CK(cudaMalloc(&entries, (n_slices + 1) * sizeof(int64_t)));
     CK(cudaMalloc(&err, 2 * sizeof(int)));
-    CK(cudaMalloc(&gbits, sizeof(unsigned long long)));
+    CK(cudaMalloc(&gbits, 2 * sizeof(unsigned long long)));
     CK(cudaMemsetAsync(deg, 0, n_rows * sizeof(int32_t), st));
     CK(cudaMemsetAsync(fill, 0, n_rows * sizeof(int32_t), st));
     CK(cudaMemsetAsync(err, 0, 2 * sizeof(int), st));
-    CK(cudaMemsetAsync(gbits, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(gbits, 0, 2 * sizeof(unsigned long long), st));
 
     if (in.n_hop > 0) {
         k_count<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.n_orb, in.hop_i, in.hop_j,
@@ -340,10 +346,10 @@ int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
                                                   out.user_to_row, out.diag64);
     CK(cudaGetLastError());
     k_sort_rows<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, deg, out.diag64,
-                                                     out.col, out.val64, gbits);
+                                                     out.col, out.val64, gbits, gbits + 1);
     CK(cudaGetLastError());
-    unsigned long long hg = 0;
-    CK(cudaMemcpyAsync(&hg, gbits, sizeof(hg), cudaMemcpyDeviceToHost, st));
+    unsigned long long hg[2] = {0, 0};
+    CK(cudaMemcpyAsync(hg, gbits, sizeof(hg), cudaMemcpyDeviceToHost, st));
 
     // chunk -> sample table
     int64_t n_chunks = n_rows / kChunkRows;
@@ -372,8 +378,9 @@ int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
     }
     CK(cudaStreamSynchronize(st));
     double g;
-    memcpy(&g, &hg, sizeof(g));
+    memcpy(&g, &hg[0], sizeof(g));
     out.gershgorin = g;
+    out.bandwidth = (int64_t)hg[1];
     if (!keep64) {
         cudaFree(out.val64);
         cudaFree(out.diag64);

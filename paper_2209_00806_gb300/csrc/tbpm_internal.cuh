@@ -26,6 +26,7 @@ constexpr int kMaxGroups = 64;
 constexpr int kVariantZigZag = 1;       // alternate the traversal direction per launch
 constexpr int kVariantStreamHints = 2;  // evict-first loads of the own-row streams
 constexpr int kVariantTma = 4;          // persistent TMA-staged term kernel
+constexpr int kVariantFused = 8;        // all terms of a step in one wavefront launch
 
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.
@@ -113,6 +114,39 @@ cudaError_t launch_get_states(const void *psi, int64_t n_orb, int n_states,
                               const int32_t *user_to_row, int group_state0, int B,
                               int fp32, double2 *out_user, cudaStream_t st);
 
+// One term of the fused step (fused_kernels.cu): buffer indices 0..2 of the
+// group (x < 0: x is psi; z < 0: none) and the coefficients.
+struct FusedTerm {
+    int x, z, out, final_term;
+    double c_hi, c_lo, gamma;
+    float c_hi_f, c_lo_f, gamma_f;
+};
+
+struct FusedArgs {
+    SellView H;
+    const void *psi;            // current state (read only during the step)
+    const void *psi0;
+    void *bufs[3];
+    const FusedTerm *terms;     // [J]
+    const int32_t *items;       // [J * n_tiles] (j << 25 | t) in wavefront order
+    int64_t n_items;
+    int64_t n_tiles;
+    int tile_rows, radius;
+    int *done;                  // [J][n_tiles] epoch flags
+    unsigned long long *counter;
+    const int *epoch_ptr;       // epoch = *epoch_ptr + 1
+    int *err;
+    const double *scale;
+    const float *scale_f;
+    const int32_t *chunk_sample;
+    double *tile_partial;       // [n_tiles][B][3]
+    double *partial;            // [n_chunks][B][3]
+    int *chunk_count;
+};
+
+cudaError_t launch_step_fused(const FusedArgs &f, int fp32, int B, int num_sms, cudaStream_t st);
+int fused_tile_rows(int fp32, int B);
+
 // Persistent TMA-staged term kernel (tma_kernels.cu); err bit 4 = bounded
 // wait expired.
 cudaError_t launch_term_tma(const TermArgs &a, int fp32, int B, int max_width, int *err,
@@ -157,6 +191,7 @@ struct BuildOutput {
     int64_t n_hop = 0;
     double gershgorin = 0.0;
     int max_width = 0;
+    int64_t bandwidth = 0;           // max |col - row| over the stored entries
 };
 
 // Returns TBPM status; fills msg on failure.  Allocations in `out` are owned

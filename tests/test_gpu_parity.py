@@ -187,6 +187,46 @@ def test_gpu_tma_kernel_is_bit_identical(tb, prec):
         assert np.array_equal(c, outs[0][0]) and np.array_equal(phi, outs[0][1])
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kind", ["graphene", "random", "batch"])
+def test_gpu_fused_step(tb, prec, kind):
+    """The wavefront-fused step: the same states as the per-term kernels (bit
+    for bit: same arithmetic per row) and C within rounding of the reduction
+    order; against the oracle as everywhere else."""
+    offs = None
+    if kind == "graphene":
+        smp = lattice.graphene(40, 37, pbc=True, seed=8, onsite_w=1.0, vacancy_frac=0.02)
+        s, S, parts = 9.5, 7, None
+    elif kind == "random":
+        smp = lattice.random_graph(6000, 15000, seed=12, onsite_w=2.0)   # bandwidth ~ n
+        s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(exact.dense_h(smp))))
+        S, parts = 3, None
+    else:
+        parts = [lattice.graphene(L, L, pbc=True, seed=30 + L, onsite_w=0.5) for L in (7, 30, 12)]
+        smp, offs = lattice.concat(parts)
+        s, S = 9.5, 4
+    th = rng.phases(77, S, smp.n_orb)
+    base, _, phi0, _ = run_gpu(tb, smp, s, th, 30, precision=prec, offsets=offs, cfg=(8, 128, 1))
+    fused, st, phi1, _ = run_gpu(tb, smp, s, th, 30, precision=prec, offsets=offs, cfg=(8, 128, 8))
+    assert np.array_equal(phi0, phi1)
+    assert np.max(np.abs(base - fused)) < (1e-13 if prec == 0 else 1e-6)
+    if parts is None:
+        ref = run_oracle(smp, s, th, 30)
+        assert np.max(np.abs(fused[0] - ref)) < (1e-10 if prec == 0 else 2e-5)
+    else:
+        for k, q in enumerate(parts):
+            ref = run_oracle(q, s, th[:, offs[k]:offs[k + 1]], 30)
+            assert np.max(np.abs(fused[k] - ref)) < (1e-10 if prec == 0 else 2e-5)
+
+
+def test_gpu_fused_step_graph_replay(tb):
+    smp = lattice.graphene(30, 30, pbc=True, seed=2, onsite_w=1.0)
+    th = rng.phases(5, 4, smp.n_orb)
+    a, _, _, _ = run_gpu(tb, smp, 9.5, th, 20, precision=1, cfg=(4, 128, 8))
+    b, _, _, _ = run_gpu(tb, smp, 9.5, th, 20, precision=1, cfg=(4, 128, 8), flags=2)
+    assert np.array_equal(a, b)
+
+
 def test_gpu_resume_continues_the_propagation(tb):
     smp = lattice.graphene(10, 10, pbc=True, seed=3, onsite_w=0.5)
     th = rng.phases(2, 3, smp.n_orb)
