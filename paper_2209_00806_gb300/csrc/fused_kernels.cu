@@ -197,7 +197,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_fused(FusedArgs f)
                 if (tt < 0 || tt >= f.n_tiles) continue;
                 long long it = 0;
                 while (ld_acquire(flags + tt) < epoch) {
-                    if (++it > kPollLimit) {
+                    // give up after kPollLimit polls, or at once when another
+                    // block already gave up (the launch then only drains)
+                    if (++it > kPollLimit || (ld_acquire(f.err) & 4)) {
                         atomicOr(f.err, 4);
                         break;
                     }

@@ -113,7 +113,7 @@ def test_gpu_autotune_picks_a_valid_shape(tb):
         p.set_phase_states(th)
         best = p.autotune(Z, precision=1, probe_steps=2)
         assert best["group"] in (2, 4) and best["threads"] in (128, 256, 512)
-        assert best["variant"] in (0, 1, 3) and best["ms_per_step"] > 0
+        assert best["variant"] in (0, 1, 3, 4, 5, 8) and best["ms_per_step"] > 0
         c = p.propagate(Z, 30, 1)
     ref = run_oracle(smp, 9.5, th, 30)
     assert np.max(np.abs(c[0] - ref)) < 2e-5
