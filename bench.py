@@ -230,6 +230,17 @@ def kernel_traffic():
     return d, d
 
 
+def reduce_max_time(ms, world, device=None):
+    """Slowest rank's time (the whole job's time under weak scaling)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def sample_part(w, k):
     """Sample k of a (possibly batched) workload as its own bond list."""
     from tbpm_inputs import lattice
@@ -315,11 +326,7 @@ def run_gb300(args):
                 acc["drift"] = max(acc["drift"], st["max_norm_drift"])
             e1.record(stream)
             barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max_time(e0.elapsed_time(e1), world, dev)
         ms_term = acc["ms_term"] / acc["n_term"] if acc["n_term"] else None
         return dict(ms=ms, res=res, stats=prop.stats(), ms_term=ms_term, clocks=clk.summary(),
                     launches=acc["launches"], renorm=acc["renorm"], drift=acc["drift"])
@@ -380,11 +387,7 @@ def run_gb300(args):
         for _ in range(args.steps):
             host_step()
         barrier()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = reduce_max_time(time.perf_counter() - t0, world, dev)
         h2d = sum(x.numel() * x.element_size() for x in (h_on, h_hi, h_hj, h_hv, h_th))
         d2h = h_c.numel() * h_c.element_size() + NS * S * (NT + 1) * 8   # C + norms
         e2e = {"value": total_units / dt, "unit": "orbital-Chebyshev-steps/s",

@@ -168,9 +168,11 @@ int tbpm_bessel_coefficients(double z, double tol, int max_terms, double *J_out,
  * Each time step runs M-1 fused sparse-product terms of the Clenshaw form
  * of the paper's Chebyshev sum and one deterministic FP64 reduction.
  * In FP32 the norm of each state is carried in FP64: when |<phi|phi> - 1|
- * exceeds 1e-5 the next step starts from phi / |phi|.
+ * exceeds the renormalisation bound the next step starts from phi / |phi|
+ * (tbpm_set_norm_policy).
  * Errors: STATE (no Hamiltonian or states), INVALID_ARG, NORM_DRIFT (drift
- * above 1e-6 in FP64 or 1e-2 in FP32: s too small), NONFINITE, CUDA. */
+ * above the hard bound: s too small), NONFINITE, TIMEOUT (a bounded device
+ * wait of the TMA or fused kernels expired), CUDA. */
 int tbpm_propagate(tbpm_ctx *ctx, double z, int n_steps, int precision, double *corr_out,
                    int where_out, int flags);
 
@@ -233,8 +235,22 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
 #define TBPM_VARIANT_TMA 4           /* persistent term kernel: each tile's row streams
                                         and matrix slices staged in shared memory by
                                         bulk asynchronous copies, 3 stages ahead */
+#define TBPM_VARIANT_FUSED 8         /* all terms of a time step in one cooperative
+                                        launch, ordered as a wavefront over row tiles
+                                        so intermediate vectors stay in L2; needs a
+                                        banded row order (TBPM_BUILD_REORDER_RCM) */
+#define TBPM_VARIANT_FUSED_TILE(k) ((k) << 4)  /* fused tile rows x 4^k, k = 0..2 */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
+
+/* Norm policy of the propagation (a5).  FP32: when |<phi|phi> - 1| of a
+ * state exceeds renorm_fp32 (default 1e-5) after a step, the next step starts
+ * from phi / |phi| (the norm is summed and the factor applied in FP64
+ * before rounding to FP32); above hard_fp32 (default 1e-2) the call fails
+ * with TBPM_E_NORM_DRIFT.  FP64: above hard_fp64 (default 1e-6) the call
+ * fails.  The unitary evolution of Sec. 2.2 keeps the norm; drift means
+ * rounding (FP32) or an s below the spectral radius.  Bounds must be > 0. */
+int tbpm_set_norm_policy(tbpm_ctx *ctx, double renorm_fp32, double hard_fp32, double hard_fp64);
 
 /* Autotuner: for the current Hamiltonian and states, time probe_steps
  * (1..64) steps of each candidate launch shape -- state-group width (the

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("tbpm_propagate_adjoint", _I32, [P, _F64, _I32, P, _I32, _I32, P, P, _I32]),
     ("tbpm_dos_adjoint", _I32, [P, _I32, _I32, _F64, _I32, _F64, _F64, P]),
     ("tbpm_set_launch_config", _I32, [P, _I32, _I32, _I32, _I32]),
+    ("tbpm_set_norm_policy", _I32, [P, _F64, _F64, _F64]),
     ("tbpm_correlation_noalloc", _I32, [P, P, _I64, _I32, P, P, P]),
     ("tbpm_autotune", _I32, [P, _I32, _F64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                              ctypes.POINTER(_I32), ctypes.POINTER(_F64)]),
@@ -232,6 +233,10 @@ def tbpm_propagate_adjoint(ctx, z, n_steps, gbar, where, K, grad_hop, grad_onsit
 def tbpm_dos_adjoint(dl_dd, n_e, n_steps, tau, window, e_min, e_max, gbar_out):
     return check(None, lib.tbpm_dos_adjoint(ptr(dl_dd), n_e, n_steps, tau, window, e_min,
                                             e_max, ptr(gbar_out)))
+
+
+def tbpm_set_norm_policy(ctx, renorm_fp32=1e-5, hard_fp32=1e-2, hard_fp64=1e-6):
+    return check(ctx, lib.tbpm_set_norm_policy(ctx, renorm_fp32, hard_fp32, hard_fp64))
 
 
 def tbpm_autotune(ctx, precision, z, probe_steps=4):

@@ -56,6 +56,7 @@ struct tbpm_ctx {
     int threads[2] = {256, 256}; // threads per block per precision
     int variant[2] = {kVariantZigZag, kVariantZigZag};  // term-kernel launch variants
     int num_sms = 0;
+    double renorm_fp32 = 1e-5, hard_fp32 = 1e-2, hard_fp64 = 1e-6;   // norm policy
     std::vector<Group> groups;
     double *d_partial = nullptr;
     int64_t partial_len = 0;
@@ -533,12 +534,26 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
         return fail(c, TBPM_E_INVALID_ARG, "group width must be a power of two within the cap");
     if (threads < 64 || threads > 1024 || (threads & (threads - 1)))
         return fail(c, TBPM_E_INVALID_ARG, "threads must be a power of two in 64..1024");
-    if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused))
+    if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
+                                  (3 << kVariantFusedTileShift)) ||
+        ((variant >> kVariantFusedTileShift) & 3) == 3)
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
     if (c->max_group[precision] != max_group || c->threads[precision] != threads) free_groups(c);
     c->max_group[precision] = max_group;
     c->threads[precision] = threads;
     c->variant[precision] = variant;
+    return TBPM_OK;
+}
+
+extern "C" int tbpm_set_norm_policy(tbpm_ctx *c, double renorm_fp32, double hard_fp32,
+                                    double hard_fp64)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!(renorm_fp32 > 0.0) || !(hard_fp32 > 0.0) || !(hard_fp64 > 0.0))
+        return fail(c, TBPM_E_INVALID_ARG, "norm bounds must be > 0");
+    c->renorm_fp32 = renorm_fp32;
+    c->hard_fp32 = hard_fp32;
+    c->hard_fp64 = hard_fp64;
     return TBPM_OK;
 }
 
@@ -588,7 +603,7 @@ static int ensure_groups(tbpm_ctx *c, int prec)
     int64_t need_b = 0;
     for (auto &g : c->groups) {
         const int L = prec == TBPM_FP64 ? g.B : std::max(1, g.B / 2);
-        need_b = std::max<int64_t>(need_b, c->H.n_rows * L / 512 * g.B * 3);   // closing-term blocks of 512
+        need_b = std::max<int64_t>(need_b, c->H.n_rows * L / 128 * g.B * 3);   // closing-term blocks of 128
     }
     if (need_b > c->block_partial_len) {
         cudaFree(c->d_block_partial);
@@ -850,8 +865,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         ra.step = c->d_step;
         ra.corr = c->d_corr;
         ra.norms = c->d_norms;
-        ra.renorm_bound = 1e-5;
-        ra.hard_bound = fp32 ? 1e-2 : 1e-6;
+        ra.renorm_bound = c->renorm_fp32;
+        ra.hard_bound = fp32 ? c->hard_fp32 : c->hard_fp64;
         ra.renorm_count = c->d_renorm;
         ra.error_flags = c->d_flags;
 
@@ -860,7 +875,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         FusedArgs fa;
         memset(&fa, 0, sizeof(fa));
         if (fused) {
-            const int R = fused_tile_rows(fp32, g.B);
+            int R = fused_tile_rows(fp32, g.B, (c->variant[precision] >> kVariantFusedTileShift) & 3);
+            while (R > kChunkRows && c->H.n_rows % R) R /= 4;   // tiles must cover the rows exactly
             const int radius = (int)((c->H.bandwidth + R - 1) / R);
             int maxB = 1;
             for (auto &g2 : c->groups) maxB = std::max(maxB, g2.B);
@@ -1413,7 +1429,9 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
     if (widths.empty()) widths.push_back(1);
     const int thread_opts[] = {128, 256, 512};
     const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints,
-                                kVariantTma, kVariantTma | kVariantZigZag, kVariantFused};
+                                kVariantTma, kVariantTma | kVariantZigZag, kVariantFused,
+                                kVariantFused | (1 << kVariantFusedTileShift),
+                                kVariantFused | (2 << kVariantFusedTileShift)};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
     for (int B : widths)

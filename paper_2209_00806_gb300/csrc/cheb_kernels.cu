@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_term(TermArgs a)
 // form every product and sum is FP64, but rows are summed in a shared-memory
 // tree (one add per value) instead of a butterfly (one add per value and
 // level on every lane).
-constexpr int kFinalThreads = 512;
+constexpr int kFinalThreads = 128;
 
 template <typename V, int L, int SPL, bool COMPUTE>
 __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
@@ -287,8 +287,8 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
             red[(lrow * B + b) * 3 + 2] = (double)pnr[j];
         }
         __syncthreads();
-        if (threadIdx.x < 8 * B * 3) {
-            const int gidx = threadIdx.x / (B * 3), v = threadIdx.x % (B * 3);
+        for (int idx = threadIdx.x; idx < 8 * B * 3; idx += kFinalThreads) {
+            const int gidx = idx / (B * 3), v = idx % (B * 3);
             double s = 0.0;
             for (int row = gidx; row < ROWS; row += 8) s += red[row * B * 3 + v];
             grp[gidx][v] = s;
@@ -303,12 +303,10 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
     __syncthreads();
     constexpr int per_chunk = kChunkRows / ROWS;     // blocks per chunk
     const int64_t chunk = bid / per_chunk;
-    if (threadIdx.x < B * 3) {
-        a.block_partial[bid * (B * 3) + threadIdx.x] = grp[0][threadIdx.x];
-        __threadfence();
-    }
-    __syncthreads();
     if (threadIdx.x == 0) {
+        // one writer, one fence, one ticket per block
+        for (int v = 0; v < B * 3; ++v) a.block_partial[bid * (B * 3) + v] = grp[0][v];
+        __threadfence();
         const int ticket = atomicAdd(a.chunk_count + chunk, 1);
         last = (ticket == per_chunk - 1);
     }

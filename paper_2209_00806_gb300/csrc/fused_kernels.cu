@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_fused(FusedArgs f)
     const int R = f.tile_rows;
     const int passes = R / ROWS_PER_PASS;
     const int epoch = *f.epoch_ptr + 1;
-    const int per_chunk = kChunkRows / R;
+    const int per_chunk = R < kChunkRows ? kChunkRows / R : 1;
 
     if (tid == 0) s_next = atomicAdd(f.counter, 1ull);
     __syncthreads();
@@ -214,33 +214,16 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_fused(FusedArgs f)
         const void *z = tm.z < 0 ? nullptr : f.bufs[tm.z];
         float fre[SPL], fim[SPL], fnr[SPL];
         double dre[SPL], dim[SPL], dnr[SPL];
+        auto zero = [&]() {
 #pragma unroll
-        for (int q = 0; q < SPL; ++q) {
-            fre[q] = fim[q] = fnr[q] = 0.f;
-            dre[q] = dim[q] = dnr[q] = 0.0;
-        }
-        for (int pass = 0; pass < passes; ++pass) {
-            const int64_t r = t * R + pass * ROWS_PER_PASS + tid / L;
-            const V *sc = FCoef<V>::scale(f);
-            if (sc) sc += (int64_t)f.chunk_sample[r / kChunkRows] * B;
-            const Cf<V, SPL> o = fused_row<V, L, SPL>(f, tm, x, z, r, l, sc);
-            reinterpret_cast<Lane *>(out)[r * L + l] = pkf(o);
-            if (tm.final_term) {
-                Cf<V, SPL> p0;
-                unpf(__ldg(reinterpret_cast<const Lane *>(f.psi0) + r * L + l), p0);
-#pragma unroll
-                for (int q = 0; q < SPL; ++q) {
-                    const V pre = fma(p0.re[q], o.re[q], p0.im[q] * o.im[q]);
-                    const V pim = fma(p0.re[q], o.im[q], -(p0.im[q] * o.re[q]));
-                    const V pnr = fma(o.re[q], o.re[q], o.im[q] * o.im[q]);
-                    if (sizeof(V) == 4) { fre[q] += (float)pre; fim[q] += (float)pim; fnr[q] += (float)pnr; }
-                    else { dre[q] += (double)pre; dim[q] += (double)pim; dnr[q] += (double)pnr; }
-                }
+            for (int q = 0; q < SPL; ++q) {
+                fre[q] = fim[q] = fnr[q] = 0.f;
+                dre[q] = dim[q] = dnr[q] = 0.0;
             }
-        }
-        if (tm.final_term) {
-            // per-tile partial of <psi0|phi> and <phi|phi>: butterfly over the
-            // warp's rows (FP32 form in FP32), FP64 from the warp sums up
+        };
+        // block sum of the per-thread partials (FP32 form: FP32 within the
+        // warp, FP64 from the warp sums up) into `dst` (B*3 doubles)
+        auto block_sum = [&](double *dst) {
 #pragma unroll
             for (int off = L; off < 32; off <<= 1) {
 #pragma unroll
@@ -266,23 +249,56 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_fused(FusedArgs f)
                 }
             }
             __syncthreads();
-            const int64_t chunk = t / per_chunk;
             if (tid < B * 3) {
-                double s = 0.0;
-                for (int w2 = 0; w2 < NW; ++w2) s += red[w2][tid];
-                f.tile_partial[t * (B * 3) + tid] = s;
-                __threadfence();
+                double s2 = 0.0;
+                for (int w2 = 0; w2 < NW; ++w2) s2 += red[w2][tid];
+                dst[tid] = s2;
             }
             __syncthreads();
-            if (tid == 0) last = (atomicAdd(f.chunk_count + chunk, 1) == per_chunk - 1);
+        };
+        zero();
+        const int passes_per_chunk = kChunkRows / ROWS_PER_PASS;
+        for (int pass = 0; pass < passes; ++pass) {
+            const int64_t r = t * R + pass * ROWS_PER_PASS + tid / L;
+            const V *sc = FCoef<V>::scale(f);
+            if (sc) sc += (int64_t)f.chunk_sample[r / kChunkRows] * B;
+            const Cf<V, SPL> o = fused_row<V, L, SPL>(f, tm, x, z, r, l, sc);
+            reinterpret_cast<Lane *>(out)[r * L + l] = pkf(o);
+            if (tm.final_term) {
+                Cf<V, SPL> p0;
+                unpf(__ldg(reinterpret_cast<const Lane *>(f.psi0) + r * L + l), p0);
+#pragma unroll
+                for (int q = 0; q < SPL; ++q) {
+                    const V pre = fma(p0.re[q], o.re[q], p0.im[q] * o.im[q]);
+                    const V pim = fma(p0.re[q], o.im[q], -(p0.im[q] * o.re[q]));
+                    const V pnr = fma(o.re[q], o.re[q], o.im[q] * o.im[q]);
+                    if (sizeof(V) == 4) { fre[q] += (float)pre; fim[q] += (float)pim; fnr[q] += (float)pnr; }
+                    else { dre[q] += (double)pre; dim[q] += (double)pim; dnr[q] += (double)pnr; }
+                }
+                // a tile of at least one chunk: the chunk's partial is complete here
+                if (R >= kChunkRows && (pass + 1) % passes_per_chunk == 0) {
+                    const int64_t chunk = (t * R + (int64_t)pass * ROWS_PER_PASS) / kChunkRows;
+                    block_sum(f.partial + chunk * (B * 3));
+                    zero();
+                }
+            }
+        }
+        if (tm.final_term && R < kChunkRows) {
+            // tiles smaller than a chunk: per-tile partial, the chunk's last tile adds them
+            const int64_t chunk = t / per_chunk;
+            block_sum(f.tile_partial + t * (B * 3));
+            if (tid == 0) {
+                __threadfence();
+                last = (atomicAdd(f.chunk_count + chunk, 1) == per_chunk - 1);
+            }
             __syncthreads();
             if (last) {
                 __threadfence();
                 if (tid < B * 3) {
-                    double s = 0.0;
+                    double s2 = 0.0;
                     for (int k = 0; k < per_chunk; ++k)
-                        s += __ldcg(f.tile_partial + (chunk * per_chunk + k) * (B * 3) + tid);
-                    f.partial[chunk * (B * 3) + tid] = s;
+                        s2 += __ldcg(f.tile_partial + (chunk * per_chunk + k) * (B * 3) + tid);
+                    f.partial[chunk * (B * 3) + tid] = s2;
                 }
                 if (tid == 0) f.chunk_count[chunk] = 0;
             }
@@ -312,13 +328,16 @@ cudaError_t launch_fused_t(const FusedArgs &f, int num_sms, cudaStream_t st)
 
 }  // namespace
 
-int fused_tile_rows(int fp32, int B)
+int fused_tile_rows(int fp32, int B, int log4_mult)
 {
-    // 256 rows per item keeps the wavefront band small; rows per pass is
-    // 512 / L, so the tile must be a multiple of that
+    // 256 rows per item (times 4^log4_mult, at most the 1024-row reduction
+    // chunk times 16) keeps the wavefront band small; rows per pass is 512 / L,
+    // so the tile must be a multiple of that
     const int L = fp32 ? (B >= 2 ? B / 2 : 1) : B;
     const int rpp = kFusedThreads / L;
-    return rpp > 256 ? rpp : 256;
+    int rows = rpp > 256 ? rpp : 256;
+    for (int k = 0; k < log4_mult; ++k) rows *= 4;
+    return rows;
 }
 
 cudaError_t launch_step_fused(const FusedArgs &f, int fp32, int B, int num_sms, cudaStream_t st)

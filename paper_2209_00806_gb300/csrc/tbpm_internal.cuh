@@ -27,6 +27,7 @@ constexpr int kVariantZigZag = 1;       // alternate the traversal direction per
 constexpr int kVariantStreamHints = 2;  // evict-first loads of the own-row streams
 constexpr int kVariantTma = 4;          // persistent TMA-staged term kernel
 constexpr int kVariantFused = 8;        // all terms of a step in one wavefront launch
+constexpr int kVariantFusedTileShift = 4;  // bits 4-5: fused tile rows x 4^k
 
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.
@@ -145,7 +146,7 @@ struct FusedArgs {
 };
 
 cudaError_t launch_step_fused(const FusedArgs &f, int fp32, int B, int num_sms, cudaStream_t st);
-int fused_tile_rows(int fp32, int B);
+int fused_tile_rows(int fp32, int B, int log4_mult);
 
 // Persistent TMA-staged term kernel (tma_kernels.cu); err bit 4 = bounded
 // wait expired.

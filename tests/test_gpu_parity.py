@@ -131,6 +131,24 @@ def test_gpu_fp32_dos_l1(tb):
     assert st["max_norm_drift"] < 1e-3
 
 
+def test_gpu_fp32_norm_carry_renormalises(tb):
+    """With a renormalisation bound below the FP32 drift every step restarts
+    from phi / |phi| (FP64 norm); the correlations stay on the oracle's."""
+    w = workloads.disordered_graphene(L=48, n_steps=200, n_energies=1024)
+    th = w.thetas()[0]
+    with tb.Propagator() as p:
+        p.build_sample(w.sample, w.s)
+        tb._native.tbpm_set_norm_policy(p.ctx, 1e-12, 1e-2, 1e-6)
+        p.set_phase_states(th)
+        c = p.propagate(w.z, w.n_steps, 1)
+        st = p.stats()
+        nrm = p.norms()
+    ref = run_oracle(w.sample, w.s, th, w.n_steps)
+    assert st["renormalisations"] > w.n_steps          # nearly every state, every step
+    assert np.max(np.abs(c[0] - ref)) < 2e-5
+    assert np.max(np.abs(nrm - 1)) < 1e-6
+
+
 def test_gpu_rcm_reorder_and_permuted_input(tb):
     smp = lattice.graphene(16, 16, pbc=True, seed=2, onsite_w=1.0, vacancy_frac=0.02)
     perm = np.random.default_rng(7).permutation(smp.n_orb)
