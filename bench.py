@@ -40,10 +40,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="disordered",
-                    choices=["disordered", "batched", "graphene_dos"],
+                    choices=["disordered", "batched", "graphene_dos", "differentiable"],
                     help="disordered: 2048^2 disordered graphene, 4 states, 1024 steps "
                          "(default, the headline); batched: 32 uneven samples x 16 states, "
-                         "512 steps; graphene_dos: 64x64 pristine graphene, 1 state, 1024 steps")
+                         "512 steps; graphene_dos: 64x64 pristine graphene, 1 state, 1024 steps; "
+                         "differentiable: 512^2 graphene, DOS loss, FP64 forward + adjoint")
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
@@ -438,10 +439,83 @@ def run_gb300(args):
     return 0
 
 
+def run_differentiable(args):
+    """One step = the DOS loss and its gradient with respect to every hopping
+    and onsite energy: FP64 forward, host DOS and DOS adjoint, checkpointed
+    adjoint propagation (K = 64)."""
+    import torch
+
+    import paper_2209_00806_gb300 as tb
+    from paper_2209_00806_gb300 import _native as N
+    from tbpm_inputs import workloads
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    w = workloads.differentiable_graphene()
+    pw = workloads.pristine_like(w)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    smp = w.sample
+    S, NT = w.n_states, w.n_steps
+    theta = torch.as_tensor(w.thetas()[0], device=dev)
+    d = {k: torch.as_tensor(getattr(smp, k), device=dev) for k in ("hop_i", "hop_j", "hop_v", "onsite")}
+    p = tb.Propagator(local, stream.cuda_stream)
+    corr = torch.empty((1, S, NT + 1), dtype=torch.complex128, device=dev)
+
+    def dos_of(hv, on):
+        p.build(smp.n_orb, on, d["hop_i"], d["hop_j"], hv, w.s)
+        p.set_phase_states(theta)
+        p.propagate(w.z, NT, N.TBPM_FP64, out=corr)
+        return tb.dos(corr.mean(dim=1)[0].cpu().numpy(), w.tau, *w.e_range, w.n_energies)[1]
+
+    target = dos_of(torch.as_tensor(pw.sample.hop_v, device=dev),
+                    torch.zeros(smp.n_orb, dtype=torch.float64, device=dev))
+
+    def one_step():
+        D = dos_of(d["hop_v"], d["onsite"])
+        loss = float(np.sum((D - target) ** 2))
+        g = tb.dos_adjoint(2.0 * (D - target), NT, w.tau, *w.e_range)
+        gbar = torch.as_tensor(np.ascontiguousarray(np.broadcast_to(g / S, (1, S, NT + 1))), device=dev)
+        gh, go = p.adjoint(w.z, NT, gbar, K=64)
+        return loss, gh, go
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            loss, gh, go = one_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    M = len(tb.tbpm_bessel_coefficients(w.z))
+    units = smp.n_orb * S * NT * (M - 1) * args.steps
+    line = {"metric": "orbital-Chebyshev-steps/s", "value": units / (ms * 1e-3),
+            "unit": "orbital-Chebyshev-steps/s (forward steps of a loss+gradient evaluation)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "differentiable_graphene_512x512", "n_orb": int(smp.n_orb),
+                       "n_bonds": int(smp.n_hop), "states": S, "time_steps": NT,
+                       "checkpoint_every": 64, "dos_bins": w.n_energies,
+                       "loss": "sum_E (D - D_pristine)^2",
+                       "gradients": "all t_b and eps_i"},
+            "loss": loss, "grad_norm_hop": float(torch.linalg.norm(gh)),
+            "grad_norm_onsite": float(torch.linalg.norm(go)),
+            "gpu_launches": int(p.stats()["kernel_launches"]), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    p.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "differentiable":
+        return run_differentiable(args)
     return run_gb300(args)
 
 

@@ -693,20 +693,25 @@ void split_coeff(double c, int fp32, double *hi, double *lo)
 }  // namespace
 
 // Item table of the wavefront-fused step: every (term j, tile t) ordered by
-// the key t + j (radius + 1), so each item's dependencies -- (j-1, t') for
-// |t' - t| <= radius -- come earlier; items of equal key are independent.
-static int ensure_fused(tbpm_ctx *c, int J, int R, int radius, int maxB)
+// the key t + j D with D = radius + 1 + lag, so each item's dependencies --
+// (j-1, t') for |t' - t| <= radius -- come earlier; items of equal key are
+// independent.  The extra lag (twice the grid's blocks per term) lets term
+// j-1 run far enough ahead that an item's dependencies are normally finished
+// by the time it is handed out, so the resident blocks do not queue behind
+// one another.
+static int ensure_fused(tbpm_ctx *c, int J, int R, int radius, int maxB, int grid)
 {
     const int64_t T = c->H.n_rows / R;
     if (T >= ((int64_t)1 << 25) || J >= 128)
         return fail(c, TBPM_E_UNSUPPORTED, "fused step: too many tiles or terms");
-    if (c->items_key[0] != J || c->items_key[1] != R || c->items_key[2] != radius) {
+    const int D = radius + 1 + (2 * grid + J - 1) / J;
+    if (c->items_key[0] != J || c->items_key[1] != R || c->items_key[2] != D) {
         std::vector<int32_t> items;
         items.reserve((size_t)J * T);
-        const int64_t kmax = (T - 1) + (int64_t)(J - 1) * (radius + 1);
+        const int64_t kmax = (T - 1) + (int64_t)(J - 1) * D;
         for (int64_t k = 0; k <= kmax; ++k)
             for (int j = 0; j < J; ++j) {
-                const int64_t t = k - (int64_t)j * (radius + 1);
+                const int64_t t = k - (int64_t)j * D;
                 if (t >= 0 && t < T) items.push_back((int32_t)(((uint32_t)j << 25) | (uint32_t)t));
             }
         cudaFree(c->d_items);
@@ -718,7 +723,7 @@ static int ensure_fused(tbpm_ctx *c, int J, int R, int radius, int maxB)
         c->items_len = (int64_t)items.size();
         c->items_key[0] = J;
         c->items_key[1] = R;
-        c->items_key[2] = radius;
+        c->items_key[2] = D;
     }
     if (c->done_len < (int64_t)J * T) {
         cudaFree(c->d_done);
@@ -880,7 +885,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             const int radius = (int)((c->H.bandwidth + R - 1) / R);
             int maxB = 1;
             for (auto &g2 : c->groups) maxB = std::max(maxB, g2.B);
-            rc = ensure_fused(c, M - 1, R, radius, maxB);
+            rc = ensure_fused(c, M - 1, R, radius, maxB, fused_grid(fp32, g.B, c->num_sms));
             if (rc) return rc;
             std::vector<FusedTerm> tabs(3 * (size_t)kMaxTerms);
             for (int cur0 = 0; cur0 < 3; ++cur0) {

@@ -340,6 +340,34 @@ int fused_tile_rows(int fp32, int B, int log4_mult)
     return rows;
 }
 
+// Blocks of the cooperative grid (all resident).
+int fused_grid(int fp32, int B, int num_sms)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define TBPM_OCC(V, L, SPL) \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<V, L, SPL>, kFusedThreads, 0)
+    if (!fp32) {
+        switch (B) {
+        case 1: TBPM_OCC(double, 1, 1); break;
+        case 2: TBPM_OCC(double, 2, 1); break;
+        case 4: TBPM_OCC(double, 4, 1); break;
+        case 8: TBPM_OCC(double, 8, 1); break;
+        }
+    } else {
+        switch (B) {
+        case 1: TBPM_OCC(float, 1, 1); break;
+        case 2: TBPM_OCC(float, 1, 2); break;
+        case 4: TBPM_OCC(float, 2, 2); break;
+        case 8: TBPM_OCC(float, 4, 2); break;
+        case 16: TBPM_OCC(float, 8, 2); break;
+        }
+    }
+#undef TBPM_OCC
+    if (e != cudaSuccess || per_sm < 1) return 0;
+    return per_sm * num_sms;
+}
+
 cudaError_t launch_step_fused(const FusedArgs &f, int fp32, int B, int num_sms, cudaStream_t st)
 {
     if (!fp32) {

@@ -147,6 +147,7 @@ struct FusedArgs {
 
 cudaError_t launch_step_fused(const FusedArgs &f, int fp32, int B, int num_sms, cudaStream_t st);
 int fused_tile_rows(int fp32, int B, int log4_mult);
+int fused_grid(int fp32, int B, int num_sms);
 
 // Persistent TMA-staged term kernel (tma_kernels.cu); err bit 4 = bounded
 // wait expired.
