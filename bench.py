@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shape (profiling runs)")
     return ap.parse_args()
 
 
@@ -305,7 +307,10 @@ def run_gb300(args):
     prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets)
     prop.set_phase_states(d_th)
     for prec in legs:
-        tuned[prec] = prop.autotune(w.z, precision=prec, probe_steps=3)
+        if args.no_autotune:
+            tuned[prec] = {"group": "default", "threads": 256, "variant": 1}
+        else:
+            tuned[prec] = prop.autotune(w.z, precision=prec, probe_steps=3)
 
     def timed(precision):
         flags = N.TBPM_PROP_GRAPH if graph else N.TBPM_PROP_PROFILE
