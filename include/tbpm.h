@@ -43,7 +43,7 @@ extern "C" {
 #define TBPM_E_NONFINITE 6      /* NaN or Inf met in a state or a reduction */
 #define TBPM_E_TIMEOUT 7        /* a bounded device-side wait gave up (TMA kernel) */
 #define TBPM_E_STATE 8          /* call order: e.g. propagate before build */
-#define TBPM_E_UNSUPPORTED 9    /* valid request this build does not provide */
+#define TBPM_E_UNSUPPORTED 9    /* valid request the library does not provide */
 
 /* ---- precision of the propagation --------------------------------------- */
 #define TBPM_FP64 0  /* complex128 states, FP64 H~, FP64 reductions */
@@ -62,6 +62,9 @@ extern "C" {
 #define TBPM_BUILD_NO_FP64 2      /* keep only FP32 values (saves memory) */
 #define TBPM_BUILD_NO_FP32 4      /* keep only FP64 values */
 #define TBPM_BUILD_REORDER_RCM 8  /* reverse Cuthill-McKee row order per sample */
+#define TBPM_BUILD_NO_UNIFORM 16  /* do not use the one-value form when every hopping
+                                     is equal (by default the term kernels then skip
+                                     the value loads) */
 
 /* ---- flags of tbpm_propagate -------------------------------------------- */
 #define TBPM_PROP_PROFILE 1   /* time the kernels with CUDA events (tbpm_stats) */
@@ -226,7 +229,7 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
 /* Launch shape of the propagation kernels for one precision: states are
  * split into groups of power-of-two width <= max_group (FP64 <= 8,
  * FP32 <= 16), each group propagated as one blocked sparse product per term;
- * threads per block is a power of two in 64..1024; variant is a set of
+ * threads per block is 64, 128 or 256; variant is a set of
  * TBPM_VARIANT_* bits.  Chosen by tbpm_autotune or by hand.  Changing the
  * width or block size drops the current propagation buffers. */
 #define TBPM_VARIANT_ZIGZAG 1        /* alternate the row traversal direction per term,
@@ -254,8 +257,8 @@ int tbpm_set_norm_policy(tbpm_ctx *ctx, double renorm_fp32, double hard_fp32, do
 
 /* Autotuner: for the current Hamiltonian and states, time probe_steps
  * (1..64) steps of each candidate launch shape -- state-group width (the
- * block width of the blocked sparse product), threads per block (128, 256,
- * 512) and TBPM_VARIANT_* bits -- and keep the fastest as the context's
+ * block width of the blocked sparse product), threads per block (128, 256)
+ * and TBPM_VARIANT_* bits -- and keep the fastest as the context's
  * configuration for `precision`.  The chosen values are written to the
  * non-NULL out pointers.  The slice height is fixed at 32 rows (one warp's
  * rows share a slice).  Leaves no propagation to resume.

@@ -431,8 +431,8 @@ extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *
     in.d_sample_row_off = d_row_off;
     in.d_perm = d_perm;
     std::string msg;
-    rc = build_sell(in, !(flags & TBPM_BUILD_NO_FP64), !(flags & TBPM_BUILD_NO_FP32), c->H,
-                    c->st, msg);
+    rc = build_sell(in, !(flags & TBPM_BUILD_NO_FP64), !(flags & TBPM_BUILD_NO_FP32),
+                    !(flags & TBPM_BUILD_NO_UNIFORM), c->H, c->st, msg);
     cudaStreamSynchronize(c->st);
     release();
     if (rc) {
@@ -532,8 +532,8 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
     const int cap = precision == TBPM_FP64 ? 8 : 16;
     if (max_group < 1 || max_group > cap || (max_group & (max_group - 1)))
         return fail(c, TBPM_E_INVALID_ARG, "group width must be a power of two within the cap");
-    if (threads < 64 || threads > 1024 || (threads & (threads - 1)))
-        return fail(c, TBPM_E_INVALID_ARG, "threads must be a power of two in 64..1024");
+    if (threads < 64 || threads > 256 || (threads & (threads - 1)))
+        return fail(c, TBPM_E_INVALID_ARG, "threads must be 64, 128 or 256");
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
                                   (3 << kVariantFusedTileShift)) ||
         ((variant >> kVariantFusedTileShift) & 3) == 3)
@@ -853,6 +853,9 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         base.H = Hv;
         base.chunk_sample = c->H.chunk_sample;
         base.n_rows = c->H.n_rows;
+        base.uniform = c->H.uniform;
+        base.h_uniform = c->H.h_uniform;
+        base.h_uniform_f = (float)c->H.h_uniform;
         base.psi0 = g.psi0;
         base.partial = c->d_partial;
         base.block_partial = c->d_block_partial;
@@ -1432,7 +1435,7 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
     for (int B = cap; B >= 1; B /= 2)
         if (B <= c->n_states && (B >= 2 || c->n_states == 1)) widths.push_back(B);
     if (widths.empty()) widths.push_back(1);
-    const int thread_opts[] = {128, 256, 512};
+    const int thread_opts[] = {128, 256};
     const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints,
                                 kVariantTma, kVariantTma | kVariantZigZag, kVariantFused,
                                 kVariantFused | (1 << kVariantFusedTileShift),

@@ -237,6 +237,14 @@ __global__ void k_bond_rows(int64_t n_hop, const int64_t *hi, const int64_t *hj,
     rows[2 * b + 1] = user_to_row[hj[b]];
 }
 
+// Clears *same unless every hopping equals the first one (after scaling).
+__global__ void k_uniform(int64_t n_hop, const double *hv, double inv_s, int *same)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n_hop) return;
+    if (hv[b] * inv_s != hv[0] * inv_s) atomicAnd(same, 0);
+}
+
 __global__ void k_to_f32(int64_t n, const double *src, float *dst)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -262,8 +270,8 @@ void free_build(BuildOutput &b)
     b = BuildOutput();
 }
 
-int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
-               cudaStream_t st, std::string &msg)
+int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
+               BuildOutput &out, cudaStream_t st, std::string &msg)
 {
     const int T = 256;
     std::vector<int64_t> row_off(in.n_samples + 1);
@@ -362,6 +370,20 @@ int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
                        cudaMemcpyHostToDevice, st));
 
     out.n_hop = in.n_hop;
+    if (detect_uniform && in.n_hop > 0) {
+        // one hopping value everywhere (e.g. pristine or onsite-disordered
+        // lattices): the term kernels then need no value loads
+        CK(cudaMemsetAsync(err, 0xff, sizeof(int), st));
+        k_uniform<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_v, in.inv_s, err);
+        CK(cudaGetLastError());
+        int same = 0;
+        double v0 = 0.0;
+        CK(cudaMemcpyAsync(&same, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&v0, in.hop_v, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        out.uniform = same != 0;
+        out.h_uniform = v0 * in.inv_s;
+    }
     if (keep64 && in.n_hop > 0) {      // bond -> rows, for the adjoint's parameter gradients
         CK(cudaMalloc(&out.bond_rows, 2 * in.n_hop * sizeof(int32_t)));
         k_bond_rows<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j,

@@ -96,12 +96,14 @@ template <> struct Coef<double> {
     __device__ static double hi(const TermArgs &a) { return a.c_hi; }
     __device__ static double lo(const TermArgs &a) { return a.c_lo; }
     __device__ static const double *scale(const TermArgs &a) { return a.scale; }
+    __device__ static double hu(const TermArgs &a) { return a.h_uniform; }
 };
 template <> struct Coef<float> {
     __device__ static float g(const TermArgs &a) { return a.gamma_f; }
     __device__ static float hi(const TermArgs &a) { return a.c_hi_f; }
     __device__ static float lo(const TermArgs &a) { return a.c_lo_f; }
     __device__ static const float *scale(const TermArgs &a) { return a.scale_f; }
+    __device__ static float hu(const TermArgs &a) { return a.h_uniform_f; }
 };
 
 template <typename V, int L, int SPL>
@@ -136,18 +138,25 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
     for (int k = 0; k < w; k += 4) {
         int32_t c[4];
         V h[4];
+        bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const bool ok = k + u < w;
-            c[u] = ok ? __ldg(colp + (int64_t)(k + u) * kSliceRows) : (int32_t)r;
-            h[u] = ok ? __ldg(valp + (int64_t)(k + u) * kSliceRows) : (V)0;
+            ok[u] = k + u < w;
+            c[u] = ok[u] ? __ldg(colp + (int64_t)(k + u) * kSliceRows) : (int32_t)r;
+            if (a.uniform) {
+                // one value for all entries; padded slots (col == own row) add nothing
+                ok[u] = ok[u] && c[u] != (int32_t)r;
+                h[u] = Coef<V>::hu(a);
+            } else {
+                h[u] = ok[u] ? __ldg(valp + (int64_t)(k + u) * kSliceRows) : (V)0;
+            }
         }
         Cv<V, SPL> xv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) xv[u] = ld_ro<V, L, SPL>(a.x, c[u], l);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (k + u < w) {
+            if (ok[u]) {
 #pragma unroll
                 for (int j = 0; j < SPL; ++j) {
                     y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
@@ -190,8 +199,10 @@ __device__ __forceinline__ int64_t block_in_order(const TermArgs &a)
     return a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
 }
 
+// FP32: at most 40 registers (12 blocks of 128 threads per SM) -- the kernel
+// is latency-bound, so residency matters; FP64: unconstrained.
 template <typename V, int L, int SPL>
-__global__ void __launch_bounds__(1024) k_term(TermArgs a)
+__global__ void __launch_bounds__(256, sizeof(V) == 4 ? 6 : 1) k_term(TermArgs a)
 {
     const int64_t t = block_in_order(a) * blockDim.x + threadIdx.x;
     const int64_t r = t / L;

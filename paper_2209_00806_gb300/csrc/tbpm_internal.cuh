@@ -56,6 +56,9 @@ struct TermArgs {
     int64_t n_rows;
     int variant;          // kVariant* bits
     int reverse;          // walk the blocks from the end (zig-zag order)
+    int uniform;          // every off-diagonal value equals h_uniform (no value loads)
+    double h_uniform;
+    float h_uniform_f;
     // closing term only (H.col == nullptr: reduce `out` without computing it)
     const void *psi0;
     double *partial;        // [n_chunks][B][3]
@@ -194,12 +197,14 @@ struct BuildOutput {
     double gershgorin = 0.0;
     int max_width = 0;
     int64_t bandwidth = 0;           // max |col - row| over the stored entries
+    int uniform = 0;                 // all off-diagonal values are equal
+    double h_uniform = 0.0;          // that value (H~ units)
 };
 
 // Returns TBPM status; fills msg on failure.  Allocations in `out` are owned
 // by the caller afterwards (freed with free_build).
-int build_sell(const BuildInput &in, int keep64, int keep32, BuildOutput &out,
-               cudaStream_t st, std::string &msg);
+int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
+               BuildOutput &out, cudaStream_t st, std::string &msg);
 void free_build(BuildOutput &b);
 
 // Thread-local message returned by tbpm_last_error(NULL) (api.cu).
