@@ -243,6 +243,8 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
                                         so intermediate vectors stay in L2; needs a
                                         banded row order (TBPM_BUILD_REORDER_RCM) */
 #define TBPM_VARIANT_FUSED_TILE(k) ((k) << 4)  /* fused tile rows x 4^k, k = 0..2 */
+#define TBPM_VARIANT_WIDE 64         /* term kernel with 32-byte lanes (one thread per
+                                        row for 4 FP32 or 2 FP64 states) */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
 

@@ -535,7 +535,7 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
     if (threads < 64 || threads > 256 || (threads & (threads - 1)))
         return fail(c, TBPM_E_INVALID_ARG, "threads must be 64, 128 or 256");
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
-                                  (3 << kVariantFusedTileShift)) ||
+                                  (3 << kVariantFusedTileShift) | kVariantWide) ||
         ((variant >> kVariantFusedTileShift) & 3) == 3)
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
     if (c->max_group[precision] != max_group || c->threads[precision] != threads) free_groups(c);
@@ -1093,8 +1093,11 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         double vb = 0.0;
         for (auto &g : c->groups) vb += (double)c->n_orb * 4.0 * g.B * cs;
         vb /= c->groups.size();
+        // matrix: a column (and a value, unless one value serves all) per
+        // stored entry, and the diagonal
         const double valb = fp32 ? 4.0 : 8.0;
-        S.bytes_term = vb + (double)c->H.nnz_true * (4.0 + valb) + (double)c->n_orb * valb;
+        const double entry = 4.0 + (c->H.uniform ? 0.0 : valb);
+        S.bytes_term = vb + (double)c->H.nnz_true * entry + (double)c->n_orb * valb;
     }
     if (profile) {
         float ms = 0.f;
@@ -1437,6 +1440,7 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
     if (widths.empty()) widths.push_back(1);
     const int thread_opts[] = {128, 256};
     const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints,
+                                kVariantZigZag | kVariantWide,
                                 kVariantTma, kVariantTma | kVariantZigZag, kVariantFused,
                                 kVariantFused | (1 << kVariantFusedTileShift),
                                 kVariantFused | (2 << kVariantFusedTileShift)};

@@ -27,10 +27,17 @@
 namespace tbpm {
 namespace {
 
+// A lane moves 16 bytes (one complex128, or two complex64) in the default
+// layout, or 32 bytes (two of those) in the wide-lane variant.
+struct W32F { float4 a, b; };
+struct W32D { double2 a, b; };
+
 template <typename V, int SPL> struct LaneT;
 template <> struct LaneT<double, 1> { typedef double2 type; };
+template <> struct LaneT<double, 2> { typedef W32D type; };
 template <> struct LaneT<float, 1> { typedef float2 type; };
 template <> struct LaneT<float, 2> { typedef float4 type; };
+template <> struct LaneT<float, 4> { typedef W32F type; };
 
 template <typename V, int SPL> struct Cv {
     V re[SPL], im[SPL];
@@ -42,11 +49,80 @@ __device__ __forceinline__ void unpack(const float4 &v, Cv<float, 2> &o)
 {
     o.re[0] = v.x; o.im[0] = v.y; o.re[1] = v.z; o.im[1] = v.w;
 }
+__device__ __forceinline__ void unpack(const W32D &v, Cv<double, 2> &o)
+{
+    o.re[0] = v.a.x; o.im[0] = v.a.y; o.re[1] = v.b.x; o.im[1] = v.b.y;
+}
+__device__ __forceinline__ void unpack(const W32F &v, Cv<float, 4> &o)
+{
+    o.re[0] = v.a.x; o.im[0] = v.a.y; o.re[1] = v.a.z; o.im[1] = v.a.w;
+    o.re[2] = v.b.x; o.im[2] = v.b.y; o.re[3] = v.b.z; o.im[3] = v.b.w;
+}
 __device__ __forceinline__ double2 pack(const Cv<double, 1> &o) { return make_double2(o.re[0], o.im[0]); }
 __device__ __forceinline__ float2 pack(const Cv<float, 1> &o) { return make_float2(o.re[0], o.im[0]); }
 __device__ __forceinline__ float4 pack(const Cv<float, 2> &o)
 {
     return make_float4(o.re[0], o.im[0], o.re[1], o.im[1]);
+}
+__device__ __forceinline__ W32D pack(const Cv<double, 2> &o)
+{
+    W32D v;
+    v.a = make_double2(o.re[0], o.im[0]);
+    v.b = make_double2(o.re[1], o.im[1]);
+    return v;
+}
+__device__ __forceinline__ W32F pack(const Cv<float, 4> &o)
+{
+    W32F v;
+    v.a = make_float4(o.re[0], o.im[0], o.re[1], o.im[1]);
+    v.b = make_float4(o.re[2], o.im[2], o.re[3], o.im[3]);
+    return v;
+}
+
+// 16-byte lanes load as one vector access, 32-byte lanes as two.
+template <typename T> __device__ __forceinline__ T lane_ldg(const T *p) { return __ldg(p); }
+template <typename T> __device__ __forceinline__ T lane_ldcs(const T *p) { return __ldcs(p); }
+template <typename T> __device__ __forceinline__ T lane_ld(const T *p) { return *p; }
+template <typename T> __device__ __forceinline__ void lane_st(T *p, const T &v) { *p = v; }
+template <> __device__ __forceinline__ W32F lane_ldg(const W32F *p)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    W32F v; v.a = __ldg(q); v.b = __ldg(q + 1); return v;
+}
+template <> __device__ __forceinline__ W32D lane_ldg(const W32D *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    W32D v; v.a = __ldg(q); v.b = __ldg(q + 1); return v;
+}
+template <> __device__ __forceinline__ W32F lane_ldcs(const W32F *p)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    W32F v; v.a = __ldcs(q); v.b = __ldcs(q + 1); return v;
+}
+template <> __device__ __forceinline__ W32D lane_ldcs(const W32D *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    W32D v; v.a = __ldcs(q); v.b = __ldcs(q + 1); return v;
+}
+template <> __device__ __forceinline__ W32F lane_ld(const W32F *p)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    W32F v; v.a = q[0]; v.b = q[1]; return v;
+}
+template <> __device__ __forceinline__ W32D lane_ld(const W32D *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    W32D v; v.a = q[0]; v.b = q[1]; return v;
+}
+template <> __device__ __forceinline__ void lane_st(W32F *p, const W32F &v)
+{
+    float4 *q = reinterpret_cast<float4 *>(p);
+    q[0] = v.a; q[1] = v.b;
+}
+template <> __device__ __forceinline__ void lane_st(W32D *p, const W32D &v)
+{
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = v.a; q[1] = v.b;
 }
 
 // Load the lane data of row `r` through the read-only path.
@@ -55,7 +131,7 @@ __device__ __forceinline__ Cv<V, SPL> ld_ro(const void *base, int64_t r, int l)
 {
     typedef typename LaneT<V, SPL>::type Lane;
     Cv<V, SPL> o;
-    unpack(__ldg(reinterpret_cast<const Lane *>(base) + r * L + l), o);
+    unpack(lane_ldg(reinterpret_cast<const Lane *>(base) + r * L + l), o);
     return o;
 }
 template <typename V, int L, int SPL>
@@ -63,7 +139,7 @@ __device__ __forceinline__ Cv<V, SPL> ld(const void *base, int64_t r, int l)
 {
     typedef typename LaneT<V, SPL>::type Lane;
     Cv<V, SPL> o;
-    unpack(reinterpret_cast<const Lane *>(base)[r * L + l], o);
+    unpack(lane_ld(reinterpret_cast<const Lane *>(base) + r * L + l), o);
     return o;
 }
 // Own-row stream read with an evict-first hint (kept out of the way of the
@@ -73,14 +149,14 @@ __device__ __forceinline__ Cv<V, SPL> ld_cs(const void *base, int64_t r, int l)
 {
     typedef typename LaneT<V, SPL>::type Lane;
     Cv<V, SPL> o;
-    unpack(__ldcs(reinterpret_cast<const Lane *>(base) + r * L + l), o);
+    unpack(lane_ldcs(reinterpret_cast<const Lane *>(base) + r * L + l), o);
     return o;
 }
 template <typename V, int L, int SPL>
 __device__ __forceinline__ void st(void *base, int64_t r, int l, const Cv<V, SPL> &v)
 {
     typedef typename LaneT<V, SPL>::type Lane;
-    reinterpret_cast<Lane *>(base)[r * L + l] = pack(v);
+    lane_st(reinterpret_cast<Lane *>(base) + r * L + l, pack(v));
 }
 
 // out = c psi + gamma (-i) (H~ x) + z for lane l of row r.  The own-row
@@ -199,10 +275,11 @@ __device__ __forceinline__ int64_t block_in_order(const TermArgs &a)
     return a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
 }
 
-// FP32: at most 40 registers (12 blocks of 128 threads per SM) -- the kernel
-// is latency-bound, so residency matters; FP64: unconstrained.
+// FP32: at most 40 registers (12 blocks of 128 threads per SM; 80 for the
+// wide lanes) -- the kernel is latency-bound, so residency matters; FP64:
+// unconstrained.
 template <typename V, int L, int SPL>
-__global__ void __launch_bounds__(256, sizeof(V) == 4 ? 6 : 1) k_term(TermArgs a)
+__global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 3) : 1) k_term(TermArgs a)
 {
     const int64_t t = block_in_order(a) * blockDim.x + threadIdx.x;
     const int64_t r = t / L;
@@ -489,6 +566,22 @@ template <bool FINAL>
 cudaError_t dispatch(const TermArgs &a, int fp32, int B, int threads, bool compute,
                      cudaStream_t st)
 {
+    if (!FINAL && (a.variant & kVariantWide)) {
+        // one thread per row and 32-byte lanes: fewer lanes share the index loads
+        if (!fp32) {
+            switch (B) {
+            case 2: return launch_term_t<double, 1, 2>(a, threads, st);
+            case 4: return launch_term_t<double, 2, 2>(a, threads, st);
+            case 8: return launch_term_t<double, 4, 2>(a, threads, st);
+            }
+        } else {
+            switch (B) {
+            case 4: return launch_term_t<float, 1, 4>(a, threads, st);
+            case 8: return launch_term_t<float, 2, 4>(a, threads, st);
+            case 16: return launch_term_t<float, 4, 4>(a, threads, st);
+            }
+        }
+    }
 #define TBPM_CASE(V, L, SPL)                                              \
     return FINAL ? launch_final_t<V, L, SPL>(a, threads, compute, st)    \
                  : launch_term_t<V, L, SPL>(a, threads, st)

@@ -28,6 +28,7 @@ constexpr int kVariantStreamHints = 2;  // evict-first loads of the own-row stre
 constexpr int kVariantTma = 4;          // persistent TMA-staged term kernel
 constexpr int kVariantFused = 8;        // all terms of a step in one wavefront launch
 constexpr int kVariantFusedTileShift = 4;  // bits 4-5: fused tile rows x 4^k
+constexpr int kVariantWide = 64;        // term kernel with 32-byte lanes
 
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.

@@ -53,7 +53,7 @@ def test_gpu_fp64_disordered_vacancies_several_groups(tb):
 
 
 @pytest.mark.parametrize("cfg", [(1, 64, 0), (2, 128, 1), (8, 256, 3), (4, 256, 2), (4, 256, 4),
-                                 (8, 256, 5), (1, 256, 4)])
+                                 (8, 256, 5), (1, 256, 4), (4, 128, 65), (2, 64, 64)])
 def test_gpu_fp64_ragged_rows_launch_shapes(tb, cfg):
     smp = lattice.random_graph(3001, 9000, seed=3, onsite_w=2.0)   # degrees 0 .. ~15
     H = exact.dense_h(smp)
@@ -94,7 +94,7 @@ def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
 
 
 @pytest.mark.parametrize("cfg", [(16, 128, 3), (4, 256, 1), (2, 64, 0), (16, 256, 4), (4, 256, 5),
-                                 (2, 256, 4), (1, 256, 0)])
+                                 (2, 256, 4), (1, 256, 0), (16, 128, 65), (4, 128, 64)])
 def test_gpu_fp32_launch_shapes(tb, cfg):
     smp = lattice.random_graph(2500, 7000, seed=9, onsite_w=2.0)
     H = exact.dense_h(smp)
@@ -113,7 +113,7 @@ def test_gpu_autotune_picks_a_valid_shape(tb):
         p.set_phase_states(th)
         best = p.autotune(Z, precision=1, probe_steps=2)
         assert best["group"] in (2, 4) and best["threads"] in (128, 256)
-        assert best["variant"] in (0, 1, 3, 4, 5, 8) and best["ms_per_step"] > 0
+        assert best["variant"] in (0, 1, 3, 4, 5, 8, 24, 40, 65) and best["ms_per_step"] > 0
         c = p.propagate(Z, 30, 1)
     ref = run_oracle(smp, 9.5, th, 30)
     assert np.max(np.abs(c[0] - ref)) < 2e-5
@@ -210,7 +210,7 @@ def test_gpu_tma_kernel_is_bit_identical(tb, prec):
     smp = lattice.graphene(33, 31, pbc=True, seed=6, onsite_w=1.0, vacancy_frac=0.02)
     th = rng.phases(12, 4, smp.n_orb)
     outs = []
-    for variant in (0, 4, 5):
+    for variant in (0, 4, 5, 65):
         c, _, phi, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, cfg=(4, 256, variant),
                                flags=2 if variant == 5 else 0)
         outs.append((c, phi))
