@@ -54,7 +54,9 @@ struct tbpm_ctx {
     int prec = -1;               // precision of the group buffers
     int max_group[2] = {8, 16};  // widest state group per precision
     int threads[2] = {256, 256}; // threads per block per precision
-    int variant[2] = {kVariantZigZag, kVariantZigZag};  // term-kernel launch variants
+    // term-kernel launch variants (FP64, FP32): the fastest on GB300 for
+    // graphene-like lattices; tbpm_autotune re-checks for the actual matrix
+    int variant[2] = {kVariantZigZag, kVariantZigZag | kVariantWide};
     int num_sms = 0;
     double renorm_fp32 = 1e-5, hard_fp32 = 1e-2, hard_fp64 = 1e-6;   // norm policy
     std::vector<Group> groups;
