@@ -40,11 +40,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="disordered",
-                    choices=["disordered", "batched", "graphene_dos", "differentiable"],
+                    choices=["disordered", "batched", "graphene_dos", "differentiable", "tbg"],
                     help="disordered: 2048^2 disordered graphene, 4 states, 1024 steps "
                          "(default, the headline); batched: 32 uneven samples x 16 states, "
                          "512 steps; graphene_dos: 64x64 pristine graphene, 1 state, 1024 steps; "
-                         "differentiable: 512^2 graphene, DOS loss, FP64 forward + adjoint")
+                         "differentiable: 512^2 graphene, DOS loss, FP64 forward + adjoint; "
+                         "tbg: twisted bilayer flake (--side nm), 6 A cutoff, 8 states")
+    ap.add_argument("--side", type=float, default=200.0, help="tbg flake side in nm")
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
@@ -74,6 +76,8 @@ def workload_inputs(args, rank):
         w = workloads.batched_graphene()
     elif args.workload == "graphene_dos":
         w = workloads.graphene_dos(n_steps=args.time_steps)
+    elif args.workload == "tbg":
+        w = workloads.twisted_bilayer_flake(side_nm=args.side, n_steps=args.time_steps)
     else:
         w = workloads.disordered_graphene(L=args.L, n_steps=args.time_steps)
     # weak scaling: rank r propagates its own states (seeds offset by the rank)
@@ -99,6 +103,12 @@ def config_dict(w, args, world):
     elif args.workload == "graphene_dos":
         d.update(workload="graphene_dos_64x64", onsite_disorder_eV="none",
                  l2="working set inside L2 (latency-bound; no L2 flush)")
+    elif args.workload == "tbg":
+        d.update(workload=f"twisted_bilayer_{args.side:g}nm", twist_deg=1.05, cutoff_A=6,
+                 entries_per_row=round(2 * w.sample.n_hop / w.sample.n_orb, 1),
+                 row_order="reverse Cuthill-McKee (interleaves the layers)",
+                 l2=f"inputs larger than L2 (state vectors {cs32:.0f} MB FP32, matrix "
+                    f"{w.sample.n_hop * 2 * 8 / 1e6:.0f} MB)")
     else:
         d.update(workload=f"disordered_graphene_{args.L}x{args.L}",
                  onsite_disorder_eV="U[-0.5,0.5]", vacancies="1%",
@@ -286,11 +296,12 @@ def run_gb300(args):
     corr_d = torch.empty((NS, S, NT + 1), dtype=torch.complex128, device=dev)
     # precisions measured per workload: the first one is the headline `value`
     legs = {"disordered": [N.TBPM_FP32, N.TBPM_FP64], "batched": [N.TBPM_FP32],
-            "graphene_dos": [N.TBPM_FP64]}[args.workload]
+            "graphene_dos": [N.TBPM_FP64], "tbg": [N.TBPM_FP32]}[args.workload]
+    bflags = N.TBPM_BUILD_REORDER_RCM if args.workload == "tbg" else 0
     graph = args.workload == "graphene_dos"     # launch-latency bound: replay step graphs
 
     def one_step(precision, flags):
-        prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets)
+        prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets, flags=bflags)
         prop.set_phase_states(d_th)
         prop.propagate(w.z, NT, precision, out=corr_d, flags=flags)
         c = corr_d.mean(dim=1).cpu().numpy()          # state average per sample
@@ -304,7 +315,7 @@ def run_gb300(args):
 
     # autotune the launch shape once per precision (outside the timed region)
     tuned = {}
-    prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets)
+    prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets, flags=bflags)
     prop.set_phase_states(d_th)
     for prec in legs:
         if args.no_autotune:
@@ -379,7 +390,7 @@ def run_gb300(args):
         def host_step():
             N.tbpm_build_hamiltonian(prop.ctx, smp.n_orb, h_on.data_ptr(), smp.n_hop,
                                      h_hi.data_ptr(), h_hj.data_ptr(), h_hv.data_ptr(), w.s, NS,
-                                     offs, N.TBPM_HOST, 0)
+                                     offs, N.TBPM_HOST, bflags)
             N.tbpm_set_phase_states(prop.ctx, S, h_th.data_ptr(), N.TBPM_HOST)
             N.tbpm_propagate(prop.ctx, w.z, NT, head, h_c.data_ptr(), N.TBPM_HOST,
                              N.TBPM_PROP_GRAPH if graph else 0)

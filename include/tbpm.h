@@ -71,8 +71,9 @@ extern "C" {
 #define TBPM_PROP_GRAPH 2     /* replay each time step as a captured CUDA graph */
 #define TBPM_PROP_RESUME 4    /* continue from the current states instead of
                                  restarting from psi0; C is still <psi0|phi> */
-#define TBPM_PROP_PERSISTENT 8 /* one cooperative launch per time step with a
-                                  bounded grid barrier between terms */
+#define TBPM_PROP_PERSISTENT 8 /* one cooperative launch per time step: the
+                                  wavefront-fused step (TBPM_VARIANT_FUSED) for
+                                  this call, with bounded dependency waits */
 
 typedef struct tbpm_ctx tbpm_ctx;
 
@@ -90,11 +91,15 @@ typedef struct tbpm_stats {
     double gershgorin;       /* Gershgorin bound of H~ = H / s (dimensionless) */
     double ms_total;         /* device time of the last call (PROFILE) */
     double ms_term_avg;      /* average duration of one interior Chebyshev
-                                term kernel (PROFILE) */
+                                term kernel (PROFILE); with the fused step,
+                                its time divided by the M-1 terms */
     double ms_final_avg;     /* average duration of the closing term kernel */
     double ms_reduce_avg;    /* average duration of the correlation reduction */
     int64_t term_launches;   /* interior term launches that were timed */
-    double bytes_term;       /* algorithmic bytes of one interior term launch */
+    double bytes_term;       /* algorithmic bytes of one interior term launch:
+                                4 state vectors, a column per stored entry
+                                (plus a value unless one value serves all),
+                                the diagonal */
     double max_norm_drift;   /* max over steps and states of |<phi|phi> - 1| */
 } tbpm_stats;
 

@@ -53,7 +53,7 @@ struct tbpm_ctx {
     // propagation state
     int prec = -1;               // precision of the group buffers
     int max_group[2] = {8, 16};  // widest state group per precision
-    int threads[2] = {256, 256}; // threads per block per precision
+    int threads[2] = {128, 128}; // threads per block per precision
     // term-kernel launch variants (FP64, FP32): the fastest on GB300 for
     // graphene-like lattices; tbpm_autotune re-checks for the actual matrix
     int variant[2] = {kVariantZigZag, kVariantZigZag | kVariantWide};
@@ -778,9 +778,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         return fail(c, TBPM_E_STATE, "nothing to resume in this precision");
     const bool profile = (flags & TBPM_PROP_PROFILE) != 0;
     const bool graph = (flags & TBPM_PROP_GRAPH) != 0 && !profile;
-    const bool fused = (c->variant[precision] & kVariantFused) != 0;
-    if (flags & TBPM_PROP_PERSISTENT)
-        return fail(c, TBPM_E_UNSUPPORTED, "persistent mode is not built");
+    const bool fused = (c->variant[precision] & kVariantFused) != 0 ||
+                       (flags & TBPM_PROP_PERSISTENT) != 0;
 
     std::vector<double> J(kMaxTerms);
     int M = 0;

@@ -189,3 +189,47 @@ def concat(samples: list[Sample]) -> tuple[Sample, np.ndarray]:
     hv = np.concatenate([s.hop_v for s in samples])
     return Sample(n_orb=n, onsite=onsite if any_onsite else None, hop_i=hi, hop_j=hj,
                   hop_v=hv, meta=dict(kind="batch", n_samples=len(samples))), offs
+
+
+def twisted_bilayer(side_nm: float, theta_deg: float = 1.05, cutoff_nm: float = 0.6,
+                    seed: int = 0) -> Sample:
+    """Square flake of twisted bilayer graphene with open boundaries.
+
+    Two honeycomb layers (a = 0.246 nm, C-C 0.142 nm) stacked AA at the
+    origin, the bottom at z = 0 and the top at z = 0.335 nm rotated by theta
+    about the origin; both layers clipped to [-side/2, side/2]^2.  Every pair
+    closer than the cutoff is a bond with the two-centre p_z form
+        t(d) = Vpp_pi (1 - (z/d)^2) + Vpp_sigma (z/d)^2,
+        Vpp_pi = -2.7 exp(-(d - 0.142)/0.045) eV,
+        Vpp_sigma = 0.48 exp(-(d - 0.335)/0.045) eV  (d, z in nm),
+    and zero onsite energy.  Orbitals are numbered layer by layer (bottom
+    first), so interlayer partners are far apart in the numbering.
+    """
+    from scipy.spatial import cKDTree
+    half = 0.5 * side_nm
+    reach = int(np.ceil(side_nm / 0.123)) + 4
+    n = np.arange(-reach, reach + 1)
+    n1, n2 = np.meshgrid(n, n, indexing="ij")
+    origin = n1.reshape(-1, 1) * A1 + n2.reshape(-1, 1) * A2
+    base = np.concatenate([origin, origin + (A1 + A2) / 3.0])
+    layers = []
+    for k, ang in enumerate((0.0, np.deg2rad(theta_deg))):
+        c, s_ = np.cos(ang), np.sin(ang)
+        p = base @ np.array([[c, s_], [-s_, c]])
+        p = p[(np.abs(p[:, 0]) <= half) & (np.abs(p[:, 1]) <= half)]
+        layers.append(np.column_stack([p, np.full(p.shape[0], 0.335 * k)]))
+    pos = np.concatenate(layers)
+    pairs = cKDTree(pos).query_pairs(cutoff_nm, output_type="ndarray")
+    d_vec = pos[pairs[:, 1]] - pos[pairs[:, 0]]
+    d = np.linalg.norm(d_vec, axis=1)
+    zz = np.abs(d_vec[:, 2])
+    r2 = (zz / d) ** 2
+    vpi = -2.7 * np.exp(-(d - 0.142) / 0.045)
+    vsig = 0.48 * np.exp(-(d - 0.335) / 0.045)
+    hv = vpi * (1.0 - r2) + vsig * r2
+    return Sample(n_orb=pos.shape[0], onsite=None,
+                  hop_i=np.ascontiguousarray(pairs[:, 0].astype(np.int64)),
+                  hop_j=np.ascontiguousarray(pairs[:, 1].astype(np.int64)),
+                  hop_v=np.ascontiguousarray(hv), pos=pos[:, :2],
+                  meta=dict(kind="twisted_bilayer", side_nm=side_nm, theta_deg=theta_deg,
+                            cutoff_nm=cutoff_nm, n_bottom=layers[0].shape[0]))

@@ -122,3 +122,16 @@ def pristine_like(w: Workload) -> Workload:
     return Workload(w.name + "_pristine", smp, w.offsets.copy(), w.s, w.z, w.n_states,
                     w.n_steps, w.n_energies, w.e_range, w.seed, list(w.sample_seeds),
                     dict(w.info))
+
+
+def twisted_bilayer_flake(side_nm: float = 100.0, n_states: int = 8, n_steps: int = 1024,
+                          n_energies: int = 4096) -> Workload:
+    """Twisted bilayer graphene, 1.05 degrees, square open flake of side
+    `side_nm` (the 1.2 um flake scaled down), 6 Angstrom Slater-Koster p_z
+    cutoff (about 66 entries per row), onsite 0, s = 12 eV (the spectral
+    radius of this hopping form exceeds 10 eV), 8 states."""
+    seed = master_seed(5)
+    smp = lattice.twisted_bilayer(side_nm, seed=seed)
+    return Workload("twisted_bilayer", smp, np.array([0, smp.n_orb], dtype=np.int64), 12.0,
+                    Z_STEP, n_states, n_steps, n_energies, (-12.0, 12.0), seed, [seed],
+                    dict(side_nm=side_nm))

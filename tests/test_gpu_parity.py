@@ -250,6 +250,14 @@ def test_gpu_fused_step(tb, prec, kind):
             assert np.max(np.abs(fused[k] - ref)) < (1e-10 if prec == 0 else 2e-5)
 
 
+def test_gpu_persistent_flag_runs_the_fused_step(tb):
+    smp = lattice.graphene(24, 24, pbc=True, seed=9, onsite_w=1.0)
+    th = rng.phases(6, 4, smp.n_orb)
+    a, _, pa, _ = run_gpu(tb, smp, 9.5, th, 20, precision=0)
+    b, _, pb, _ = run_gpu(tb, smp, 9.5, th, 20, precision=0, flags=8)
+    assert np.array_equal(pa, pb) and np.max(np.abs(a - b)) < 1e-13
+
+
 def test_gpu_fused_step_graph_replay(tb):
     smp = lattice.graphene(30, 30, pbc=True, seed=2, onsite_w=1.0)
     th = rng.phases(5, 4, smp.n_orb)
@@ -351,3 +359,23 @@ def test_gpu_ldos_single_site_states(tb):
     for k, i in enumerate(sites):
         ed = np.exp(-1j * np.outer(times, E)) @ (np.abs(U[i]) ** 2)
         assert np.max(np.abs(c[0, k] - ed)) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gpu_twisted_bilayer_wide_rows(tb, prec):
+    """Twisted bilayer flake: ~63 entries per row, asymmetric spectrum
+    (s = 12 eV), layer-by-layer numbering; with and without RCM order, plain,
+    wide-lane and TMA kernels, against the oracle and exact diagonalisation."""
+    w = workloads.twisted_bilayer_flake(side_nm=5.0, n_steps=60)
+    smp = w.sample
+    th = w.thetas()[0][:3]
+    ref = run_oracle(smp, w.s, th, w.n_steps)
+    times = w.tau * np.arange(w.n_steps + 1)
+    ed = exact.ed_corr(smp, oracle.phase_states(th)[0], times)
+    assert np.max(np.abs(ref[0] - ed)) < 1e-11
+    tol = 1e-10 if prec == 0 else 2e-5
+    for bflags in (0, 8):
+        for cfg in ((2, 128, 1), (2, 128, 65), (2, 128, 4)):
+            c, st, _, _ = run_gpu(tb, smp, w.s, th, w.n_steps, precision=prec, bflags=bflags,
+                                  cfg=cfg)
+            assert np.max(np.abs(c[0] - ref)) < tol, (bflags, cfg)
