@@ -442,8 +442,20 @@ def run_gb300(args):
             r64 = runs[N.TBPM_FP64]
             en, d32 = r0["res"]
             _, d64 = r64["res"]
+            # the FP64 term is bound by GB300's FP64 pipe: 10 flops per lane-row
+            # (diagonal 2, combine 8) plus 4 per stored entry
+            st64 = r64["stats"]
+            flops = float(smp.n_orb * S * 10 + st64["nnz_true"] * S * 4)
+            alu = None
+            if r64["ms_term"]:
+                ach = flops / (r64["ms_term"] * 1e-3) / 1e9
+                alu = {"bound": "alu", "achieved": ach, "peak": 1250.0, "unit": "GFLOP/s",
+                       "frac": ach / 1250.0, "traffic": None,
+                       "peak_source": "nominal FP64 FMA rate of GB300 (1.25 TFLOP/s)",
+                       "flops_per_launch": flops}
             line["fp64_form"] = {"value": vals[N.TBPM_FP64], "ms_per_step": r64["ms"] / args.steps,
                                  "dtype": "f64", "roofline": roofline(r64, "fp64"),
+                                 "roofline_alu": alu,
                                  "clocks": r64["clocks"], "max_norm_drift": r64["drift"]}
             line["speedup_fp32_over_fp64"] = vals[head] / vals[N.TBPM_FP64]
             line["dos_l1_fp32_vs_fp64"] = float(np.max(np.sum(np.abs(d32 - d64), axis=1)) *

@@ -65,6 +65,9 @@ extern "C" {
 #define TBPM_BUILD_NO_UNIFORM 16  /* do not use the one-value form when every hopping
                                      is equal (by default the term kernels then skip
                                      the value loads) */
+#define TBPM_BUILD_COMPLEX_HOPS 32 /* hop_v holds complex hoppings, (re, im) double
+                                      pairs (complex128): Peierls phases of a
+                                      magnetic field (Sec. 2.1) */
 
 /* ---- flags of tbpm_propagate -------------------------------------------- */
 #define TBPM_PROP_PROFILE 1   /* time the kernels with CUDA events (tbpm_stats) */
@@ -121,14 +124,18 @@ const char *tbpm_last_error(const tbpm_ctx *ctx);
 
 /* a1. Lattice -> Hamiltonian (Sec. 2.1, Eq. ham_mat_finite, with the hopping
  * convention of Sec. 4.1: a bond (i, j, t) is the matrix element
- * <phi_i|h|phi_j> = t, the conjugate element H_ji = t is implied), rescaled
+ * <phi_i|h|phi_j> = t, the conjugate element H_ji = conj(t) is implied), rescaled
  * to H~ = H / s (Sec. 2.2).
  *   n_orb          orbitals, 1 .. 2^31 - 1 in total
  *   onsite         [n_orb] eps_i in eV, host or device, or NULL for zeros
  *   n_hop, hop_i, hop_j, hop_v
  *                  [n_hop] bonds, int64 indices and real hoppings in eV, host
  *                  or device; i != j, both in the same sample.  A pair listed
- *                  twice adds up.
+ *                  twice adds up.  With TBPM_BUILD_COMPLEX_HOPS hop_v is
+ *                  [n_hop] complex128 (re, im pairs), H_ij = t, H_ji = conj(t);
+ *                  such a Hamiltonian runs the plain term kernels (no TMA,
+ *                  wide-lane or fused variants; TBPM_PROP_PERSISTENT and the
+ *                  adjoint return TBPM_E_UNSUPPORTED).
  *   s              rescale factor in eV, > 0
  *   n_samples      independent samples packed block-diagonally (>= 1)
  *   sample_offsets [n_samples + 1] host int64, orbitals of sample k are

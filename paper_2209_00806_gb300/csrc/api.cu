@@ -398,7 +398,9 @@ extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *
     rc = stage(c, onsite, n_orb, where, const_cast<double **>(&d_on), &o1);
     if (!rc) rc = stage(c, hop_i, n_hop, where, const_cast<int64_t **>(&d_hi), &o2);
     if (!rc) rc = stage(c, hop_j, n_hop, where, const_cast<int64_t **>(&d_hj), &o3);
-    if (!rc) rc = stage(c, hop_v, n_hop, where, const_cast<double **>(&d_hv), &o4);
+    const bool cplx = (flags & TBPM_BUILD_COMPLEX_HOPS) != 0;
+    if (!rc) rc = stage(c, hop_v, (size_t)n_hop * (cplx ? 2 : 1), where,
+                        const_cast<double **>(&d_hv), &o4);
     int64_t *d_off = nullptr, *d_row_off = nullptr;
     int32_t *d_perm = nullptr;
     if (!rc) rc = dalloc(c, &d_off, n_samples + 1);
@@ -432,6 +434,7 @@ extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *
     in.d_sample_off = d_off;
     in.d_sample_row_off = d_row_off;
     in.d_perm = d_perm;
+    in.cplx = cplx ? 1 : 0;
     std::string msg;
     rc = build_sell(in, !(flags & TBPM_BUILD_NO_FP64), !(flags & TBPM_BUILD_NO_FP32),
                     !(flags & TBPM_BUILD_NO_UNIFORM), c->H, c->st, msg);
@@ -778,8 +781,10 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         return fail(c, TBPM_E_STATE, "nothing to resume in this precision");
     const bool profile = (flags & TBPM_PROP_PROFILE) != 0;
     const bool graph = (flags & TBPM_PROP_GRAPH) != 0 && !profile;
-    const bool fused = (c->variant[precision] & kVariantFused) != 0 ||
-                       (flags & TBPM_PROP_PERSISTENT) != 0;
+    const bool fused = !c->H.cplx && ((c->variant[precision] & kVariantFused) != 0 ||
+                                      (flags & TBPM_PROP_PERSISTENT) != 0);
+    if (c->H.cplx && (flags & TBPM_PROP_PERSISTENT))
+        return fail(c, TBPM_E_UNSUPPORTED, "the fused step takes real hoppings only");
 
     std::vector<double> J(kMaxTerms);
     int M = 0;
@@ -855,6 +860,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         base.chunk_sample = c->H.chunk_sample;
         base.n_rows = c->H.n_rows;
         base.uniform = c->H.uniform;
+        base.cplx = c->H.cplx;
         base.h_uniform = c->H.h_uniform;
         base.h_uniform_f = (float)c->H.h_uniform;
         base.psi0 = g.psi0;
@@ -994,6 +1000,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 }
                 TermArgs t = base;
                 t.variant = c->variant[precision];
+                // complex values have the plain term kernels only (16-byte lanes)
+                if (c->H.cplx) t.variant &= kVariantZigZag | kVariantStreamHints;
                 t.reverse = (t.variant & kVariantZigZag) ? (int)(k & 1) : 0;
                 t.x = L.x < 0 ? g.buf[cur] : g.buf[L.x];
                 t.x_is_psi = L.x < 0;
@@ -1097,7 +1105,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         // matrix: a column (and a value, unless one value serves all) per
         // stored entry, and the diagonal
         const double valb = fp32 ? 4.0 : 8.0;
-        const double entry = 4.0 + (c->H.uniform ? 0.0 : valb);
+        const double entry = 4.0 + (c->H.uniform ? 0.0 : valb * (c->H.cplx ? 2 : 1));
         S.bytes_term = vb + (double)c->H.nnz_true * entry + (double)c->n_orb * valb;
     }
     if (profile) {
@@ -1224,6 +1232,8 @@ extern "C" int tbpm_propagate_adjoint(tbpm_ctx *c, double z, int n_steps, const 
     if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
     if (!c->have_h || c->n_states < 1)
         return fail(c, TBPM_E_STATE, "build the Hamiltonian and set states first");
+    if (c->H.cplx)
+        return fail(c, TBPM_E_UNSUPPORTED, "the adjoint takes real hoppings only");
     if (!c->H.val64 || (c->H.n_hop > 0 && !c->H.bond_rows))
         return fail(c, TBPM_E_STATE, "the adjoint needs the FP64 Hamiltonian");
     if (n_steps < 1 || K < 1 || !gbar || !grad_hop || !grad_onsite)

@@ -56,7 +56,7 @@ __global__ void k_map_orbitals(int64_t n_orb, int n_samples, const int64_t *samp
 // error bits: 1 index out of range, 2 self bond, 4 bond across samples,
 // 8 non-finite value
 __global__ void k_count(int64_t n_hop, int64_t n_orb, const int64_t *hi, const int64_t *hj,
-                        const double *hv, const int32_t *user_to_row,
+                        const double *hv, int vw, const int32_t *user_to_row,
                         const int32_t *orb_sample, int32_t *deg, int *err)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -65,8 +65,10 @@ __global__ void k_count(int64_t n_hop, int64_t n_orb, const int64_t *hi, const i
     if (i < 0 || j < 0 || i >= n_orb || j >= n_orb) { atomicOr(err, 1); return; }
     if (i == j) { atomicOr(err, 2); return; }
     if (orb_sample[i] != orb_sample[j]) { atomicOr(err, 4); return; }
-    double v = hv[b];
-    if (!(v == v) || v - v != 0.0) { atomicOr(err, 8); return; }
+    for (int q = 0; q < vw; ++q) {
+        double v = hv[b * vw + q];
+        if (!(v == v) || v - v != 0.0) { atomicOr(err, 8); return; }
+    }
     atomicAdd(&deg[user_to_row[i]], 1);
     atomicAdd(&deg[user_to_row[j]], 1);
 }
@@ -149,6 +151,8 @@ int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st,
     return rc;
 }
 
+// Values are VW doubles per entry: 1 (real hoppings) or 2 (complex, re/im).
+template <int VW>
 __global__ void k_pad_fill(int64_t n_rows, const int64_t *slice_ptr, int32_t *col,
                            double *val)
 {
@@ -160,10 +164,11 @@ __global__ void k_pad_fill(int64_t n_rows, const int64_t *slice_ptr, int32_t *co
     int w = (int)((slice_ptr[q + 1] - base) / kSliceRows);
     for (int k = 0; k < w; ++k) {
         col[base + (int64_t)k * kSliceRows + lr] = (int32_t)r;
-        val[base + (int64_t)k * kSliceRows + lr] = 0.0;
+        for (int q = 0; q < VW; ++q) val[(base + (int64_t)k * kSliceRows + lr) * VW + q] = 0.0;
     }
 }
 
+template <int VW>
 __global__ void k_fill(int64_t n_hop, const int64_t *hi, const int64_t *hj, const double *hv,
                        double inv_s, const int32_t *user_to_row, const int64_t *slice_ptr,
                        int32_t *fill, int32_t *col, double *val)
@@ -171,15 +176,19 @@ __global__ void k_fill(int64_t n_hop, const int64_t *hi, const int64_t *hj, cons
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= n_hop) return;
     int32_t ri = user_to_row[hi[b]], rj = user_to_row[hj[b]];
-    double v = hv[b] * inv_s;
     int pi = atomicAdd(&fill[ri], 1);
     int64_t ei = slice_ptr[ri / kSliceRows] + (int64_t)pi * kSliceRows + ri % kSliceRows;
     col[ei] = rj;
-    val[ei] = v;
     int pj = atomicAdd(&fill[rj], 1);
     int64_t ej = slice_ptr[rj / kSliceRows] + (int64_t)pj * kSliceRows + rj % kSliceRows;
     col[ej] = ri;
-    val[ej] = v;                 // conj(t) = t for real hoppings
+    // H_ij = t, H_ji = conj(t)
+    val[ei * VW] = hv[b * VW] * inv_s;
+    val[ej * VW] = hv[b * VW] * inv_s;
+    if (VW == 2) {
+        val[ei * VW + 1] = hv[b * VW + 1] * inv_s;
+        val[ej * VW + 1] = -(hv[b * VW + 1] * inv_s);
+    }
 }
 
 __global__ void k_diag(int64_t n_orb, const double *onsite, double inv_s,
@@ -194,6 +203,7 @@ __global__ void k_diag(int64_t n_orb, const double *onsite, double inv_s,
 // product's summation order is independent of the fill order; then the
 // Gershgorin row bound |d_r| + sum |H~_rc|, max-reduced as the bit pattern of
 // a non-negative double (which orders like an unsigned integer).
+template <int VW>
 __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int32_t *deg,
                             const double *diag, int32_t *col, double *val,
                             unsigned long long *gersh_bits, unsigned long long *band)
@@ -202,25 +212,28 @@ __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int3
     if (r >= n_rows) return;
     int64_t base = slice_ptr[r / kSliceRows] + r % kSliceRows;
     int d = deg[r];
+    auto E = [&](int k) { return base + (int64_t)k * kSliceRows; };
     for (int a = 1; a < d; ++a) {
-        int32_t c = col[base + (int64_t)a * kSliceRows];
-        double v = val[base + (int64_t)a * kSliceRows];
+        int32_t c = col[E(a)];
+        double v0 = val[E(a) * VW], v1 = VW == 2 ? val[E(a) * VW + 1] : 0.0;
         int b = a - 1;
         while (b >= 0) {
-            int32_t cb = col[base + (int64_t)b * kSliceRows];
-            double vb = val[base + (int64_t)b * kSliceRows];
-            if (cb < c || (cb == c && vb <= v)) break;
-            col[base + (int64_t)(b + 1) * kSliceRows] = cb;
-            val[base + (int64_t)(b + 1) * kSliceRows] = vb;
+            int32_t cb = col[E(b)];
+            double w0 = val[E(b) * VW], w1 = VW == 2 ? val[E(b) * VW + 1] : 0.0;
+            if (cb < c || (cb == c && (w0 < v0 || (w0 == v0 && w1 <= v1)))) break;
+            col[E(b + 1)] = cb;
+            val[E(b + 1) * VW] = w0;
+            if (VW == 2) val[E(b + 1) * VW + 1] = w1;
             --b;
         }
-        col[base + (int64_t)(b + 1) * kSliceRows] = c;
-        val[base + (int64_t)(b + 1) * kSliceRows] = v;
+        col[E(b + 1)] = c;
+        val[E(b + 1) * VW] = v0;
+        if (VW == 2) val[E(b + 1) * VW + 1] = v1;
     }
     double g = fabs(diag[r]);
     long long bw = 0;
     for (int a = 0; a < d; ++a) {
-        g += fabs(val[base + (int64_t)a * kSliceRows]);
+        g += VW == 2 ? hypot(val[E(a) * VW], val[E(a) * VW + 1]) : fabs(val[E(a) * VW]);
         const long long dist = (long long)col[base + (int64_t)a * kSliceRows] - (long long)r;
         bw = max(bw, dist < 0 ? -dist : dist);
     }
@@ -274,6 +287,7 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
                BuildOutput &out, cudaStream_t st, std::string &msg)
 {
     const int T = 256;
+    const int vw = in.cplx ? 2 : 1;      // doubles per stored value
     std::vector<int64_t> row_off(in.n_samples + 1);
     CK(cudaMemcpyAsync(row_off.data(), in.d_sample_row_off,
                        (in.n_samples + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -306,7 +320,7 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
 
     if (in.n_hop > 0) {
         k_count<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.n_orb, in.hop_i, in.hop_j,
-                                                       in.hop_v, out.user_to_row,
+                                                       in.hop_v, vw, out.user_to_row,
                                                        out.orb_sample, deg, err);
         CK(cudaGetLastError());
     }
@@ -339,22 +353,35 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
 
     int64_t nnz_alloc = out.nnz_pad > 0 ? out.nnz_pad : 1;
     CK(cudaMalloc(&out.col, nnz_alloc * sizeof(int32_t)));
-    CK(cudaMalloc(&out.val64, nnz_alloc * sizeof(double)));
+    CK(cudaMalloc(&out.val64, nnz_alloc * vw * sizeof(double)));
+    out.cplx = in.cplx;
     CK(cudaMalloc(&out.diag64, n_rows * sizeof(double)));
     CK(cudaMemsetAsync(out.diag64, 0, n_rows * sizeof(double), st));
-    k_pad_fill<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, out.val64);
+    if (vw == 2)
+        k_pad_fill<2><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, out.val64);
+    else
+        k_pad_fill<1><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, out.val64);
     CK(cudaGetLastError());
     if (in.n_hop > 0) {
-        k_fill<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j, in.hop_v,
-                                                      in.inv_s, out.user_to_row,
-                                                      out.slice_ptr, fill, out.col, out.val64);
+        if (vw == 2)
+            k_fill<2><<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j, in.hop_v,
+                                                             in.inv_s, out.user_to_row,
+                                                             out.slice_ptr, fill, out.col, out.val64);
+        else
+            k_fill<1><<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j, in.hop_v,
+                                                             in.inv_s, out.user_to_row,
+                                                             out.slice_ptr, fill, out.col, out.val64);
         CK(cudaGetLastError());
     }
     k_diag<<<blocks_for(in.n_orb, T), T, 0, st>>>(in.n_orb, in.onsite, in.inv_s,
                                                   out.user_to_row, out.diag64);
     CK(cudaGetLastError());
-    k_sort_rows<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, deg, out.diag64,
-                                                     out.col, out.val64, gbits, gbits + 1);
+    if (vw == 2)
+        k_sort_rows<2><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, deg, out.diag64,
+                                                            out.col, out.val64, gbits, gbits + 1);
+    else
+        k_sort_rows<1><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, deg, out.diag64,
+                                                            out.col, out.val64, gbits, gbits + 1);
     CK(cudaGetLastError());
     unsigned long long hg[2] = {0, 0};
     CK(cudaMemcpyAsync(hg, gbits, sizeof(hg), cudaMemcpyDeviceToHost, st));
@@ -370,7 +397,7 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
                        cudaMemcpyHostToDevice, st));
 
     out.n_hop = in.n_hop;
-    if (detect_uniform && in.n_hop > 0) {
+    if (detect_uniform && in.n_hop > 0 && vw == 1) {
         // one hopping value everywhere (e.g. pristine or onsite-disordered
         // lattices): the term kernels then need no value loads
         CK(cudaMemsetAsync(err, 0xff, sizeof(int), st));
@@ -391,10 +418,11 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
         CK(cudaGetLastError());
     }
     if (keep32) {
-        CK(cudaMalloc(&out.val32, nnz_alloc * sizeof(float)));
+        CK(cudaMalloc(&out.val32, nnz_alloc * vw * sizeof(float)));
         CK(cudaMalloc(&out.diag32, n_rows * sizeof(float)));
         if (out.nnz_pad > 0)
-            k_to_f32<<<blocks_for(out.nnz_pad, T), T, 0, st>>>(out.nnz_pad, out.val64, out.val32);
+            k_to_f32<<<blocks_for(out.nnz_pad * vw, T), T, 0, st>>>(out.nnz_pad * vw, out.val64,
+                                                                    out.val32);
         k_to_f32<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.diag64, out.diag32);
         CK(cudaGetLastError());
     }

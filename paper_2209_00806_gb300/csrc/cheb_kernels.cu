@@ -182,7 +182,13 @@ template <> struct Coef<float> {
     __device__ static float hu(const TermArgs &a) { return a.h_uniform_f; }
 };
 
-template <typename V, int L, int SPL>
+template <typename V> struct Val2;
+template <> struct Val2<double> { typedef double2 type; };
+template <> struct Val2<float> { typedef float2 type; };
+
+// CX: complex matrix values (re, im) per stored entry (Peierls phases);
+// otherwise real values.
+template <typename V, int L, int SPL, bool CX>
 __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int l,
                                                const V *sc)
 {
@@ -211,15 +217,25 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
     Cv<V, SPL> y = ld_ro<V, L, SPL>(a.x, r, l);
 #pragma unroll
     for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
+    typedef typename Val2<V>::type V2;
+    const V2 *valp2 = reinterpret_cast<const V2 *>(a.H.val) + base + lr;
     for (int k = 0; k < w; k += 4) {
         int32_t c[4];
-        V h[4];
+        V h[4], hm[4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             ok[u] = k + u < w;
             c[u] = ok[u] ? __ldg(colp + (int64_t)(k + u) * kSliceRows) : (int32_t)r;
-            if (a.uniform) {
+            hm[u] = (V)0;
+            if (CX) {
+                V2 v2;
+                v2.x = (V)0;
+                v2.y = (V)0;
+                if (ok[u]) v2 = __ldg(valp2 + (int64_t)(k + u) * kSliceRows);
+                h[u] = v2.x;
+                hm[u] = v2.y;
+            } else if (a.uniform) {
                 // one value for all entries; padded slots (col == own row) add nothing
                 ok[u] = ok[u] && c[u] != (int32_t)r;
                 h[u] = Coef<V>::hu(a);
@@ -237,6 +253,10 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
                 for (int j = 0; j < SPL; ++j) {
                     y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
                     y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                    if (CX) {       // (h + i hm)(x_re + i x_im)
+                        y.re[j] = fma(-hm[u], xv[u].im[j], y.re[j]);
+                        y.im[j] = fma(hm[u], xv[u].re[j], y.im[j]);
+                    }
                 }
             }
         }
@@ -278,7 +298,7 @@ __device__ __forceinline__ int64_t block_in_order(const TermArgs &a)
 // FP32: at most 40 registers (12 blocks of 128 threads per SM; 80 for the
 // wide lanes) -- the kernel is latency-bound, so residency matters; FP64:
 // unconstrained.
-template <typename V, int L, int SPL>
+template <typename V, int L, int SPL, bool CX>
 __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 3) : 1) k_term(TermArgs a)
 {
     const int64_t t = block_in_order(a) * blockDim.x + threadIdx.x;
@@ -287,7 +307,7 @@ __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 3) : 1) 
     if (r >= a.n_rows) return;
     const V *sc = Coef<V>::scale(a);
     if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
-    Cv<V, SPL> o = term_row<V, L, SPL>(a, r, l, sc);
+    Cv<V, SPL> o = term_row<V, L, SPL, CX>(a, r, l, sc);
     st<V, L, SPL>(a.out, r, l, o);
 }
 
@@ -307,7 +327,7 @@ __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 3) : 1) 
 // level on every lane).
 constexpr int kFinalThreads = 128;
 
-template <typename V, int L, int SPL, bool COMPUTE>
+template <typename V, int L, int SPL, bool COMPUTE, bool CX>
 __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
 {
     constexpr int B = L * SPL;
@@ -324,7 +344,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
     if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * B;
     Cv<V, SPL> o;
     if (COMPUTE) {
-        o = term_row<V, L, SPL>(a, r, l, sc);
+        o = term_row<V, L, SPL, CX>(a, r, l, sc);
         st<V, L, SPL>(a.out, r, l, o);
     } else {
         o = ld<V, L, SPL>(a.out, r, l);
@@ -541,50 +561,50 @@ __global__ void k_get_states(const void *psi, int64_t n_orb, const int32_t *user
         dst[(int64_t)(g0 + b) * n_orb + u] = StoreC<V, 1>::get(psi, r * B + b);
 }
 
-template <typename V, int L, int SPL>
+template <typename V, int L, int SPL, bool CX>
 cudaError_t launch_term_t(const TermArgs &a, int threads, cudaStream_t st)
 {
     const int64_t n_threads = a.n_rows * L;
     const unsigned blocks = (unsigned)((n_threads + threads - 1) / threads);
-    k_term<V, L, SPL><<<blocks, threads, 0, st>>>(a);
+    k_term<V, L, SPL, CX><<<blocks, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename V, int L, int SPL>
+template <typename V, int L, int SPL, bool CX>
 cudaError_t launch_final_t(const TermArgs &a, int threads, bool compute, cudaStream_t st)
 {
     (void)threads;   // the closing term has its own block size
     const unsigned blocks = (unsigned)(a.n_rows * L / kFinalThreads);
     if (compute)
-        k_final<V, L, SPL, true><<<blocks, kFinalThreads, 0, st>>>(a);
+        k_final<V, L, SPL, true, CX><<<blocks, kFinalThreads, 0, st>>>(a);
     else
-        k_final<V, L, SPL, false><<<blocks, kFinalThreads, 0, st>>>(a);
+        k_final<V, L, SPL, false, CX><<<blocks, kFinalThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <bool FINAL>
-cudaError_t dispatch(const TermArgs &a, int fp32, int B, int threads, bool compute,
-                     cudaStream_t st)
+template <bool FINAL, bool CX>
+cudaError_t dispatch_cx(const TermArgs &a, int fp32, int B, int threads, bool compute,
+                        cudaStream_t st)
 {
-    if (!FINAL && (a.variant & kVariantWide)) {
+    if (!FINAL && !CX && (a.variant & kVariantWide)) {
         // one thread per row and 32-byte lanes: fewer lanes share the index loads
         if (!fp32) {
             switch (B) {
-            case 2: return launch_term_t<double, 1, 2>(a, threads, st);
-            case 4: return launch_term_t<double, 2, 2>(a, threads, st);
-            case 8: return launch_term_t<double, 4, 2>(a, threads, st);
+            case 2: return launch_term_t<double, 1, 2, false>(a, threads, st);
+            case 4: return launch_term_t<double, 2, 2, false>(a, threads, st);
+            case 8: return launch_term_t<double, 4, 2, false>(a, threads, st);
             }
         } else {
             switch (B) {
-            case 4: return launch_term_t<float, 1, 4>(a, threads, st);
-            case 8: return launch_term_t<float, 2, 4>(a, threads, st);
-            case 16: return launch_term_t<float, 4, 4>(a, threads, st);
+            case 4: return launch_term_t<float, 1, 4, false>(a, threads, st);
+            case 8: return launch_term_t<float, 2, 4, false>(a, threads, st);
+            case 16: return launch_term_t<float, 4, 4, false>(a, threads, st);
             }
         }
     }
-#define TBPM_CASE(V, L, SPL)                                              \
-    return FINAL ? launch_final_t<V, L, SPL>(a, threads, compute, st)    \
-                 : launch_term_t<V, L, SPL>(a, threads, st)
+#define TBPM_CASE(V, L, SPL)                                                  \
+    return FINAL ? launch_final_t<V, L, SPL, CX>(a, threads, compute, st)    \
+                 : launch_term_t<V, L, SPL, CX>(a, threads, st)
     if (!fp32) {
         switch (B) {
         case 1: TBPM_CASE(double, 1, 1);
@@ -603,6 +623,14 @@ cudaError_t dispatch(const TermArgs &a, int fp32, int B, int threads, bool compu
     }
 #undef TBPM_CASE
     return cudaErrorInvalidValue;
+}
+
+template <bool FINAL>
+cudaError_t dispatch(const TermArgs &a, int fp32, int B, int threads, bool compute,
+                     cudaStream_t st)
+{
+    return a.cplx ? dispatch_cx<FINAL, true>(a, fp32, B, threads, compute, st)
+                  : dispatch_cx<FINAL, false>(a, fp32, B, threads, compute, st);
 }
 
 }  // namespace

@@ -35,7 +35,7 @@ constexpr int kVariantWide = 64;        // term kernel with 32-byte lanes
 struct SellView {
     const int64_t *slice_ptr;  // [n_slices + 1]
     const int32_t *col;        // [nnz_pad]
-    const void *val;           // double or float [nnz_pad]
+    const void *val;           // double or float [nnz_pad], pairs (re, im) if complex
     const void *diag;          // double or float [n_rows]
 };
 
@@ -58,6 +58,7 @@ struct TermArgs {
     int variant;          // kVariant* bits
     int reverse;          // walk the blocks from the end (zig-zag order)
     int uniform;          // every off-diagonal value equals h_uniform (no value loads)
+    int cplx;             // complex matrix values (re, im) per entry
     double h_uniform;
     float h_uniform_f;
     // closing term only (H.col == nullptr: reduce `out` without computing it)
@@ -180,6 +181,7 @@ struct BuildInput {
     const int64_t *d_sample_off;      // device [n_samples + 1] (caller order)
     const int64_t *d_sample_row_off;  // device [n_samples + 1] (padded rows)
     const int32_t *d_perm;            // device [n_orb] caller -> position in sample, or nullptr
+    int cplx;                         // hop_v holds (re, im) per bond
 };
 
 struct BuildOutput {
@@ -199,6 +201,7 @@ struct BuildOutput {
     int max_width = 0;
     int64_t bandwidth = 0;           // max |col - row| over the stored entries
     int uniform = 0;                 // all off-diagonal values are equal
+    int cplx = 0;                    // values are complex (re, im) per entry
     double h_uniform = 0.0;          // that value (H~ units)
 };
 

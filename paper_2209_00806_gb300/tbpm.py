@@ -51,8 +51,15 @@ class Propagator:
         return self
 
     def build_sample(self, sample, s, sample_offsets=None, flags=0):
+        """Complex hoppings (Peierls phases) select TBPM_BUILD_COMPLEX_HOPS."""
+        hv = sample.hop_v
+        if np.iscomplexobj(hv):
+            hv = np.ascontiguousarray(hv, dtype=np.complex128)
+            flags |= N.TBPM_BUILD_COMPLEX_HOPS
+        else:
+            hv = _c64(hv)
         return self.build(sample.n_orb, _c64(sample.onsite), _ci64(sample.hop_i),
-                          _ci64(sample.hop_j), _c64(sample.hop_v), s, sample_offsets, flags)
+                          _ci64(sample.hop_j), hv, s, sample_offsets, flags)
 
     def set_phase_states(self, theta):
         self.n_states = int(theta.shape[0])

@@ -233,3 +233,26 @@ def twisted_bilayer(side_nm: float, theta_deg: float = 1.05, cutoff_nm: float = 
                   hop_v=np.ascontiguousarray(hv), pos=pos[:, :2],
                   meta=dict(kind="twisted_bilayer", side_nm=side_nm, theta_deg=theta_deg,
                             cutoff_nm=cutoff_nm, n_bottom=layers[0].shape[0]))
+
+
+FLUX_QUANTUM = 4135.667696      # h / e in T nm^2
+
+
+def peierls(sample: Sample, B_tesla: float) -> Sample:
+    """Perpendicular magnetic field by Peierls substitution (Sec. 2.1, and the
+    Landau-gauge form of Sec. 4): with A = (B y, 0, 0) the line integral of A
+    along the straight bond from orbital i to orbital j is
+    B (x_j - x_i) (y_i + y_j) / 2, so t_ij -> t_ij exp(i pi B (x_j - x_i)
+    (y_j + y_i) / Phi_0) with Phi_0 = h / e.  Needs orbital positions and
+    open boundaries (the Landau gauge is not periodic).  The result has
+    complex128 hoppings."""
+    if sample.pos is None:
+        raise ValueError("the Peierls phases need orbital positions")
+    if sample.meta.get("pbc", False):
+        raise ValueError("the Landau gauge needs open boundaries")
+    x, y = sample.pos[:, 0], sample.pos[:, 1]
+    i, j = sample.hop_i, sample.hop_j
+    phase = np.pi * B_tesla * (x[j] - x[i]) * (y[j] + y[i]) / FLUX_QUANTUM
+    hv = sample.hop_v.astype(np.complex128) * np.exp(1j * phase)
+    return Sample(n_orb=sample.n_orb, onsite=sample.onsite, hop_i=i, hop_j=j, hop_v=hv,
+                  pos=sample.pos, meta=dict(sample.meta, B_tesla=B_tesla))

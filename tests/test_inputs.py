@@ -1,6 +1,7 @@
 """The seeded input generators: SplitMix64 against its published output,
 draw ranges, lattice sizes, vacancies, and the workload recipes."""
 import numpy as np
+import pytest
 
 from tbpm_inputs import lattice, rng, workloads
 
@@ -52,3 +53,70 @@ def test_workload_recipes():
     th = small.thetas()
     assert [t.shape for t in th] == [(2, int(small.offsets[k + 1] - small.offsets[k]))
                                      for k in range(3)]
+
+
+def _hexagon_flux(smp, B):
+    """Flux (in units of Phi_0) through each hexagon of an open graphene
+    flake, from the product of the Peierls factors around it."""
+    pairs = {}
+    for b in range(smp.n_hop):
+        i, j = int(smp.hop_i[b]), int(smp.hop_j[b])
+        pairs[(i, j)] = smp.hop_v[b]
+        pairs[(j, i)] = np.conj(smp.hop_v[b])
+    L2 = smp.meta["L2"]
+    out = []
+    # the hexagon around the cell corner shared by cells (n1, n2), (n1+1, n2), (n1, n2+1)
+    for n1 in range(smp.meta["L1"] - 1):
+        for n2 in range(L2 - 1):
+            cell = lambda a, b: 2 * (a * L2 + b)
+            ring = [cell(n1, n2) + 1, cell(n1 + 1, n2), cell(n1 + 1, n2) + 1,
+                    cell(n1 + 1, n2 + 1), cell(n1, n2 + 1) + 1, cell(n1, n2 + 1)]
+            prod = 1.0 + 0j
+            ok = True
+            for a, b in zip(ring, ring[1:] + ring[:1]):
+                if (a, b) not in pairs:
+                    ok = False
+                    break
+                prod *= pairs[(a, b)] / abs(pairs[(a, b)])
+            if ok:
+                out.append(np.angle(prod) / (2 * np.pi))
+    return np.array(out)
+
+
+def _cell_area():
+    return abs(lattice.A1[0] * lattice.A2[1] - lattice.A1[1] * lattice.A2[0])
+
+
+def test_peierls_flux_per_hexagon():
+    """The Peierls factors around every hexagon multiply to exp(+-2 pi i B
+    A_hex / Phi_0), A_hex = |a1 x a2| (one hexagon per primitive cell): the
+    field is uniform and of the stated strength, whatever the gauge."""
+    B = 500.0
+    smp = lattice.peierls(lattice.graphene(6, 5, pbc=False, with_pos=True), B)
+    assert np.iscomplexobj(smp.hop_v)
+    assert np.allclose(np.abs(smp.hop_v), 2.7)
+    flux = _hexagon_flux(smp, B)
+    assert len(flux) == 20
+    expect = B * _cell_area() / lattice.FLUX_QUANTUM
+    assert np.allclose(np.abs(flux), expect, rtol=1e-12, atol=1e-15)
+    assert np.all(np.sign(flux) == np.sign(flux[0]))
+
+
+def test_peierls_integer_flux_is_a_gauge_of_zero_field():
+    """One flux quantum per hexagon is gauge-equivalent to no field on a
+    simply connected flake: the spectrum is that of B = 0."""
+    from tests import exact
+    base = lattice.graphene(5, 4, pbc=False, with_pos=True, onsite_w=0.7, seed=2)
+    B1 = lattice.FLUX_QUANTUM / _cell_area()
+    e0 = np.linalg.eigvalsh(exact.dense_h(base))
+    e1 = np.linalg.eigvalsh(exact.dense_h(lattice.peierls(base, B1)))
+    eh = np.linalg.eigvalsh(exact.dense_h(lattice.peierls(base, 0.5 * B1)))
+    assert np.max(np.abs(e1 - e0)) < 1e-9
+    assert np.max(np.abs(eh - e0)) > 1e-2
+
+
+def test_peierls_needs_positions_and_open_boundaries():
+    with pytest.raises(ValueError):
+        lattice.peierls(lattice.graphene(4, 4, pbc=False), 10.0)
+    with pytest.raises(ValueError):
+        lattice.peierls(lattice.graphene(4, 4, pbc=True, with_pos=True), 10.0)

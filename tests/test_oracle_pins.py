@@ -145,10 +145,15 @@ def test_oracle_one_step_vs_expm():
         assert np.linalg.norm(psi[p] - U @ psi0[p]) < 1e-13
 
 
-@pytest.mark.parametrize("kind", ["disordered_vacancies", "random_graph"])
+@pytest.mark.parametrize("kind", ["disordered_vacancies", "random_graph", "magnetic_flake"])
 def test_oracle_corr_vs_exact_diagonalisation(kind):
     if kind == "disordered_vacancies":
         smp = lattice.graphene(12, 10, pbc=True, seed=11, onsite_w=1.0, vacancy_frac=0.03)
+        s = 9.5
+    elif kind == "magnetic_flake":
+        # complex hoppings: Peierls phases of a 250 T field (Sec. 2.1)
+        smp = lattice.peierls(lattice.graphene(12, 10, pbc=False, seed=11, onsite_w=1.0,
+                                               vacancy_frac=0.03, with_pos=True), 250.0)
         s = 9.5
     else:
         smp = lattice.random_graph(300, 700, seed=2, onsite_w=2.0)
