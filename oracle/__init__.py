@@ -12,7 +12,9 @@ closed form, the Bloch-sum solution of pristine graphene, SciPy's Bessel
 functions, invariants) live in ``tests/``.
 
 Parity pinned: Bessel table, H x, propagation, correlation and DOS (see the
-tests named ``test_oracle_*``).
+tests named ``test_oracle_*``).  The AC-conductivity path (Fermi-Dirac
+operator, current operator, two-state correlation, conductivity integral)
+is in ``oracle/ac.py``, pinned by ``tests/test_oracle_ac.py``.
 """
 from __future__ import annotations
 
