@@ -257,6 +257,9 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
 #define TBPM_VARIANT_FUSED_TILE(k) ((k) << 4)  /* fused tile rows x 4^k, k = 0..2 */
 #define TBPM_VARIANT_WIDE 64         /* term kernel with 32-byte lanes (one thread per
                                         row for 4 FP32 or 2 FP64 states) */
+#define TBPM_VARIANT_SPLIT2 128      /* each row's entries split over 2 threads (long
+                                        rows: more gathers in flight); real values */
+#define TBPM_VARIANT_SPLIT4 256      /* the same over 4 threads (not with SPLIT2) */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
 
@@ -306,6 +309,71 @@ int tbpm_correlation_noalloc(const double *psi0, const double *phi, int64_t n_or
 
 /* Statistics of the last call on ctx. */
 int tbpm_get_stats(tbpm_ctx *ctx, tbpm_stats *out);
+
+/* ---- AC (optical) conductivity (Sec. 2.7, with the Fermi-Dirac operator of
+ * Sec. 2.2) --------------------------------------------------------------- */
+
+/* c1. Bond vectors for the current operator J_a = -i sum t_ij d^a_ij c_i^+ c_j
+ * (Sec. 2.7; e / hbar factored out, units eV nm), d_ij = r_j - r_i.
+ *   dx, dy  [n_hop] components (nm) of d_b for bond b of the bond list given
+ *           to tbpm_build_hamiltonian (same order), host or device, finite.
+ *           For a periodic sample d_b is the bond's own image (the minimum
+ *           image for nearest neighbours), not a difference of positions.
+ * Entry (i, j) gets d_b and its conjugate partner (j, i) gets -d_b.  A pair
+ * listed twice must have the same vector.  Kept until the next
+ * tbpm_build_hamiltonian.  Errors: STATE (no Hamiltonian), INVALID_ARG
+ * (missing or non-finite vectors), OOM, CUDA. */
+int tbpm_set_bond_vectors(tbpm_ctx *ctx, const double *dx, const double *dy, int where);
+
+/* c2. Chebyshev coefficients of the Fermi function on the rescaled axis,
+ * f(x) = 1 / (exp(beta_s (x - mu_s)) + 1) = c_0/2 + sum_{k>=1} c_k T_k(x)
+ * (Sec. 2.2; beta_s = beta s, mu_s = mu / s), by the trapezoid rule of
+ * c_k = (2/pi) int_0^pi f(cos t) cos(k t) dt evaluated with an FFT, truncated
+ * after the last |c_k| > 1e-15 max|c|.
+ *   c_out    [k_max] or NULL to query the count only
+ *   n_terms  out: the number of coefficients K
+ * Errors: INVALID_ARG, UNSUPPORTED (K > k_max). */
+int tbpm_fermi_coefficients(double beta_s, double mu_s, int k_max, double *c_out,
+                            int *n_terms);
+
+/* c3. AC-conductivity correlation (Sec. 2.7).  For each initial state psi of
+ * each sample (the states set on ctx, at most 16 per sample):
+ *   psi_2 = f(H) psi,  psi_1b = [1 - f(H)] J_b psi  (b = x, y),
+ * f(H) = 1 / (exp(beta (H - mu)) + 1) by the Chebyshev series of c2 with
+ * Clenshaw's recurrence in FP64; then psi, psi_2, psi_1x, psi_1y advance
+ * together (one state group, `precision` as in tbpm_propagate) and after every
+ * step the library records
+ *   corr[k][p][ab][n] = <psi_2(n tau)| J_a |psi_1b(n tau)>,  ab = xx, xy, yx, yy
+ * (a = current direction, b = field direction).
+ *   z, n_steps    as tbpm_propagate (tau = z / s)
+ *   beta, mu      inverse temperature (1/eV) and chemical potential (eV)
+ *   corr_out      complex128 [n_samples][n_states][4][n_steps + 1]
+ *   where_out     TBPM_HOST or TBPM_DEVICE
+ *   flags         TBPM_PROP_PROFILE, TBPM_PROP_GRAPH, TBPM_PROP_PERSISTENT
+ * Needs tbpm_set_bond_vectors.  The caller's states are restored afterwards
+ * (correlations and norms of the run are not kept).  Norm checks are taken
+ * relative to each state's norm at t = 0.  Errors: STATE (no Hamiltonian,
+ * states or bond vectors), INVALID_ARG (more than 16 states, TBPM_PROP_RESUME,
+ * beta <= 0), UNSUPPORTED (Fermi series longer than 2^22 terms), OOM, CUDA,
+ * NORM_DRIFT, NONFINITE. */
+int tbpm_ac_correlation(tbpm_ctx *ctx, double z, int n_steps, double beta, double mu,
+                        int precision, double *corr_out, int where_out, int flags);
+
+/* c4. Real part of the AC conductivity from correlation rows (Sec. 2.7, Eq.
+ * AC): for each row C and each omega,
+ *   sigma(omega) = norm (exp(-beta omega) - 1) / omega
+ *                  * int_0^T exp(-eta t) sin(omega t) 2 Im C(t) dt,
+ * trapezoid rule on t_n = n tau, T = n_steps tau.  In units of e^2 / hbar
+ * when C comes from c3 (eV^2 nm^2) and norm = N_orb / area (nm^-2) turns the
+ * random-state average into the trace per area; spin degeneracy is the
+ * caller's factor.
+ *   corr       complex128 [n_rows][n_steps + 1] (host)
+ *   omegas     [n_omega] > 0 (eV);  eta >= 0 damping (the E -> 0+ limit)
+ *   sigma_out  [n_rows][n_omega]
+ * Errors: INVALID_ARG. */
+int tbpm_ac_conductivity(const double *corr, int n_rows, int n_steps, double tau, double beta,
+                         double eta, const double *omegas, int n_omega, double norm,
+                         double *sigma_out);
 
 #ifdef __cplusplus
 }

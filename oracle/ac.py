@@ -12,7 +12,8 @@ primitives:
   of the defining integral, evaluated by FFT as the paper says), and the
   real Chebyshev recurrence T_{k+1} = 2 H~ T_k - T_{k-1}, T_0 = 1, T_1 = H~.
   Current operator (Sec. 2.7): J = -i sum_{ij} t_ij (r_j - r_i) c_i^+ c_j, with
-  the charge e / hbar left out (units eV nm).
+  the charge e / hbar left out (units eV nm); r_j - r_i is the bond vector,
+  given per bond (a periodic bond carries its own image).
   Two states (Sec. 2.7): psi_1(t) = e^{-iHt} [1 - f(H)] J_b psi(0) and
   psi_2(t) = e^{-iHt} f(H) psi(0); the correlation is <psi_2(t)| J_a |psi_1(t)>.
   Real part of the conductivity (Sec. 2.7, Eq. AC): the time integral of
@@ -86,42 +87,44 @@ def fermi_apply(sample, s: float, beta_s: float, mu_s: float, v: np.ndarray) -> 
     return acc
 
 
-def current_apply(sample, pos_a: np.ndarray, v: np.ndarray) -> np.ndarray:
-    """J_a v with (J_a)_ij = -i t_ij (a_j - a_i) over the bond list and its
-    conjugate partner (J_a)_ji = -i conj(t_ij) (a_i - a_j); units eV nm."""
+def current_apply(sample, d_a: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """J_a v with (J_a)_ij = -i t_ij d^a_ij over the bond list (d_ij = r_j - r_i,
+    the bond vector, given per bond) and its conjugate partner
+    (J_a)_ji = -i conj(t_ij) (-d^a_ij); units eV nm."""
     v = np.ascontiguousarray(v, dtype=np.complex128)
     i, j = sample.hop_i, sample.hop_j
     t = np.asarray(sample.hop_v, dtype=np.complex128)
-    d = pos_a[j] - pos_a[i]
+    d = np.asarray(d_a, dtype=np.float64)
     y = np.zeros_like(v)
     np.add.at(y, i, -1j * t * d * v[j])
     np.add.at(y, j, -1j * np.conj(t) * (-d) * v[i])
     return y
 
 
-def ac_states(sample, s: float, beta: float, mu: float, pos: np.ndarray,
+def ac_states(sample, s: float, beta: float, mu: float, dr: np.ndarray,
               psi0: np.ndarray):
     """psi_2(0) = f psi0 and psi_1(0)_b = [1 - f] J_b psi0 for b = x, y."""
     beta_s, mu_s = beta * s, mu / s
     psi2 = fermi_apply(sample, s, beta_s, mu_s, psi0)
     psi1 = []
     for b in range(2):
-        jb = current_apply(sample, pos[:, b], psi0)
+        jb = current_apply(sample, dr[:, b], psi0)
         psi1.append(jb - fermi_apply(sample, s, beta_s, mu_s, jb))
     return psi2, psi1
 
 
 def ac_correlation(sample, s: float, z: float, n_steps: int, beta: float, mu: float,
-                   pos: np.ndarray, psi0: np.ndarray) -> np.ndarray:
+                   dr: np.ndarray, psi0: np.ndarray) -> np.ndarray:
     """corr[p, ab, n] = <psi_2(n tau)| J_a |psi_1(n tau)>_b for every state p,
-    ab = xx, xy, yx, yy (a = current direction, b = perturbation)."""
+    ab = xx, xy, yx, yy (a = current direction, b = perturbation); dr are the
+    bond vectors [n_hop, 2]."""
     psi0 = np.atleast_2d(np.asarray(psi0, dtype=np.complex128))
     S = psi0.shape[0]
     out = np.empty((S, 4, n_steps + 1), dtype=np.complex128)
     for p in range(S):
-        psi2, psi1 = ac_states(sample, s, beta, mu, pos, psi0[p])
+        psi2, psi1 = ac_states(sample, s, beta, mu, dr, psi0[p])
         for n in range(n_steps + 1):
-            ja = [current_apply(sample, pos[:, a], psi2) for a in range(2)]
+            ja = [current_apply(sample, dr[:, a], psi2) for a in range(2)]
             for a in range(2):
                 for b in range(2):
                     # <psi_2|J_a|psi_1> = <J_a psi_2|psi_1> (J_a is Hermitian)

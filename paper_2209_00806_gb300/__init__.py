@@ -9,4 +9,4 @@ object wrapper.  Importing fails loudly if the CUDA library is not built.
 from . import _native  # noqa: F401  (raises ImportError when libtbpm.so is missing)
 from ._native import (TBPM_FP32, TBPM_FP64, TbpmError, tbpm_bessel_coefficients,  # noqa: F401
                       tbpm_dos)
-from .tbpm import Propagator, dos, dos_adjoint  # noqa: F401
+from .tbpm import Propagator, ac_conductivity, dos, dos_adjoint, fermi_coefficients  # noqa: F401

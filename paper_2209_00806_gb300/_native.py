@@ -47,6 +47,10 @@ TBPM_PROP_PERSISTENT = 8
 TBPM_VARIANT_ZIGZAG = 1
 TBPM_VARIANT_STREAM_HINTS = 2
 TBPM_VARIANT_TMA = 4
+TBPM_VARIANT_FUSED = 8
+TBPM_VARIANT_WIDE = 64
+TBPM_VARIANT_SPLIT2 = 128
+TBPM_VARIANT_SPLIT4 = 256
 
 
 class TbpmError(RuntimeError):
@@ -100,6 +104,10 @@ SIGNATURES = [
     ("tbpm_autotune", _I32, [P, _I32, _F64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                              ctypes.POINTER(_I32), ctypes.POINTER(_F64)]),
     ("tbpm_get_stats", _I32, [P, ctypes.POINTER(tbpm_stats)]),
+    ("tbpm_set_bond_vectors", _I32, [P, P, P, _I32]),
+    ("tbpm_fermi_coefficients", _I32, [_F64, _F64, _I32, P, ctypes.POINTER(_I32)]),
+    ("tbpm_ac_correlation", _I32, [P, _F64, _I32, _F64, _F64, _I32, P, _I32, _I32]),
+    ("tbpm_ac_conductivity", _I32, [P, _I32, _I32, _F64, _F64, _F64, P, _I32, _F64, P]),
 ]
 
 
@@ -251,6 +259,33 @@ def tbpm_autotune(ctx, precision, z, probe_steps=4):
 def tbpm_correlation_noalloc(psi0, phi, n_orb, n_states, corr_out, norm_out, stream=None):
     return check(None, lib.tbpm_correlation_noalloc(ptr(psi0), ptr(phi), n_orb, n_states,
                                                     ptr(corr_out), ptr(norm_out), stream))
+
+
+def tbpm_set_bond_vectors(ctx, dx, dy, where=None):
+    return check(ctx, lib.tbpm_set_bond_vectors(ctx, ptr(dx), ptr(dy),
+                                                where_of(dx) if where is None else where))
+
+
+def tbpm_fermi_coefficients(beta_s: float, mu_s: float, k_max: int = 1 << 22):
+    n = _I32()
+    check(None, lib.tbpm_fermi_coefficients(beta_s, mu_s, k_max, None, ctypes.byref(n)))
+    c = np.zeros(n.value)
+    check(None, lib.tbpm_fermi_coefficients(beta_s, mu_s, n.value, ptr(c), ctypes.byref(n)))
+    return c
+
+
+def tbpm_ac_correlation(ctx, z, n_steps, beta, mu, precision, corr_out, where_out=None,
+                        flags=0):
+    if where_out is None:
+        where_out = where_of(corr_out)
+    return check(ctx, lib.tbpm_ac_correlation(ctx, z, n_steps, beta, mu, precision,
+                                              ptr(corr_out), where_out, flags))
+
+
+def tbpm_ac_conductivity(corr, n_rows, n_steps, tau, beta, eta, omegas, n_omega, norm,
+                         sigma_out):
+    return check(None, lib.tbpm_ac_conductivity(ptr(corr), n_rows, n_steps, tau, beta, eta,
+                                                ptr(omegas), n_omega, norm, ptr(sigma_out)))
 
 
 def tbpm_set_launch_config(ctx, precision, max_group, threads, variant=1):

@@ -83,6 +83,13 @@ struct tbpm_ctx {
     double2 *d_corr = nullptr;
     double *d_norms = nullptr;
     int corr_steps = -1;         // n_steps of the buffers above
+    double *d_norm_ref = nullptr;          // [n_samples][n_states] squared norms at t = 0
+    int64_t norm_ref_len = 0;
+    // AC-conductivity correlation
+    double *d_bond_dx = nullptr, *d_bond_dy = nullptr;   // [nnz_pad] bond vector per entry
+    bool ac_on = false;
+    double2 *d_ac_corr = nullptr;          // [n_samples][n_states / 4][4][n_steps + 1]
+    double *d_ac_partial = nullptr;        // [n_rows / kAcRows][4][8]
     bool have_run = false;
     std::vector<cudaEvent_t> events;
     tbpm_stats stats;
@@ -173,6 +180,12 @@ void free_hamiltonian(tbpm_ctx *c)
     c->items_len = c->done_len = c->tile_partial_len = 0;
     c->items_key[0] = c->items_key[1] = c->items_key[2] = -1;
     cudaFree(c->d_step);
+    cudaFree(c->d_norm_ref);
+    cudaFree(c->d_bond_dx);
+    cudaFree(c->d_bond_dy);
+    c->d_norm_ref = nullptr;
+    c->norm_ref_len = 0;
+    c->d_bond_dx = c->d_bond_dy = nullptr;
     c->d_block_partial = nullptr;
     c->d_chunk_count = nullptr;
     c->block_partial_len = 0;
@@ -540,8 +553,10 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
     if (threads < 64 || threads > 256 || (threads & (threads - 1)))
         return fail(c, TBPM_E_INVALID_ARG, "threads must be 64, 128 or 256");
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
-                                  (3 << kVariantFusedTileShift) | kVariantWide) ||
-        ((variant >> kVariantFusedTileShift) & 3) == 3)
+                                  (3 << kVariantFusedTileShift) | kVariantWide | kVariantSplit2 |
+                                  kVariantSplit4) ||
+        ((variant >> kVariantFusedTileShift) & 3) == 3 ||
+        ((variant & kVariantSplit2) && (variant & kVariantSplit4)))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
     if (c->max_group[precision] != max_group || c->threads[precision] != threads) free_groups(c);
     c->max_group[precision] = max_group;
@@ -808,6 +823,20 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
     }
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->st));
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_renorm, 0, sizeof(unsigned long long), c->st));
+    {
+        const int64_t need = (int64_t)c->n_samples * c->n_states;
+        if (need > c->norm_ref_len) {
+            if (resume) return fail(c, TBPM_E_STATE, "nothing to resume for these states");
+            cudaFree(c->d_norm_ref);
+            c->d_norm_ref = nullptr;
+            c->norm_ref_len = 0;
+            rc = dalloc(c, &c->d_norm_ref, need);
+            if (rc) return rc;
+            c->norm_ref_len = need;
+        }
+    }
+    if (c->ac_on && (!c->d_ac_corr || !c->d_ac_partial || !c->d_bond_dx))
+        return fail(c, TBPM_E_STATE, "AC buffers missing");
 
     const size_t cs = fp32 ? 8 : 16;
     const int threads = c->threads[precision];
@@ -884,6 +913,38 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         ra.hard_bound = fp32 ? c->hard_fp32 : c->hard_fp64;
         ra.renorm_count = c->d_renorm;
         ra.error_flags = c->d_flags;
+        ra.norm_ref = c->d_norm_ref;
+        ra.set_ref = 0;
+
+        // AC-conductivity observer on the state buffer `bi` (after the reduction
+        // of the same step, whose counter it reads)
+        auto observe = [&](int bi) -> int {
+            if (!c->ac_on) return TBPM_OK;
+            AcArgs oa;
+            oa.H = Hv;
+            oa.dx = c->d_bond_dx;
+            oa.dy = c->d_bond_dy;
+            oa.psi = g.buf[bi];
+            oa.scale = fp32 ? g.scale : nullptr;
+            oa.chunk_sample = c->H.chunk_sample;
+            oa.n_rows = c->H.n_rows;
+            oa.B = g.B;
+            oa.block_partial = c->d_ac_partial;
+            CUDA_OR_FAIL(c, launch_ac_observe(oa, fp32, c->H.cplx, c->st));
+            AcReduceArgs ar;
+            ar.block_partial = c->d_ac_partial;
+            ar.sample_chunk_off = c->d_sample_chunk_off;
+            ar.n_samples = c->n_samples;
+            ar.B = g.B;
+            ar.group_state0 = g.s0;
+            ar.n_states = c->n_states;
+            ar.n_steps = n_steps;
+            ar.step = c->d_step;
+            ar.s = c->s;
+            ar.corr_ac = c->d_ac_corr;
+            CUDA_OR_FAIL(c, launch_ac_reduce(ar, c->st));
+            return TBPM_OK;
+        };
 
         // wavefront-fused step: item table, flags and the term tables of the
         // three buffer rotations
@@ -947,8 +1008,13 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             CUDA_OR_FAIL(c, launch_final(t0, fp32, g.B, threads, c->st));
             ra.scale = nullptr;
             ra.scale_f = nullptr;
+            ra.set_ref = resume ? 0 : 1;
             CUDA_OR_FAIL(c, launch_reduce(ra, c->st));
+            ra.set_ref = 0;
             launches += 2;
+            rc = observe(g.cur);
+            if (rc) return rc;
+            if (c->ac_on) launches += 2;
         }
         ra.scale = g.scale;
         ra.scale_f = g.scale_f;
@@ -977,7 +1043,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 }
                 CUDA_OR_FAIL(c, launch_reduce(ra, c->st));
                 if (timed) CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 4], c->st));
-                return TBPM_OK;
+                return observe(*next_cur);
             }
             std::vector<Launch> sch = schedule(a, cur, next_cur);
             size_t e0 = 0;
@@ -1036,7 +1102,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             }
             CUDA_OR_FAIL(c, launch_reduce(ra, c->st));
             if (timed) CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + 4], c->st));
-            return TBPM_OK;
+            return observe(*next_cur);
         };
 
         for (int n = 0; n < n_steps; ++n) {
@@ -1064,6 +1130,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             }
             g.cur = nxt;
             launches += fused ? 2 : M;   // term kernels (or the fused step) + one reduction
+            if (c->ac_on) launches += 2; // observer + its reduction
         }
     }
     if (profile) CUDA_OR_FAIL(c, cudaEventRecord(ev_all1, c->st));
@@ -1092,8 +1159,12 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
     for (int k = 0; k < 8; ++k) S.group_width[k] = k < S.n_groups ? c->groups[k].B : 0;
     S.renormalisations = (int64_t)h_renorm;
     S.kernel_launches = launches;
+    // drift of each state's squared norm relative to its value at the first step
     double md = 0.0;
-    for (double v : norms) md = std::max(md, fabs(v - 1.0));
+    for (size_t k = 0; k < cnt; ++k) {
+        const double ref = norms[k - k % (n_steps + 1)];
+        md = std::max(md, ref > 0.0 ? fabs(norms[k] / ref - 1.0) : norms[k]);
+    }
     S.max_norm_drift = md;
     S.ms_total = S.ms_term_avg = S.ms_final_avg = S.ms_reduce_avg = 0.0;
     S.term_launches = 0;
@@ -1452,6 +1523,9 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
     const int thread_opts[] = {128, 256};
     const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints,
                                 kVariantZigZag | kVariantWide,
+                                kVariantZigZag | kVariantSplit2, kVariantZigZag | kVariantSplit4,
+                                kVariantZigZag | kVariantWide | kVariantSplit2,
+                                kVariantZigZag | kVariantWide | kVariantSplit4,
                                 kVariantTma, kVariantTma | kVariantZigZag, kVariantFused,
                                 kVariantFused | (1 << kVariantFusedTileShift),
                                 kVariantFused | (2 << kVariantFusedTileShift)};
@@ -1476,4 +1550,198 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
     if (best_ms_per_step) *best_ms_per_step = best;
     c->have_run = false;
     return TBPM_OK;
+}
+
+// Bond vectors d_b = r_j - r_i (nm) of the bond list, onto the stored entries.
+extern "C" int tbpm_set_bond_vectors(tbpm_ctx *c, const double *dx, const double *dy, int where)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->have_h) return fail(c, TBPM_E_STATE, "build the Hamiltonian first");
+    if (c->H.n_hop > 0 && (!dx || !dy)) return fail(c, TBPM_E_INVALID_ARG, "bond vectors missing");
+    if (where != TBPM_HOST && where != TBPM_DEVICE)
+        return fail(c, TBPM_E_INVALID_ARG, "where must be TBPM_HOST or TBPM_DEVICE");
+    int rc = enter(c);
+    if (rc) return rc;
+    const size_t nnz = (size_t)std::max<int64_t>(c->H.nnz_pad, 1);
+    if (!c->d_bond_dx) {
+        rc = dalloc(c, &c->d_bond_dx, nnz);
+        if (!rc) rc = dalloc(c, &c->d_bond_dy, nnz);
+        if (rc) {
+            cudaFree(c->d_bond_dx);
+            c->d_bond_dx = nullptr;
+            return rc;
+        }
+    }
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_bond_dx, 0, nnz * sizeof(double), c->st));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_bond_dy, 0, nnz * sizeof(double), c->st));
+    const double *d_x = nullptr, *d_y = nullptr;
+    bool ox = false, oy = false;
+    int *claim = nullptr;
+    rc = stage(c, dx, (size_t)c->H.n_hop, where, const_cast<double **>(&d_x), &ox);
+    if (!rc) rc = stage(c, dy, (size_t)c->H.n_hop, where, const_cast<double **>(&d_y), &oy);
+    if (!rc) rc = dalloc(c, &claim, nnz);
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaMemsetAsync(claim, 0, nnz * sizeof(int), c->st);
+    if (!rc && e == cudaSuccess) e = cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->st);
+    if (!rc && e == cudaSuccess)
+        e = launch_bond_vectors(c->H.n_hop, c->H.bond_rows, c->H.slice_ptr, c->H.col, d_x, d_y,
+                                claim, c->d_bond_dx, c->d_bond_dy, c->d_flags, c->st);
+    int h_err = 0;
+    if (!rc && e == cudaSuccess)
+        e = cudaMemcpyAsync(&h_err, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (ox) cudaFree((void *)d_x);
+    if (oy) cudaFree((void *)d_y);
+    cudaFree(claim);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(c, TBPM_E_CUDA, std::string("bond vectors: ") + cudaGetErrorString(e));
+    if (h_err) {
+        cudaFree(c->d_bond_dx);
+        cudaFree(c->d_bond_dy);
+        c->d_bond_dx = c->d_bond_dy = nullptr;
+        return fail(c, TBPM_E_INVALID_ARG, (h_err & 2) ? "non-finite bond vector"
+                                                       : "bond list does not match the Hamiltonian");
+    }
+    c->err.clear();
+    return leave(c);
+}
+
+// AC-conductivity correlation (Sec. 2.7): for each initial state psi (n_states
+// per sample, at most 16), psi_2 = f(H) psi and psi_1b = [1 - f(H)] J_b psi
+// (FP64, Fermi operator by Chebyshev-Clenshaw, Sec. 2.2), then psi, psi_2,
+// psi_1x, psi_1y propagate as four lanes of one state group and the observer
+// records <psi_2(t)|J_a|psi_1b(t)> after every step.  The caller's states are
+// restored afterwards.
+extern "C" int tbpm_ac_correlation(tbpm_ctx *c, double z, int n_steps, double beta, double mu,
+                                   int precision, double *corr_out, int where_out, int flags)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->have_h || c->n_states < 1)
+        return fail(c, TBPM_E_STATE, "build the Hamiltonian and set states first");
+    if (!c->d_bond_dx) return fail(c, TBPM_E_STATE, "set the bond vectors first");
+    if (precision != TBPM_FP64 && precision != TBPM_FP32)
+        return fail(c, TBPM_E_INVALID_ARG, "bad precision");
+    if (n_steps < 0 || !corr_out || (where_out != TBPM_HOST && where_out != TBPM_DEVICE))
+        return fail(c, TBPM_E_INVALID_ARG, "bad output arguments");
+    if (4 * c->n_states > kMaxStates)
+        return fail(c, TBPM_E_INVALID_ARG, "at most 16 initial states for the AC correlation");
+    if (flags & TBPM_PROP_RESUME)
+        return fail(c, TBPM_E_INVALID_ARG, "the AC correlation always starts at t = 0");
+    if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(mu))
+        return fail(c, TBPM_E_INVALID_ARG, "beta must be > 0 and mu finite");
+    std::vector<double> cf;
+    int rc = fermi_coefficients(beta * c->s, mu / c->s, 1e-15, 1 << 22, cf);
+    if (rc) return fail(c, rc, "Fermi series too long (beta * s too large)");
+    rc = enter(c);
+    if (rc) return rc;
+
+    const int S = c->n_states;
+    const int64_t n_rows = c->H.n_rows, n_orb = c->n_orb;
+    const size_t v4n = (size_t)n_rows * 4;
+    double2 *v4 = nullptr, *f4 = nullptr, *bb[2] = {nullptr, nullptr}, *D = nullptr;
+    auto release = [&]() {
+        cudaFree(v4);
+        cudaFree(f4);
+        cudaFree(bb[0]);
+        cudaFree(bb[1]);
+        cudaFree(D);
+    };
+    rc = dalloc(c, &v4, v4n);
+    if (!rc) rc = dalloc(c, &f4, v4n);
+    if (!rc) rc = dalloc(c, &bb[0], v4n);
+    if (!rc) rc = dalloc(c, &bb[1], v4n);
+    if (!rc) rc = dalloc(c, &D, (size_t)4 * S * n_orb);
+    if (rc) { release(); return rc; }
+
+    // preparation values: FP64 when kept, else FP32 (arithmetic in FP64)
+    const int fp32v = c->H.val64 ? 0 : 1;
+    SellView Hp;
+    Hp.slice_ptr = c->H.slice_ptr;
+    Hp.col = c->H.col;
+    Hp.val = fp32v ? (const void *)c->H.val32 : (const void *)c->H.val64;
+    Hp.diag = fp32v ? (const void *)c->H.diag32 : (const void *)c->H.diag64;
+    const int K = (int)cf.size();
+    auto prep_fail = [&](cudaError_t e) {
+        release();
+        return fail(c, TBPM_E_CUDA, std::string("AC preparation: ") + cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaMemsetAsync(v4, 0, v4n * sizeof(double2), c->st);
+    if (e != cudaSuccess) return prep_fail(e);
+    for (int p = 0; p < S; ++p) {
+        e = launch_ac_load(c->d_psi_user, p, n_orb, c->H.user_to_row, v4, c->st);
+        if (e == cudaSuccess)
+            e = launch_current4(Hp, fp32v, c->H.cplx, n_rows, c->d_bond_dx, c->d_bond_dy, c->s, v4,
+                                c->st);
+        if (e != cudaSuccess) return prep_fail(e);
+        // Clenshaw: b_k = c_k v + 2 H~ b_{k+1} - b_{k+2}, k = K-1 .. 1;
+        // f v = c_0 v / 2 + H~ b_1 - b_2 (b_K = b_{K+1} = 0)
+        int i1 = -1, i2 = -1;              // buffers of b_{k+1}, b_{k+2}
+        for (int k = K - 1; k >= 1 && e == cudaSuccess; --k) {
+            const int o = i2 >= 0 ? i2 : (i1 == 0 ? 1 : 0);
+            e = launch_cheb_real4(Hp, fp32v, c->H.cplx, n_rows, cf[k], 2.0, -1.0, v4,
+                                  i1 >= 0 ? bb[i1] : nullptr, i2 >= 0 ? bb[i2] : nullptr, bb[o],
+                                  c->st);
+            i2 = i1;
+            i1 = o;
+        }
+        if (e == cudaSuccess)
+            e = launch_cheb_real4(Hp, fp32v, c->H.cplx, n_rows, 0.5 * cf[0], 1.0, -1.0, v4,
+                                  i1 >= 0 ? bb[i1] : nullptr, i2 >= 0 ? bb[i2] : nullptr, f4, c->st);
+        if (e == cudaSuccess) e = launch_ac_store(v4, f4, p, n_orb, c->H.user_to_row, D, c->st);
+        if (e != cudaSuccess) return prep_fail(e);
+    }
+    const size_t cnt = (size_t)c->n_samples * S * 4 * (n_steps + 1);
+    rc = dalloc(c, &c->d_ac_corr, cnt);
+    if (!rc) rc = dalloc(c, &c->d_ac_partial, (size_t)(n_rows / kAcRows) * 4 * 8);
+    if (rc) {
+        cudaFree(c->d_ac_corr);
+        c->d_ac_corr = nullptr;
+        release();
+        return rc;
+    }
+    e = cudaMemsetAsync(c->d_ac_corr, 0, cnt * sizeof(double2), c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        cudaFree(c->d_ac_corr);
+        c->d_ac_corr = nullptr;
+        return prep_fail(e);
+    }
+
+    // the four states of each p become lanes 4p .. 4p+3 (groups of width >= 4)
+    double2 *user_psi = c->d_psi_user;
+    const int user_group = c->max_group[precision];
+    free_groups(c);
+    free_outputs(c);
+    c->d_psi_user = D;
+    c->n_states = 4 * S;
+    if (c->max_group[precision] < 4) c->max_group[precision] = 4;
+    c->ac_on = true;
+    rc = tbpm_propagate(c, z, n_steps, precision, nullptr, TBPM_HOST,
+                        flags & (TBPM_PROP_PROFILE | TBPM_PROP_GRAPH | TBPM_PROP_PERSISTENT));
+    c->ac_on = false;
+    std::string err = c->err;
+    if (!rc) {
+        e = cudaMemcpyAsync(corr_out, c->d_ac_corr, cnt * sizeof(double2),
+                            where_out == TBPM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                            c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) {
+            rc = TBPM_E_CUDA;
+            err = std::string("AC correlation copy: ") + cudaGetErrorString(e);
+        }
+    }
+    // restore the caller's states
+    free_groups(c);
+    free_outputs(c);
+    c->d_psi_user = user_psi;
+    c->n_states = S;
+    c->max_group[precision] = user_group;
+    cudaFree(c->d_ac_corr);
+    cudaFree(c->d_ac_partial);
+    c->d_ac_corr = nullptr;
+    c->d_ac_partial = nullptr;
+    release();                   // the derived states D included
+    if (rc) return fail(c, rc, err);
+    c->err.clear();
+    return leave(c);
 }

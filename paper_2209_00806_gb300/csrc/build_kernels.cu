@@ -411,7 +411,7 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
         out.uniform = same != 0;
         out.h_uniform = v0 * in.inv_s;
     }
-    if (keep64 && in.n_hop > 0) {      // bond -> rows, for the adjoint's parameter gradients
+    if (in.n_hop > 0) {      // bond -> rows: the adjoint's gradients, the bond vectors
         CK(cudaMalloc(&out.bond_rows, 2 * in.n_hop * sizeof(int32_t)));
         k_bond_rows<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j,
                                                            out.user_to_row, out.bond_rows);

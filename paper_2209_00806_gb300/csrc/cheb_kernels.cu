@@ -187,10 +187,12 @@ template <> struct Val2<double> { typedef double2 type; };
 template <> struct Val2<float> { typedef float2 type; };
 
 // CX: complex matrix values (re, im) per stored entry (Peierls phases);
-// otherwise real values.
-template <typename V, int L, int SPL, bool CX>
+// otherwise real values.  RS > 1 splits each row's entries over RS adjacent
+// threads (part = 0 .. RS-1 takes entries part, part + RS, ...; shuffles add
+// the parts): long rows get RS times the gathers in flight.
+template <typename V, int L, int SPL, bool CX, int RS = 1>
 __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int l,
-                                               const V *sc)
+                                               const V *sc, int part = 0)
 {
     Cv<V, SPL> p, zz;
     if (a.variant & kVariantStreamHints) {
@@ -213,26 +215,27 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
 
     // y = H~ x: diagonal first, then the row's entries in stored order,
     // four at a time so that the gathers are in flight together.
-    const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+    const V d = part == 0 ? __ldg(reinterpret_cast<const V *>(a.H.diag) + r) : (V)0;
     Cv<V, SPL> y = ld_ro<V, L, SPL>(a.x, r, l);
 #pragma unroll
     for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
     typedef typename Val2<V>::type V2;
     const V2 *valp2 = reinterpret_cast<const V2 *>(a.H.val) + base + lr;
-    for (int k = 0; k < w; k += 4) {
+    for (int k = part; k < w; k += 4 * RS) {
         int32_t c[4];
         V h[4], hm[4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            ok[u] = k + u < w;
-            c[u] = ok[u] ? __ldg(colp + (int64_t)(k + u) * kSliceRows) : (int32_t)r;
+            const int ku = k + u * RS;
+            ok[u] = ku < w;
+            c[u] = ok[u] ? __ldg(colp + (int64_t)ku * kSliceRows) : (int32_t)r;
             hm[u] = (V)0;
             if (CX) {
                 V2 v2;
                 v2.x = (V)0;
                 v2.y = (V)0;
-                if (ok[u]) v2 = __ldg(valp2 + (int64_t)(k + u) * kSliceRows);
+                if (ok[u]) v2 = __ldg(valp2 + (int64_t)ku * kSliceRows);
                 h[u] = v2.x;
                 hm[u] = v2.y;
             } else if (a.uniform) {
@@ -240,7 +243,7 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
                 ok[u] = ok[u] && c[u] != (int32_t)r;
                 h[u] = Coef<V>::hu(a);
             } else {
-                h[u] = ok[u] ? __ldg(valp + (int64_t)(k + u) * kSliceRows) : (V)0;
+                h[u] = ok[u] ? __ldg(valp + (int64_t)ku * kSliceRows) : (V)0;
             }
         }
         Cv<V, SPL> xv[4];
@@ -260,6 +263,15 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
                 }
             }
         }
+    }
+    if (RS > 1) {           // add the parts of the row (adjacent lanes of a warp)
+#pragma unroll
+        for (int o = 1; o < RS; o <<= 1)
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                y.re[j] += __shfl_xor_sync(0xffffffffu, y.re[j], o);
+                y.im[j] += __shfl_xor_sync(0xffffffffu, y.im[j], o);
+            }
     }
     if (sc) {               // FP32 norm carry: psi -> psi * scale (per state)
 #pragma unroll
@@ -298,17 +310,21 @@ __device__ __forceinline__ int64_t block_in_order(const TermArgs &a)
 // FP32: at most 40 registers (12 blocks of 128 threads per SM; 80 for the
 // wide lanes) -- the kernel is latency-bound, so residency matters; FP64:
 // unconstrained.
-template <typename V, int L, int SPL, bool CX>
+// Thread t works on row t / (L RS), lane (t / RS) % L, part t % RS.  Rows are
+// a multiple of 1024, so a warp never straddles the last row (the part
+// shuffles see full warps).
+template <typename V, int L, int SPL, bool CX, int RS>
 __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 3) : 1) k_term(TermArgs a)
 {
     const int64_t t = block_in_order(a) * blockDim.x + threadIdx.x;
-    const int64_t r = t / L;
-    const int l = (int)(t % L);
+    const int64_t r = t / (L * RS);
+    const int l = (int)((t / RS) % L);
+    const int part = (int)(t % RS);
     if (r >= a.n_rows) return;
     const V *sc = Coef<V>::scale(a);
     if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
-    Cv<V, SPL> o = term_row<V, L, SPL, CX>(a, r, l, sc);
-    st<V, L, SPL>(a.out, r, l, o);
+    Cv<V, SPL> o = term_row<V, L, SPL, CX, RS>(a, r, l, sc, part);
+    if (part == 0) st<V, L, SPL>(a.out, r, l, o);
 }
 
 // Closing term, one row per thread like k_term, with the sums of
@@ -476,7 +492,12 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs a)
         const int64_t idx = ((int64_t)s * a.n_states + state) * (a.n_steps + 1) + step;
         a.corr[idx] = make_double2(re, im);
         a.norms[idx] = nn;
-        const double drift = fabs(nn - 1.0);
+        // drift relative to the squared norm at t = 0 (1 for normalised states;
+        // the AC-conductivity states are not normalised)
+        const int64_t ridx = (int64_t)s * a.n_states + state;
+        if (a.set_ref) a.norm_ref[ridx] = nn;
+        const double ref = a.set_ref ? nn : a.norm_ref[ridx];
+        const double drift = ref > 0.0 ? fabs(nn / ref - 1.0) : nn;
         if (!(nn == nn) || !(re == re) || !(im == im) || nn - nn != 0.0) {
             atomicOr(a.error_flags, 2);
         } else if (drift > a.hard_bound) {
@@ -484,8 +505,8 @@ __global__ void __launch_bounds__(64) k_reduce(ReduceArgs a)
         }
         if (a.scale) {
             double sc = 1.0;
-            if (drift > a.renorm_bound && nn > 0.0 && nn - nn == 0.0) {
-                sc = 1.0 / sqrt(nn);
+            if (drift > a.renorm_bound && nn > 0.0 && ref > 0.0 && nn - nn == 0.0) {
+                sc = sqrt(ref / nn);
                 atomicAdd(a.renorm_count, 1ull);
             }
             a.scale[(int64_t)s * a.B + t] = sc;
@@ -561,13 +582,21 @@ __global__ void k_get_states(const void *psi, int64_t n_orb, const int32_t *user
         dst[(int64_t)(g0 + b) * n_orb + u] = StoreC<V, 1>::get(psi, r * B + b);
 }
 
-template <typename V, int L, int SPL, bool CX>
+template <typename V, int L, int SPL, bool CX, int RS = 1>
 cudaError_t launch_term_t(const TermArgs &a, int threads, cudaStream_t st)
 {
-    const int64_t n_threads = a.n_rows * L;
+    const int64_t n_threads = a.n_rows * L * RS;
     const unsigned blocks = (unsigned)((n_threads + threads - 1) / threads);
-    k_term<V, L, SPL, CX><<<blocks, threads, 0, st>>>(a);
+    k_term<V, L, SPL, CX, RS><<<blocks, threads, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+// Row-split launch (real values, interior terms): RS from the variant bits.
+template <typename V, int L, int SPL>
+cudaError_t launch_term_split(const TermArgs &a, int threads, cudaStream_t st)
+{
+    if (a.variant & kVariantSplit4) return launch_term_t<V, L, SPL, false, 4>(a, threads, st);
+    return launch_term_t<V, L, SPL, false, 2>(a, threads, st);
 }
 
 template <typename V, int L, int SPL, bool CX>
@@ -586,6 +615,39 @@ template <bool FINAL, bool CX>
 cudaError_t dispatch_cx(const TermArgs &a, int fp32, int B, int threads, bool compute,
                         cudaStream_t st)
 {
+    if (!FINAL && !CX && (a.variant & (kVariantSplit2 | kVariantSplit4))) {
+        if (a.variant & kVariantWide) {
+            if (!fp32) {
+                switch (B) {
+                case 2: return launch_term_split<double, 1, 2>(a, threads, st);
+                case 4: return launch_term_split<double, 2, 2>(a, threads, st);
+                case 8: return launch_term_split<double, 4, 2>(a, threads, st);
+                }
+            } else {
+                switch (B) {
+                case 4: return launch_term_split<float, 1, 4>(a, threads, st);
+                case 8: return launch_term_split<float, 2, 4>(a, threads, st);
+                case 16: return launch_term_split<float, 4, 4>(a, threads, st);
+                }
+            }
+        }
+        if (!fp32) {
+            switch (B) {
+            case 1: return launch_term_split<double, 1, 1>(a, threads, st);
+            case 2: return launch_term_split<double, 2, 1>(a, threads, st);
+            case 4: return launch_term_split<double, 4, 1>(a, threads, st);
+            case 8: return launch_term_split<double, 8, 1>(a, threads, st);
+            }
+        } else {
+            switch (B) {
+            case 1: return launch_term_split<float, 1, 1>(a, threads, st);
+            case 2: return launch_term_split<float, 1, 2>(a, threads, st);
+            case 4: return launch_term_split<float, 2, 2>(a, threads, st);
+            case 8: return launch_term_split<float, 4, 2>(a, threads, st);
+            case 16: return launch_term_split<float, 8, 2>(a, threads, st);
+            }
+        }
+    }
     if (!FINAL && !CX && (a.variant & kVariantWide)) {
         // one thread per row and 32-byte lanes: fewer lanes share the index loads
         if (!fp32) {

@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <complex>
 #include <vector>
 
@@ -60,6 +62,94 @@ int bessel_miller(double z, double tol, int max_terms, double *J, int *n_terms)
 //   gbar_N = 0.
 // The phase exp(-i E_k n tau) advances by one rotation per n and is
 // re-anchored from cos/sin every 64 steps.
+// In-place radix-2 complex FFT, X_k = sum_n x_n e^{-2 pi i n k / N}, N a power
+// of two (iterative Cooley-Tukey: bit reversal, then butterflies).
+static void fft(std::vector<std::complex<double>> &x)
+{
+    const size_t n = x.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(x[i], x[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = -2.0 * M_PI / (double)len;
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> w(cos(ang * (double)k), sin(ang * (double)k));
+                const std::complex<double> u = x[i + k], v = x[i + k + len / 2] * w;
+                x[i + k] = u + v;
+                x[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// Fermi function on the rescaled axis, 1 / (e^{b (x - m)} + 1), without overflow.
+static double fermi(double x, double b, double m)
+{
+    const double a = b * (x - m);
+    if (a > 0.0) {
+        const double e = exp(-a);
+        return e / (1.0 + e);
+    }
+    return 1.0 / (1.0 + exp(a));
+}
+
+// c_k = (2/N) sum_n f(cos(2 pi n / N)) cos(2 pi n k / N): the trapezoid rule of
+// c_k = (2/pi) int_0^pi f(cos t) cos(k t) dt, by FFT (Sec. 2.2).  N doubles
+// until it is at least 4 (K + 1) for the K kept terms (|c_k| > tol max|c|).
+int fermi_coefficients(double beta_s, double mu_s, double tol, int k_max, std::vector<double> &c)
+{
+    if (!(beta_s > 0.0) || !std::isfinite(beta_s) || !std::isfinite(mu_s) || !(tol > 0.0) ||
+        k_max < 1)
+        return TBPM_E_INVALID_ARG;
+    for (size_t n = 1024;; n *= 2) {
+        std::vector<std::complex<double>> x(n);
+        for (size_t i = 0; i < n; ++i)
+            x[i] = fermi(cos(2.0 * M_PI * (double)i / (double)n), beta_s, mu_s);
+        fft(x);
+        double cmax = 0.0;
+        for (size_t k = 0; k < n / 2; ++k) cmax = std::max(cmax, fabs(x[k].real()));
+        size_t K = 1;
+        for (size_t k = 0; k < n / 2; ++k)
+            if (fabs(x[k].real()) > tol * cmax) K = k + 1;
+        if (4 * (K + 1) <= n || n >= (size_t)16 * k_max) {
+            if (K > (size_t)k_max) return TBPM_E_UNSUPPORTED;
+            c.resize(K);
+            for (size_t k = 0; k < K; ++k) c[k] = 2.0 * x[k].real() / (double)n;
+            return TBPM_OK;
+        }
+    }
+}
+
+// Re sigma(omega) = norm (e^{-beta omega} - 1) / omega
+//                   * int_0^T e^{-eta t} sin(omega t) 2 Im C(t) dt   (Sec. 2.7, Eq. AC)
+// by the trapezoid rule on t_n = n tau, for each row of corr.
+int ac_conductivity(const double *corr, int n_rows, int n_steps, double tau, double beta,
+                    double eta, const double *omegas, int n_omega, double norm, double *sigma)
+{
+    if (!corr || !omegas || !sigma || n_rows < 1 || n_steps < 1 || n_omega < 1 ||
+        !(tau > 0.0) || !(beta > 0.0) || !(eta >= 0.0))
+        return TBPM_E_INVALID_ARG;
+    for (int k = 0; k < n_omega; ++k)
+        if (!(omegas[k] > 0.0) || !std::isfinite(omegas[k])) return TBPM_E_INVALID_ARG;
+    for (int row = 0; row < n_rows; ++row) {
+        const double *cr = corr + (size_t)row * (n_steps + 1) * 2;
+        for (int k = 0; k < n_omega; ++k) {
+            const double w = omegas[k];
+            double acc = 0.0;
+            for (int n = 1; n <= n_steps; ++n) {
+                const double t = tau * n;
+                const double g = exp(-eta * t) * sin(w * t) * 2.0 * cr[2 * n + 1];
+                acc += (n == n_steps ? 0.5 : 1.0) * g;
+            }
+            sigma[(size_t)row * n_omega + k] = norm * (exp(-beta * w) - 1.0) / w * tau * acc;
+        }
+    }
+    return TBPM_OK;
+}
+
 int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_min,
                 double e_max, double *gbar_out)
 {
@@ -138,4 +228,24 @@ extern "C" int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, doubl
         return TBPM_E_INVALID_ARG;
     if (window != TBPM_WINDOW_HANN) return TBPM_E_UNSUPPORTED;
     return tbpm::dos_adjoint(dl_dd, n_e, n_steps, tau, e_min, e_max, gbar_out);
+}
+
+extern "C" int tbpm_fermi_coefficients(double beta_s, double mu_s, int k_max, double *c_out,
+                                       int *n_terms)
+{
+    if (!n_terms || k_max < 1) return TBPM_E_INVALID_ARG;
+    std::vector<double> c;
+    const int rc = tbpm::fermi_coefficients(beta_s, mu_s, 1e-15, k_max, c);
+    if (rc) return rc;
+    *n_terms = (int)c.size();
+    if (c_out) memcpy(c_out, c.data(), c.size() * sizeof(double));
+    return TBPM_OK;
+}
+
+extern "C" int tbpm_ac_conductivity(const double *corr, int n_rows, int n_steps, double tau,
+                                    double beta, double eta, const double *omegas, int n_omega,
+                                    double norm, double *sigma_out)
+{
+    return tbpm::ac_conductivity(corr, n_rows, n_steps, tau, beta, eta, omegas, n_omega, norm,
+                                 sigma_out);
 }

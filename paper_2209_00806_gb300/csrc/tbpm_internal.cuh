@@ -29,6 +29,8 @@ constexpr int kVariantTma = 4;          // persistent TMA-staged term kernel
 constexpr int kVariantFused = 8;        // all terms of a step in one wavefront launch
 constexpr int kVariantFusedTileShift = 4;  // bits 4-5: fused tile rows x 4^k
 constexpr int kVariantWide = 64;        // term kernel with 32-byte lanes
+constexpr int kVariantSplit2 = 128;     // each row's entries over 2 threads
+constexpr int kVariantSplit4 = 256;     // each row's entries over 4 threads
 
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.
@@ -83,11 +85,59 @@ struct ReduceArgs {
     double *norms;                   // [n_samples][n_states][n_steps + 1]
     double *scale;                   // [n_samples * B] next-step scale (FP32) or nullptr
     float *scale_f;                  // its FP32 copy
-    double renorm_bound;             // |<phi|phi> - 1| above which to renormalise
+    double renorm_bound;             // |<phi|phi>/ref - 1| above which to renormalise
     double hard_bound;               // above which to flag NORM_DRIFT
     unsigned long long *renorm_count;
     int *error_flags;                // bit 0 drift, bit 1 non-finite
+    double *norm_ref;                // [n_samples][n_states] squared norm at t = 0
+    int set_ref;                     // this pass records norm_ref (the C_0 pass)
 };
+
+// AC-conductivity correlation (Sec. 2.7).  States of one random state p sit
+// in four adjacent lanes 4q .. 4q+3 of a group: psi(t), psi_2(t) = e^{-iHt} f psi,
+// psi_1x(t), psi_1y(t) with psi_1b = e^{-iHt} (1 - f) J_b psi.  After each time
+// step the observer forms, per row, g_a = sum_c H~_rc d^a_rc psi_2,c and
+// conj(g_a) psi_1b,r; the reduction multiplies by i s, so that the entry is
+// <J_a psi_2|psi_1b> = <psi_2|J_a|psi_1b> with (J_a)_rc = -i s H~_rc d^a_rc and
+// d_rc = r_c - r_r the bond vector of the stored entry (nm).
+constexpr int kAcRows = 128;         // rows per observer block
+struct AcArgs {
+    SellView H;                      // values of the group precision
+    const double *dx, *dy;           // [nnz_pad] bond vector of each stored entry (nm)
+    const void *psi;                 // current buffer of the group, [row][B]
+    const double *scale;             // FP32 norm carry [n_samples][B] or nullptr
+    const int32_t *chunk_sample;
+    int64_t n_rows;
+    int B;                           // multiple of 4
+    double *block_partial;           // [n_rows / kAcRows][B / 4][8]
+};
+struct AcReduceArgs {
+    const double *block_partial;
+    const int64_t *sample_chunk_off; // [n_samples + 1] in 1024-row chunks
+    int n_samples, B, group_state0, n_states, n_steps;
+    const int *step;                 // per sample, already advanced by k_reduce
+    double s;
+    double2 *corr_ac;                // [n_samples][n_states / 4][4][n_steps + 1]
+};
+cudaError_t launch_ac_observe(const AcArgs &a, int fp32, int cplx, cudaStream_t st);
+cudaError_t launch_ac_reduce(const AcReduceArgs &a, cudaStream_t st);
+// Preparation of the AC states, FP64, four lanes per row ([n_rows][4] complex):
+// lanes 0 and 1 <- psi_p; lanes 2, 3 <- J_x psi_p, J_y psi_p; Fermi Clenshaw
+// terms out = c v + gamma H~ x + zeta z on all four lanes; the result goes
+// back to the caller's layout as the four states of p.
+cudaError_t launch_ac_load(const double2 *psi_user, int p, int64_t n_orb,
+                           const int32_t *user_to_row, double2 *v4, cudaStream_t st);
+cudaError_t launch_current4(SellView H, int fp32_vals, int cplx, int64_t n_rows,
+                            const double *dxe, const double *dye, double s, double2 *v4,
+                            cudaStream_t st);
+cudaError_t launch_cheb_real4(SellView H, int fp32_vals, int cplx, int64_t n_rows, double c,
+                              double gamma, double zeta, const double2 *v, const double2 *x,
+                              const double2 *z, double2 *out, cudaStream_t st);
+cudaError_t launch_ac_store(const double2 *v4, const double2 *f4, int p, int64_t n_orb,
+                            const int32_t *user_to_row, double2 *out_user, cudaStream_t st);
+cudaError_t launch_bond_vectors(int64_t n_hop, const int32_t *bond_rows, const int64_t *slice_ptr,
+                                const int32_t *col, const double *dx, const double *dy,
+                                int *claim, double *dxe, double *dye, int *err, cudaStream_t st);
 
 // One backward (adjoint) term with gradient accumulation, FP64:
 //   out = c psi + gamma (-i) (H~ x) + z [+ gbar_step psi0],
@@ -195,7 +245,7 @@ struct BuildOutput {
     double *diag64 = nullptr;
     float *diag32 = nullptr;
     int32_t *chunk_sample = nullptr; // [n_rows / kChunkRows]
-    int32_t *bond_rows = nullptr;    // [2 n_hop] rows of each bond (kept with FP64 values)
+    int32_t *bond_rows = nullptr;    // [2 n_hop] rows of each bond
     int64_t n_hop = 0;
     double gershgorin = 0.0;
     int max_width = 0;
@@ -216,6 +266,10 @@ void set_thread_error(const std::string &m);
 
 // Host math (host_math.cpp).
 int bessel_miller(double z, double tol, int max_terms, double *J, int *n_terms);
+// Chebyshev coefficients of the Fermi function on the rescaled axis (Sec. 2.2).
+int fermi_coefficients(double beta_s, double mu_s, double tol, int k_max, std::vector<double> &c);
+int ac_conductivity(const double *corr, int n_rows, int n_steps, double tau, double beta,
+                    double eta, const double *omegas, int n_omega, double norm, double *sigma);
 int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_min,
                 double e_max, double *gbar_out);
 

@@ -87,6 +87,22 @@ class Propagator:
         N.tbpm_propagate(self.ctx, float(z), int(n_steps), precision, out, None, flags)
         return out
 
+    # c1, c3 (Sec. 2.7)
+    def set_bond_vectors(self, dr):
+        """Bond vectors r_j - r_i [n_hop, >= 2] in nm, in bond-list order."""
+        dr = np.asarray(dr, dtype=np.float64)
+        N.tbpm_set_bond_vectors(self.ctx, np.ascontiguousarray(dr[:, 0]),
+                                np.ascontiguousarray(dr[:, 1]))
+        return self
+
+    def ac_correlation(self, z, n_steps, beta, mu=0.0, precision=N.TBPM_FP64, flags=0):
+        """<psi_2(t)|J_a|psi_1b(t)> as complex128 [n_samples, n_states, 4, n_steps + 1],
+        ab = xx, xy, yx, yy."""
+        out = np.empty((self.n_samples, self.n_states, 4, n_steps + 1), dtype=np.complex128)
+        N.tbpm_ac_correlation(self.ctx, float(z), int(n_steps), float(beta), float(mu),
+                              precision, out, None, flags)
+        return out
+
     def correlation(self):
         out = np.empty((self.n_samples, self.stats()["n_steps"] + 1), dtype=np.complex128)
         N.tbpm_correlation(self.ctx, out)
@@ -138,6 +154,25 @@ def dos_adjoint(dl_dd, n_steps, tau, e_min, e_max, window=N.TBPM_WINDOW_HANN):
     d = np.ascontiguousarray(dl_dd, dtype=np.float64)
     out = np.empty(n_steps + 1, dtype=np.complex128)
     N.tbpm_dos_adjoint(d, d.shape[0], n_steps, tau, window, e_min, e_max, out)
+    return out
+
+
+def fermi_coefficients(beta_s, mu_s):
+    """Chebyshev coefficients c_0 .. c_{K-1} of the Fermi function on the
+    rescaled axis (c_0/2 convention; host FP64)."""
+    return N.tbpm_fermi_coefficients(float(beta_s), float(mu_s))
+
+
+def ac_conductivity(corr, tau, beta, eta, omegas, norm):
+    """Re sigma [..., n_omega] for correlation rows corr [..., n_steps + 1]
+    (host FP64; units e^2/hbar with norm = N_orb / area)."""
+    c = np.ascontiguousarray(corr, dtype=np.complex128)
+    lead = c.shape[:-1]
+    rows = int(np.prod(lead)) if lead else 1
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    out = np.empty(lead + (om.shape[0],))
+    N.tbpm_ac_conductivity(c, rows, c.shape[-1] - 1, float(tau), float(beta), float(eta), om,
+                           om.shape[0], float(norm), out)
     return out
 
 

@@ -36,6 +36,7 @@ class Sample:
     hop_v: np.ndarray                  # float64 [n_hop] (eV), real hoppings
     pos: np.ndarray | None = None      # float64 [n_orb, 2] (nm), optional
     meta: dict = field(default_factory=dict)
+    dr: np.ndarray | None = None       # float64 [n_hop, 2] bond vectors r_j - r_i (nm)
 
     @property
     def n_hop(self) -> int:
@@ -84,11 +85,16 @@ def graphene(L1: int, L2: int, *, pbc: bool = True, t: float = T_NN,
         onsite = rng.uniform_range(seed, rng.ONSITE, n_full, -0.5 * onsite_w, 0.5 * onsite_w)
 
     pos = None
+    dr = None
     if with_pos:
         pos = np.empty((n_full, 2))
         origin = n1[:, None] * A1[None, :] + n2[:, None] * A2[None, :]
         pos[0::2] = origin
         pos[1::2] = origin + (A1 + A2) / 3.0
+        # the three reduced hoppings' vectors (the periodic image of a wrapped
+        # bond is the nearest one)
+        b1 = (A1 + A2) / 3.0
+        dr = np.tile(np.stack([b1, A1 - b1, A2 - b1]), (n_cell, 1))
 
     n_vac = int(round(vacancy_frac * n_full))
     if n_vac > 0:
@@ -111,7 +117,7 @@ def graphene(L1: int, L2: int, *, pbc: bool = True, t: float = T_NN,
                   hop_i=np.ascontiguousarray(hi[keep_b]),
                   hop_j=np.ascontiguousarray(hj[keep_b]),
                   hop_v=np.ascontiguousarray(hv[keep_b]),
-                  pos=pos,
+                  pos=pos, dr=None if dr is None else np.ascontiguousarray(dr[keep_b]),
                   meta=dict(kind="graphene", L1=L1, L2=L2, pbc=pbc, t=t,
                             onsite_w=onsite_w, vacancies=n_vac, bond_sigma=bond_sigma,
                             seed=seed))
@@ -168,7 +174,7 @@ def permute(sample: Sample, perm: np.ndarray) -> Sample:
     pos = None if sample.pos is None else sample.pos[inv]
     return Sample(n_orb=sample.n_orb, onsite=onsite, hop_i=perm[sample.hop_i],
                   hop_j=perm[sample.hop_j], hop_v=sample.hop_v.copy(), pos=pos,
-                  meta=dict(sample.meta, permuted=True))
+                  meta=dict(sample.meta, permuted=True), dr=sample.dr)
 
 
 def concat(samples: list[Sample]) -> tuple[Sample, np.ndarray]:
@@ -187,8 +193,11 @@ def concat(samples: list[Sample]) -> tuple[Sample, np.ndarray]:
     hi = np.concatenate([s.hop_i + offs[k] for k, s in enumerate(samples)])
     hj = np.concatenate([s.hop_j + offs[k] for k, s in enumerate(samples)])
     hv = np.concatenate([s.hop_v for s in samples])
+    dr = None
+    if all(s.dr is not None or s.pos is not None for s in samples):
+        dr = np.concatenate([bond_vectors(s) for s in samples])
     return Sample(n_orb=n, onsite=onsite if any_onsite else None, hop_i=hi, hop_j=hj,
-                  hop_v=hv, meta=dict(kind="batch", n_samples=len(samples))), offs
+                  hop_v=hv, meta=dict(kind="batch", n_samples=len(samples)), dr=dr), offs
 
 
 def twisted_bilayer(side_nm: float, theta_deg: float = 1.05, cutoff_nm: float = 0.6,
@@ -255,4 +264,14 @@ def peierls(sample: Sample, B_tesla: float) -> Sample:
     phase = np.pi * B_tesla * (x[j] - x[i]) * (y[j] + y[i]) / FLUX_QUANTUM
     hv = sample.hop_v.astype(np.complex128) * np.exp(1j * phase)
     return Sample(n_orb=sample.n_orb, onsite=sample.onsite, hop_i=i, hop_j=j, hop_v=hv,
-                  pos=sample.pos, meta=dict(sample.meta, B_tesla=B_tesla))
+                  pos=sample.pos, meta=dict(sample.meta, B_tesla=B_tesla), dr=sample.dr)
+
+
+def bond_vectors(sample: Sample) -> np.ndarray:
+    """r_j - r_i [n_hop, 2] of every bond: the stored vectors when the
+    generator made them (periodic images), else differences of positions."""
+    if sample.dr is not None:
+        return sample.dr
+    if sample.pos is None:
+        raise ValueError("bond vectors need positions")
+    return sample.pos[sample.hop_j, :2] - sample.pos[sample.hop_i, :2]

@@ -1,6 +1,7 @@
 """CPU checks of the C-ABI library: it builds for sm_103a, loads, exports
 every entry point ``include/tbpm.h`` declares, and its pure-host functions
-(Bessel table, DOS transform) agree with the oracle and SciPy.  No GPU."""
+(Bessel table, DOS transform, Fermi coefficients, conductivity transform)
+agree with the oracle and SciPy.  No GPU."""
 import math
 import re
 from pathlib import Path
@@ -103,3 +104,33 @@ def test_dos_adjoint_vs_oracle(native):
         g = dos_adjoint(dl, n, 0.165, -9.5, 9.5)
         ref = oracle.dos_adjoint(dl, n, 0.165, -9.5, 9.5)
         assert np.max(np.abs(g - ref)) < 1e-11 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("beta_s,mu_s", [(367.0, 0.0), (40.0, 0.2), (3.0, -0.5)])
+def test_fermi_coefficients_vs_oracle(native, beta_s, mu_s):
+    from oracle import ac
+    from paper_2209_00806_gb300 import fermi_coefficients
+    c = fermi_coefficients(beta_s, mu_s)
+    ref = ac.fermi_coefficients(beta_s, mu_s)
+    assert len(c) == len(ref)
+    assert np.max(np.abs(c - ref)) < 1e-14
+    with pytest.raises(native.TbpmError):
+        fermi_coefficients(-1.0, 0.0)
+
+
+def test_ac_conductivity_transform_vs_oracle(native):
+    from oracle import ac
+    from paper_2209_00806_gb300 import ac_conductivity
+    gen = np.random.default_rng(4)
+    tau, n = 0.17, 900
+    E = gen.uniform(-2, 2, (3, 12))
+    w = gen.normal(size=(3, 12)) + 1j * gen.normal(size=(3, 12))
+    t = tau * np.arange(n + 1)
+    corr = np.stack([np.exp(1j * np.outer(t, E[r])) @ w[r] for r in range(3)])
+    om = np.linspace(0.05, 3.0, 37)
+    got = ac_conductivity(corr, tau, 12.0, 0.01, om, 2.5)
+    ref = ac.ac_conductivity(corr, tau, 12.0, 0.01, om, 2.5)
+    assert got.shape == (3, 37)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    with pytest.raises(native.TbpmError):
+        ac_conductivity(corr, tau, 12.0, 0.01, np.array([0.0]), 1.0)

@@ -53,7 +53,8 @@ def test_gpu_fp64_disordered_vacancies_several_groups(tb):
 
 
 @pytest.mark.parametrize("cfg", [(1, 64, 0), (2, 128, 1), (8, 256, 3), (4, 256, 2), (4, 256, 4),
-                                 (8, 256, 5), (1, 256, 4), (4, 128, 65), (2, 64, 64)])
+                                 (8, 256, 5), (1, 256, 4), (4, 128, 65), (2, 64, 64),
+                                 (1, 128, 129), (4, 256, 257), (8, 64, 385), (2, 128, 193)])
 def test_gpu_fp64_ragged_rows_launch_shapes(tb, cfg):
     smp = lattice.random_graph(3001, 9000, seed=3, onsite_w=2.0)   # degrees 0 .. ~15
     H = exact.dense_h(smp)
@@ -94,7 +95,8 @@ def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
 
 
 @pytest.mark.parametrize("cfg", [(16, 128, 3), (4, 256, 1), (2, 64, 0), (16, 256, 4), (4, 256, 5),
-                                 (2, 256, 4), (1, 256, 0), (16, 128, 65), (4, 128, 64)])
+                                 (2, 256, 4), (1, 256, 0), (16, 128, 65), (4, 128, 64),
+                                 (1, 128, 129), (8, 256, 257), (16, 128, 321), (4, 64, 193)])
 def test_gpu_fp32_launch_shapes(tb, cfg):
     smp = lattice.random_graph(2500, 7000, seed=9, onsite_w=2.0)
     H = exact.dense_h(smp)
@@ -113,7 +115,8 @@ def test_gpu_autotune_picks_a_valid_shape(tb):
         p.set_phase_states(th)
         best = p.autotune(Z, precision=1, probe_steps=2)
         assert best["group"] in (2, 4) and best["threads"] in (128, 256)
-        assert best["variant"] in (0, 1, 3, 4, 5, 8, 24, 40, 65) and best["ms_per_step"] > 0
+        assert best["variant"] in (0, 1, 3, 4, 5, 8, 24, 40, 65, 129, 257, 193, 321)
+        assert best["ms_per_step"] > 0
         c = p.propagate(Z, 30, 1)
     ref = run_oracle(smp, 9.5, th, 30)
     assert np.max(np.abs(c[0] - ref)) < 2e-5
@@ -365,7 +368,8 @@ def test_gpu_ldos_single_site_states(tb):
 def test_gpu_twisted_bilayer_wide_rows(tb, prec):
     """Twisted bilayer flake: ~63 entries per row, asymmetric spectrum
     (s = 12 eV), layer-by-layer numbering; with and without RCM order, plain,
-    wide-lane and TMA kernels, against the oracle and exact diagonalisation."""
+    wide-lane, row-split and TMA kernels, against the oracle and exact
+    diagonalisation."""
     w = workloads.twisted_bilayer_flake(side_nm=5.0, n_steps=60)
     smp = w.sample
     th = w.thetas()[0][:3]
@@ -375,7 +379,7 @@ def test_gpu_twisted_bilayer_wide_rows(tb, prec):
     assert np.max(np.abs(ref[0] - ed)) < 1e-11
     tol = 1e-10 if prec == 0 else 2e-5
     for bflags in (0, 8):
-        for cfg in ((2, 128, 1), (2, 128, 65), (2, 128, 4)):
+        for cfg in ((2, 128, 1), (2, 128, 65), (2, 128, 4), (2, 128, 257), (2, 64, 321)):
             c, st, _, _ = run_gpu(tb, smp, w.s, th, w.n_steps, precision=prec, bflags=bflags,
                                   cfg=cfg)
             assert np.max(np.abs(c[0] - ref)) < tol, (bflags, cfg)

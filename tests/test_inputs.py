@@ -120,3 +120,18 @@ def test_peierls_needs_positions_and_open_boundaries():
         lattice.peierls(lattice.graphene(4, 4, pbc=False), 10.0)
     with pytest.raises(ValueError):
         lattice.peierls(lattice.graphene(4, 4, pbc=True, with_pos=True), 10.0)
+
+
+def test_graphene_bond_vectors():
+    """Open flakes: the generator's bond vectors are differences of the
+    positions; periodic lattices: every bond vector has the C-C length (the
+    nearest image), also across the wrap."""
+    a_cc = np.linalg.norm((lattice.A1 + lattice.A2) / 3.0)
+    op = lattice.graphene(7, 5, pbc=False, with_pos=True, vacancy_frac=0.05, seed=3)
+    ref = op.pos[op.hop_j] - op.pos[op.hop_i]
+    assert np.max(np.abs(op.dr - ref)) < 1e-14
+    per = lattice.graphene(6, 5, pbc=True, with_pos=True)
+    # (the printed cell vectors are rounded: the three bond lengths agree to 1e-5)
+    assert np.allclose(np.linalg.norm(per.dr, axis=1), a_cc, rtol=1e-4)
+    wrapped = np.linalg.norm(per.pos[per.hop_j] - per.pos[per.hop_i], axis=1) > 2 * a_cc
+    assert wrapped.sum() == 6 + 5       # one wrapped bond per edge cell

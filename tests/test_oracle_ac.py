@@ -56,11 +56,11 @@ def test_oracle_ac_current_is_commutator(B):
     for a in range(2):
         X = np.diag(smp.pos[:, a])
         ref = -1j * (H @ X - X @ H) @ v
-        got = ac.current_apply(smp, smp.pos[:, a], v)
+        got = ac.current_apply(smp, lattice.bond_vectors(smp)[:, a], v)
         assert np.max(np.abs(got - ref)) < 1e-13
         # Hermitian
         lhs = np.vdot(u, got)
-        rhs = np.vdot(ac.current_apply(smp, smp.pos[:, a], u), v)
+        rhs = np.vdot(ac.current_apply(smp, lattice.bond_vectors(smp)[:, a], u), v)
         assert abs(lhs - rhs) < 1e-13
 
 
@@ -69,7 +69,7 @@ def test_oracle_ac_correlation_vs_exact_diagonalisation(B):
     smp = _flake(B)
     s, beta, mu, n_steps = 9.0, 6.0, -0.2, 40
     psi0 = oracle.phase_states(rng.phases(8, 2, smp.n_orb))
-    got = ac.ac_correlation(smp, s, Z, n_steps, beta, mu, smp.pos, psi0)
+    got = ac.ac_correlation(smp, s, Z, n_steps, beta, mu, lattice.bond_vectors(smp), psi0)
     H = exact.dense_h(smp)
     E, U = np.linalg.eigh(H)
     f = U @ np.diag(ac.fermi(E, beta, mu)) @ U.conj().T
