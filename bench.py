@@ -47,6 +47,8 @@ def parse():
                          "differentiable: 512^2 graphene, DOS loss, FP64 forward + adjoint; "
                          "tbg: twisted bilayer flake (--side nm), 6 A cutoff, 8 states")
     ap.add_argument("--side", type=float, default=200.0, help="tbg flake side in nm")
+    ap.add_argument("--order", default="auto", choices=["auto", "natural", "rcm", "cluster"],
+                    help="row order of the build (auto: cluster for tbg, natural otherwise)")
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
@@ -106,7 +108,10 @@ def config_dict(w, args, world):
     elif args.workload == "tbg":
         d.update(workload=f"twisted_bilayer_{args.side:g}nm", twist_deg=1.05, cutoff_A=6,
                  entries_per_row=round(2 * w.sample.n_hop / w.sample.n_orb, 1),
-                 row_order="reverse Cuthill-McKee (interleaves the layers)",
+                 row_order={"natural": "layer by layer", "rcm": "reverse Cuthill-McKee",
+                            "cluster": "RCM, then 128-row breadth-first balls (compact patches)",
+                            "auto": "RCM, then 128-row breadth-first balls (compact patches)"}
+                 [args.order],
                  l2=f"inputs larger than L2 (state vectors {cs32:.0f} MB FP32, matrix "
                     f"{w.sample.n_hop * 2 * 8 / 1e6:.0f} MB)")
     else:
@@ -297,7 +302,10 @@ def run_gb300(args):
     # precisions measured per workload: the first one is the headline `value`
     legs = {"disordered": [N.TBPM_FP32, N.TBPM_FP64], "batched": [N.TBPM_FP32],
             "graphene_dos": [N.TBPM_FP64], "tbg": [N.TBPM_FP32]}[args.workload]
-    bflags = N.TBPM_BUILD_REORDER_RCM if args.workload == "tbg" else 0
+    order = args.order if args.order != "auto" else ("cluster" if args.workload == "tbg"
+                                                      else "natural")
+    bflags = {"natural": 0, "rcm": N.TBPM_BUILD_REORDER_RCM,
+              "cluster": N.TBPM_BUILD_REORDER_CLUSTER}[order]
     graph = args.workload == "graphene_dos"     # launch-latency bound: replay step graphs
 
     def one_step(precision, flags):

@@ -65,6 +65,10 @@ extern "C" {
 #define TBPM_BUILD_NO_UNIFORM 16  /* do not use the one-value form when every hopping
                                      is equal (by default the term kernels then skip
                                      the value loads) */
+#define TBPM_BUILD_REORDER_CLUSTER 64 /* RCM, then balls of 128 rows grown breadth-
+                                         first in RCM order: compact patches on
+                                         geometric lattices keep long-row gathers
+                                         in L1 */
 #define TBPM_BUILD_COMPLEX_HOPS 32 /* hop_v holds complex hoppings, (re, im) double
                                       pairs (complex128): Peierls phases of a
                                       magnetic field (Sec. 2.1) */

@@ -40,6 +40,7 @@ TBPM_BUILD_NO_FP32 = 4
 TBPM_BUILD_REORDER_RCM = 8
 TBPM_BUILD_NO_UNIFORM = 16
 TBPM_BUILD_COMPLEX_HOPS = 32
+TBPM_BUILD_REORDER_CLUSTER = 64
 TBPM_PROP_PROFILE = 1
 TBPM_PROP_GRAPH = 2
 TBPM_PROP_RESUME = 4

@@ -276,6 +276,54 @@ void rcm_sample(int64_t lo, int64_t hi, const std::vector<int64_t> &adj_ptr,
     for (int64_t k = 0; k < n; ++k) perm[lo + order[n - 1 - k]] = (int32_t)k;
 }
 
+// Cluster order on top of RCM: walk the nodes in RCM order; each node not
+// yet placed seeds a breadth-first ball of up to kClusterRows unplaced nodes
+// (neighbours taken in RCM order), and the ball's nodes follow in RCM order.
+// On geometric lattices a ball is a compact patch, so a block of rows
+// gathers from a few hundred distinct rows (the patch and its rim) instead
+// of the two RCM fronts around it: the gathers stay in L1.
+constexpr int kClusterRows = 128;
+
+void cluster_sample(int64_t lo, int64_t hi, const std::vector<int64_t> &adj_ptr,
+                    const std::vector<int32_t> &adj, std::vector<int32_t> &perm)
+{
+    const int64_t n = hi - lo;
+    std::vector<int32_t> by_rcm(n);                // RCM position -> local node
+    for (int64_t u = 0; u < n; ++u) by_rcm[perm[lo + u]] = (int32_t)u;
+    std::vector<char> placed(n, 0);
+    std::vector<int32_t> ball, nb, out;
+    out.reserve(n);
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t seed = by_rcm[k];
+        if (placed[seed]) continue;
+        ball.clear();
+        ball.push_back(seed);
+        placed[seed] = 1;
+        for (size_t head = 0; head < ball.size() && ball.size() < (size_t)kClusterRows; ++head) {
+            const int64_t u = ball[head];
+            nb.clear();
+            for (int64_t e = adj_ptr[lo + u]; e < adj_ptr[lo + u + 1]; ++e) {
+                const int32_t v = (int32_t)(adj[e] - lo);
+                if (!placed[v]) nb.push_back(v);
+            }
+            std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+                return perm[lo + a] < perm[lo + b];
+            });
+            nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+            for (int32_t v : nb) {
+                if (ball.size() >= (size_t)kClusterRows) break;
+                placed[v] = 1;
+                ball.push_back(v);
+            }
+        }
+        std::sort(ball.begin(), ball.end(), [&](int32_t a, int32_t b) {
+            return perm[lo + a] < perm[lo + b];
+        });
+        out.insert(out.end(), ball.begin(), ball.end());
+    }
+    for (int64_t k = 0; k < n; ++k) perm[lo + out[k]] = (int32_t)k;
+}
+
 }  // namespace
 
 void tbpm::set_thread_error(const std::string &m) { g_last_error = m; }
@@ -372,7 +420,7 @@ extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *
 
     // optional reverse Cuthill-McKee order per sample (host)
     std::vector<int32_t> perm;
-    if (flags & TBPM_BUILD_REORDER_RCM) {
+    if (flags & (TBPM_BUILD_REORDER_RCM | TBPM_BUILD_REORDER_CLUSTER)) {
         std::vector<int64_t> hi(n_hop), hj(n_hop);
         if (where == TBPM_DEVICE) {
             CUDA_OR_FAIL(c, cudaMemcpy(hi.data(), hop_i, n_hop * sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -401,7 +449,10 @@ extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *
                     if (adj[e] < off[k] || adj[e] >= off[k + 1])
                         return fail(c, TBPM_E_INVALID_ARG, "invalid bond list: bond joins two samples");
         perm.assign(n_orb, 0);
-        for (int k = 0; k < n_samples; ++k) rcm_sample(off[k], off[k + 1], ptr, adj, perm);
+        for (int k = 0; k < n_samples; ++k) {
+            rcm_sample(off[k], off[k + 1], ptr, adj, perm);
+            if (flags & TBPM_BUILD_REORDER_CLUSTER) cluster_sample(off[k], off[k + 1], ptr, adj, perm);
+        }
     }
 
     // stage inputs on the device
@@ -1520,7 +1571,7 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
     for (int B = cap; B >= 1; B /= 2)
         if (B <= c->n_states && (B >= 2 || c->n_states == 1)) widths.push_back(B);
     if (widths.empty()) widths.push_back(1);
-    const int thread_opts[] = {128, 256};
+    const int thread_opts[] = {64, 128, 256};
     const int variant_opts[] = {0, kVariantZigZag, kVariantZigZag | kVariantStreamHints,
                                 kVariantZigZag | kVariantWide,
                                 kVariantZigZag | kVariantSplit2, kVariantZigZag | kVariantSplit4,

@@ -141,7 +141,10 @@ def test_gpu_ac_states_restored_and_errors(tb):
 def test_gpu_ac_conductivity_of_graphene_is_universal(tb):
     """Pristine periodic graphene (256 x 256 cells, 131,072 orbitals), T = 300 K,
     mu = 0: in the Dirac regime 2 mu << hbar omega << |t| the optical
-    conductivity per spin is e^2 / (8 hbar); FP32 states, 2048 steps."""
+    conductivity per spin is e^2 / (8 hbar); FP32 states, 2048 steps, damping
+    eta = 0.1 eV (the E -> 0+ of the Kubo integral; it smooths the discrete
+    transitions of the finite sample).  The oracle gives 0.93-1.08 of the
+    universal value on the same state at 0.5-1.2 eV."""
     L = 256
     smp = lattice.graphene(L, L, pbc=True, with_pos=True)
     s, beta, mu, n = 9.0, 1.0 / (8.617333262e-5 * 300.0), 0.0, 2048
@@ -154,6 +157,9 @@ def test_gpu_ac_conductivity_of_graphene_is_universal(tb):
         corr = p.ac_correlation(Z, n, beta, mu, precision=1)
     area = L * L * abs(lattice.A1[0] * lattice.A2[1] - lattice.A1[1] * lattice.A2[0])
     tau = Z / s
-    om = np.array([0.8, 1.0, 1.2])
-    sig = tb.ac_conductivity(corr[0, 0, 0], tau, beta, 0.0, om, smp.n_orb / area)
-    assert np.all(np.abs(sig / (1.0 / 8.0) - 1.0) < 0.1), sig
+    om = np.array([0.5, 0.8, 1.0, 1.2])
+    sig = tb.ac_conductivity(corr[0, 0], tau, beta, 0.1, om, smp.n_orb / area)
+    for ab in (0, 3):                                    # xx, yy
+        assert np.all(np.abs(sig[ab] / (1.0 / 8.0) - 1.0) < 0.1), (ab, sig[ab])
+    # isotropic: the Hall parts vanish against the longitudinal ones
+    assert np.max(np.abs(sig[1:3])) < 0.2 * np.min(np.abs(sig[0]))
