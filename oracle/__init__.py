@@ -14,7 +14,9 @@ functions, invariants) live in ``tests/``.
 Parity pinned: Bessel table, H x, propagation, correlation and DOS (see the
 tests named ``test_oracle_*``).  The AC-conductivity path (Fermi-Dirac
 operator, current operator, two-state correlation, conductivity integral)
-is in ``oracle/ac.py``, pinned by ``tests/test_oracle_ac.py``.
+is in ``oracle/ac.py``, pinned by ``tests/test_oracle_ac.py``; the
+quasi-eigenstates (Sec. 2.6) in ``oracle/quasi.py``, pinned by
+``tests/test_oracle_quasi.py``.
 """
 from __future__ import annotations
 
