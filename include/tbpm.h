@@ -81,6 +81,9 @@ extern "C" {
 #define TBPM_PROP_PERSISTENT 8 /* one cooperative launch per time step: the
                                   wavefront-fused step (TBPM_VARIANT_FUSED) for
                                   this call, with bounded dependency waits */
+#define TBPM_PROP_BACKWARD 16  /* negative times: each step applies e^{+iH tau}
+                                  (the same series with H -> -H); C_n is then
+                                  <psi0|psi(-n tau)> */
 
 typedef struct tbpm_ctx tbpm_ctx;
 
@@ -362,6 +365,28 @@ int tbpm_fermi_coefficients(double beta_s, double mu_s, int k_max, double *c_out
  * NORM_DRIFT, NONFINITE. */
 int tbpm_ac_correlation(tbpm_ctx *ctx, double z, int n_steps, double beta, double mu,
                         int precision, double *corr_out, int where_out, int flags);
+
+/* ---- quasi-eigenstates (Sec. 2.6) ---------------------------------------- */
+
+/* q1. Quasi-eigenstates (Sec. 2.6, Eq. quasi): for each energy E_k and each
+ * initial state psi (the states set on ctx),
+ *   Psi(E) = (tau / 2 pi) sum_{n=-N}^{N} w_n e^{i E n tau} psi(n tau),
+ *   w_n = (1 + cos(pi n / N)) / 2,
+ * from one forward and one backward run (TBPM_PROP_BACKWARD) of N = n_steps
+ * steps, accumulated on the GPU after every step in FP64; then normalised to
+ * unit norm per energy, state and sample.
+ *   z, n_steps, precision   as tbpm_propagate (n_steps >= 1)
+ *   n_energies, energies    1 .. 16 energies in eV (host)
+ *   out        complex128 [n_energies][n_states][n_orb], caller order
+ *   norms_out  [n_energies][n_states][n_samples] squared norms of Psi before
+ *              the normalisation (host), or NULL
+ *   where_out  TBPM_HOST or TBPM_DEVICE for out
+ *   flags      TBPM_PROP_PROFILE, TBPM_PROP_GRAPH, TBPM_PROP_PERSISTENT
+ * Afterwards the context holds the backward run (C_n = <psi0|psi(-n tau)>).
+ * Errors: STATE, INVALID_ARG, OOM, CUDA, NORM_DRIFT, NONFINITE, UNSUPPORTED. */
+int tbpm_quasi_eigenstates(tbpm_ctx *ctx, double z, int n_steps, int n_energies,
+                           const double *energies, int precision, double *out,
+                           double *norms_out, int where_out, int flags);
 
 /* c4. Real part of the AC conductivity from correlation rows (Sec. 2.7, Eq.
  * AC): for each row C and each omega,

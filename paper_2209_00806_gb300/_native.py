@@ -45,6 +45,7 @@ TBPM_PROP_PROFILE = 1
 TBPM_PROP_GRAPH = 2
 TBPM_PROP_RESUME = 4
 TBPM_PROP_PERSISTENT = 8
+TBPM_PROP_BACKWARD = 16
 TBPM_VARIANT_ZIGZAG = 1
 TBPM_VARIANT_STREAM_HINTS = 2
 TBPM_VARIANT_TMA = 4
@@ -109,6 +110,7 @@ SIGNATURES = [
     ("tbpm_fermi_coefficients", _I32, [_F64, _F64, _I32, P, ctypes.POINTER(_I32)]),
     ("tbpm_ac_correlation", _I32, [P, _F64, _I32, _F64, _F64, _I32, P, _I32, _I32]),
     ("tbpm_ac_conductivity", _I32, [P, _I32, _I32, _F64, _F64, _F64, P, _I32, _F64, P]),
+    ("tbpm_quasi_eigenstates", _I32, [P, _F64, _I32, _I32, P, _I32, P, P, _I32, _I32]),
 ]
 
 
@@ -287,6 +289,15 @@ def tbpm_ac_conductivity(corr, n_rows, n_steps, tau, beta, eta, omegas, n_omega,
                          sigma_out):
     return check(None, lib.tbpm_ac_conductivity(ptr(corr), n_rows, n_steps, tau, beta, eta,
                                                 ptr(omegas), n_omega, norm, ptr(sigma_out)))
+
+
+def tbpm_quasi_eigenstates(ctx, z, n_steps, energies, precision, out, norms_out=None,
+                           where_out=None, flags=0):
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    if where_out is None:
+        where_out = where_of(out)
+    return check(ctx, lib.tbpm_quasi_eigenstates(ctx, z, n_steps, e.shape[0], ptr(e), precision,
+                                                 ptr(out), ptr(norms_out), where_out, flags))
 
 
 def tbpm_set_launch_config(ctx, precision, max_group, threads, variant=1):

@@ -90,6 +90,11 @@ struct tbpm_ctx {
     bool ac_on = false;
     double2 *d_ac_corr = nullptr;          // [n_samples][n_states / 4][4][n_steps + 1]
     double *d_ac_partial = nullptr;        // [n_rows / kAcRows][4][8]
+    // quasi-eigenstates
+    bool qe_on = false;
+    int qe_K = 0;
+    double2 *d_qe_acc = nullptr;           // [K][n_rows][n_states]
+    const double2 *d_qe_coef = nullptr;    // [n_steps + 1][K] of the current run
     bool have_run = false;
     std::vector<cudaEvent_t> events;
     tbpm_stats stats;
@@ -849,6 +854,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
     const bool graph = (flags & TBPM_PROP_GRAPH) != 0 && !profile;
     const bool fused = !c->H.cplx && ((c->variant[precision] & kVariantFused) != 0 ||
                                       (flags & TBPM_PROP_PERSISTENT) != 0);
+    const double tsign = (flags & TBPM_PROP_BACKWARD) ? -1.0 : 1.0;   // e^{+iH tau} per step
     if (c->H.cplx && (flags & TBPM_PROP_PERSISTENT))
         return fail(c, TBPM_E_UNSUPPORTED, "the fused step takes real hoppings only");
 
@@ -970,6 +976,21 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         // AC-conductivity observer on the state buffer `bi` (after the reduction
         // of the same step, whose counter it reads)
         auto observe = [&](int bi) -> int {
+            if (c->qe_on) {
+                QeArgs qa;
+                qa.psi = g.buf[bi];
+                qa.scale = fp32 ? g.scale : nullptr;
+                qa.chunk_sample = c->H.chunk_sample;
+                qa.step = c->d_step;
+                qa.coef = c->d_qe_coef;
+                qa.acc = c->d_qe_acc;
+                qa.n_rows = c->H.n_rows;
+                qa.B = g.B;
+                qa.s0 = g.s0;
+                qa.S = c->n_states;
+                qa.K = c->qe_K;
+                CUDA_OR_FAIL(c, launch_qe_acc(qa, fp32, c->st));
+            }
             if (!c->ac_on) return TBPM_OK;
             AcArgs oa;
             oa.H = Hv;
@@ -1020,7 +1041,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                     ft.out = sch[k].out;
                     ft.final_term = sch[k].final_term ? 1 : 0;
                     split_coeff(sch[k].c, fp32, &ft.c_hi, &ft.c_lo);
-                    ft.gamma = sch[k].gamma;
+                    ft.gamma = tsign * sch[k].gamma;
                     ft.c_hi_f = (float)ft.c_hi;
                     ft.c_lo_f = (float)ft.c_lo;
                     ft.gamma_f = (float)ft.gamma;
@@ -1066,6 +1087,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             rc = observe(g.cur);
             if (rc) return rc;
             if (c->ac_on) launches += 2;
+            if (c->qe_on) launches += 1;
         }
         ra.scale = g.scale;
         ra.scale_f = g.scale_f;
@@ -1126,7 +1148,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 t.z = L.z < 0 ? nullptr : g.buf[L.z];
                 t.out = g.buf[L.out];
                 split_coeff(L.c, fp32, &t.c_hi, &t.c_lo);
-                t.gamma = L.gamma;
+                t.gamma = tsign * L.gamma;
                 t.c_hi_f = (float)t.c_hi;
                 t.c_lo_f = (float)t.c_lo;
                 t.gamma_f = (float)t.gamma;
@@ -1182,6 +1204,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             g.cur = nxt;
             launches += fused ? 2 : M;   // term kernels (or the fused step) + one reduction
             if (c->ac_on) launches += 2; // observer + its reduction
+            if (c->qe_on) launches += 1; // quasi-eigenstate accumulation
         }
     }
     if (profile) CUDA_OR_FAIL(c, cudaEventRecord(ev_all1, c->st));
@@ -1793,6 +1816,103 @@ extern "C" int tbpm_ac_correlation(tbpm_ctx *c, double z, int n_steps, double be
     c->d_ac_partial = nullptr;
     release();                   // the derived states D included
     if (rc) return fail(c, rc, err);
+    c->err.clear();
+    return leave(c);
+}
+
+// Quasi-eigenstates (Sec. 2.6): forward and backward runs with the
+// accumulation hook, then the caller's layout and the normalisation.
+extern "C" int tbpm_quasi_eigenstates(tbpm_ctx *c, double z, int n_steps, int n_energies,
+                                      const double *energies, int precision, double *out,
+                                      double *norms_out, int where_out, int flags)
+{
+    if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
+    if (!c->have_h || c->n_states < 1)
+        return fail(c, TBPM_E_STATE, "build the Hamiltonian and set states first");
+    if (n_steps < 1 || n_energies < 1 || n_energies > 16 || !energies || !out ||
+        (where_out != TBPM_HOST && where_out != TBPM_DEVICE))
+        return fail(c, TBPM_E_INVALID_ARG, "bad quasi-eigenstate arguments");
+    if (flags & (TBPM_PROP_RESUME | TBPM_PROP_BACKWARD))
+        return fail(c, TBPM_E_INVALID_ARG, "the quasi-eigenstates run both directions from t = 0");
+    for (int k = 0; k < n_energies; ++k)
+        if (!std::isfinite(energies[k])) return fail(c, TBPM_E_INVALID_ARG, "non-finite energy");
+    if (!(z > 0.0)) return fail(c, TBPM_E_INVALID_ARG, "z must be > 0");
+    const int K = n_energies, S = c->n_states;
+    const int64_t n_rows = c->H.n_rows, n_orb = c->n_orb;
+    const double tau = z / c->s;
+    // coefficient tables, forward then backward (the n = 0 term once)
+    std::vector<double2> tab(2 * (size_t)(n_steps + 1) * K);
+    for (int dir = 0; dir < 2; ++dir)
+        for (int n = 0; n <= n_steps; ++n) {
+            const double w = 0.5 * (1.0 + cos(M_PI * (double)n / (double)n_steps));
+            const double t = (dir ? -1.0 : 1.0) * n * tau;
+            for (int k = 0; k < K; ++k) {
+                const double f = (dir && n == 0) ? 0.0 : tau / (2.0 * M_PI) * w;
+                tab[((size_t)dir * (n_steps + 1) + n) * K + k] =
+                    make_double2(f * cos(energies[k] * t), f * sin(energies[k] * t));
+            }
+        }
+    int rc = enter(c);
+    if (rc) return rc;
+    double2 *d_tab = nullptr, *d_out = nullptr;
+    double *d_norms = nullptr;
+    int64_t *d_off = nullptr;
+    auto release = [&]() {
+        cudaFree(c->d_qe_acc);
+        c->d_qe_acc = nullptr;
+        c->d_qe_coef = nullptr;
+        c->qe_on = false;
+        cudaFree(d_tab);
+        cudaFree(d_norms);
+        cudaFree(d_off);
+        if (where_out == TBPM_HOST) cudaFree(d_out);
+    };
+    rc = dalloc(c, &c->d_qe_acc, (size_t)K * n_rows * S);
+    if (!rc) rc = dalloc(c, &d_tab, tab.size());
+    if (!rc) rc = dalloc(c, &d_norms, (size_t)K * S * c->n_samples);
+    if (!rc) rc = dalloc(c, &d_off, (size_t)c->n_samples + 1);
+    if (!rc && where_out == TBPM_HOST) rc = dalloc(c, &d_out, (size_t)K * S * n_orb);
+    if (rc) { release(); return rc; }
+    if (where_out == TBPM_DEVICE) d_out = reinterpret_cast<double2 *>(out);
+    cudaError_t e = cudaMemsetAsync(c->d_qe_acc, 0, (size_t)K * n_rows * S * sizeof(double2), c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                            c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_off, c->sample_off.data(), (c->n_samples + 1) * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);      // host tables go out of scope
+    if (e != cudaSuccess) {
+        release();
+        return fail(c, TBPM_E_CUDA, std::string("quasi-eigenstates: ") + cudaGetErrorString(e));
+    }
+    c->qe_on = true;
+    c->qe_K = K;
+    const int pf = flags & (TBPM_PROP_PROFILE | TBPM_PROP_GRAPH | TBPM_PROP_PERSISTENT);
+    c->d_qe_coef = d_tab;
+    rc = tbpm_propagate(c, z, n_steps, precision, nullptr, TBPM_HOST, pf);
+    if (!rc) {
+        c->d_qe_coef = d_tab + (size_t)(n_steps + 1) * K;
+        rc = tbpm_propagate(c, z, n_steps, precision, nullptr, TBPM_HOST, pf | TBPM_PROP_BACKWARD);
+    }
+    c->qe_on = false;
+    if (rc) {
+        std::string m = c->err;
+        release();
+        return fail(c, rc, m);
+    }
+    e = launch_qe_finish(c->d_qe_acc, K, S, n_rows, n_orb, c->n_samples, c->H.user_to_row,
+                         c->H.orb_sample, d_off, d_out, d_norms, c->st);
+    if (e == cudaSuccess && where_out == TBPM_HOST)
+        e = cudaMemcpyAsync(out, d_out, (size_t)K * S * n_orb * sizeof(double2),
+                            cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && norms_out)
+        e = cudaMemcpyAsync(norms_out, d_norms, (size_t)K * S * c->n_samples * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    release();
+    if (e != cudaSuccess)
+        return fail(c, TBPM_E_CUDA, std::string("quasi-eigenstates: ") + cudaGetErrorString(e));
     c->err.clear();
     return leave(c);
 }

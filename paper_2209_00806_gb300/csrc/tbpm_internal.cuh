@@ -119,6 +119,21 @@ struct AcReduceArgs {
     double s;
     double2 *corr_ac;                // [n_samples][n_states / 4][4][n_steps + 1]
 };
+// Quasi-eigenstate accumulation (Sec. 2.6): acc[k][r][s0 + l] += coef[n][k] psi[r][l].
+struct QeArgs {
+    const void *psi;                 // current buffer of the group, [row][B]
+    const double *scale;             // FP32 norm carry [n_samples][B] or nullptr
+    const int32_t *chunk_sample;
+    const int *step;                 // per sample, already advanced by k_reduce
+    const double2 *coef;             // [n_steps + 1][K] (tau / 2 pi) w_n e^{i E_k t_n}
+    double2 *acc;                    // [K][n_rows][S]
+    int64_t n_rows;
+    int B, s0, S, K;
+};
+cudaError_t launch_qe_acc(const QeArgs &a, int fp32, cudaStream_t st);
+cudaError_t launch_qe_finish(const double2 *acc, int K, int S, int64_t n_rows, int64_t n_orb,
+                             int n_samples, const int32_t *user_to_row, const int32_t *orb_sample,
+                             const int64_t *orb_off, double2 *out, double *norms, cudaStream_t st);
 cudaError_t launch_ac_observe(const AcArgs &a, int fp32, int cplx, cudaStream_t st);
 cudaError_t launch_ac_reduce(const AcReduceArgs &a, cudaStream_t st);
 // Preparation of the AC states, FP64, four lanes per row ([n_rows][4] complex):

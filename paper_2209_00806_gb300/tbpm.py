@@ -103,6 +103,17 @@ class Propagator:
                               precision, out, None, flags)
         return out
 
+    # q1 (Sec. 2.6)
+    def quasi_eigenstates(self, z, n_steps, energies, precision=N.TBPM_FP64, flags=0):
+        """(states [K, n_states, n_orb] complex128 of unit norm per sample,
+        squared norms before normalisation [K, n_states, n_samples])."""
+        e = np.atleast_1d(np.asarray(energies, dtype=np.float64))
+        out = np.empty((e.shape[0], self.n_states, self.n_orb), dtype=np.complex128)
+        norms = np.empty((e.shape[0], self.n_states, self.n_samples))
+        N.tbpm_quasi_eigenstates(self.ctx, float(z), int(n_steps), e, precision, out, norms,
+                                 None, flags)
+        return out, norms
+
     def correlation(self):
         out = np.empty((self.n_samples, self.stats()["n_steps"] + 1), dtype=np.complex128)
         N.tbpm_correlation(self.ctx, out)
