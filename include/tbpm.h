@@ -54,7 +54,9 @@ extern "C" {
 #define TBPM_DEVICE 1
 
 /* ---- window of the DOS transform (Sec. 2.4) ----------------------------- */
-#define TBPM_WINDOW_HANN 0
+#define TBPM_WINDOW_HANN 0         /* w_n = (1 + cos(pi n / N)) / 2 */
+#define TBPM_WINDOW_GAUSSIAN 1     /* w_n = exp(-(3 n / N)^2 / 2)  (sigma = N / 3) */
+#define TBPM_WINDOW_EXPONENTIAL 2  /* w_n = exp(-4 n / N) */
 
 /* ---- flags of tbpm_build_hamiltonian ------------------------------------ */
 #define TBPM_BUILD_STRICT_BOUND 1 /* fail with TBPM_E_SPECTRAL_BOUND if the
@@ -214,10 +216,13 @@ int tbpm_get_norms(tbpm_ctx *ctx, double *norms_out);
 
 /* a7. DOS from one averaged correlation C_0 .. C_{n_steps} (host memory),
  * Sec. 2.4, Eq. dos_tbpm:
- *   D(E) = (tau/pi) [Re C_0 / 2 + sum_{n=1}^{N-1} w_n Re(exp(i E n tau) C_n)]
- * (C(-t) = conj C(t), trapezoid rule, one-sided Hann w_n = (1+cos(pi n/N))/2),
+ *   D(E) = (tau/pi) [Re C_0 / 2 + sum_{n=1}^{N} v_n w_n Re(exp(i E n tau) C_n)]
+ * (C(-t) = conj C(t), trapezoid rule: v_n = 1, v_N = 1/2; window w_n one of
+ * TBPM_WINDOW_HANN (w_N = 0), _GAUSSIAN, _EXPONENTIAL -- Sec. 2.4 names the
+ * three without parameters; the widths above are this library's choice),
  * at bin centres E_k = e_min + (k + 1/2)(e_max - e_min)/n_e.  Pure host
- * function, FP64.  D integrates to Re C_0 over a full period 2 pi / tau. */
+ * function, FP64.  D integrates to Re C_0 over a full period 2 pi / tau.
+ * Errors: INVALID_ARG, UNSUPPORTED (unknown window). */
 int tbpm_dos(const double *corr, int n_steps, double tau, int window, double e_min,
              double e_max, int n_e, double *energies_out, double *dos_out);
 

@@ -34,6 +34,8 @@ TBPM_FP32 = 1
 TBPM_HOST = 0
 TBPM_DEVICE = 1
 TBPM_WINDOW_HANN = 0
+TBPM_WINDOW_GAUSSIAN = 1
+TBPM_WINDOW_EXPONENTIAL = 2
 TBPM_BUILD_STRICT_BOUND = 1
 TBPM_BUILD_NO_FP64 = 2
 TBPM_BUILD_NO_FP32 = 4

@@ -150,8 +150,24 @@ int ac_conductivity(const double *corr, int n_rows, int n_steps, double tau, dou
     return TBPM_OK;
 }
 
+// Window w_n of the DOS transform (Sec. 2.4 names Hann, Gaussian and
+// exponential windows without parameters): Hann (1 + cos(pi n/N))/2,
+// Gaussian exp(-(3n/N)^2 / 2) (sigma = N/3), exponential exp(-4n/N).  The
+// last sample enters with the trapezoid end weight 1/2.
+double window_weight(int window, int n, int n_steps)
+{
+    const double x = (double)n / (double)n_steps;
+    double w;
+    switch (window) {
+    case TBPM_WINDOW_GAUSSIAN: w = exp(-4.5 * x * x); break;
+    case TBPM_WINDOW_EXPONENTIAL: w = exp(-4.0 * x); break;
+    default: w = 0.5 * (1.0 + cos(M_PI * x)); break;
+    }
+    return n == n_steps ? 0.5 * w : w;
+}
+
 int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_min,
-                double e_max, double *gbar_out)
+                double e_max, int window, double *gbar_out)
 {
     typedef std::complex<double> cd;
     const double de = (e_max - e_min) / n_e;
@@ -162,7 +178,7 @@ int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_
         const double E = e_min + (k + 0.5) * de;
         const cd step(cos(E * tau), -sin(E * tau));
         cd ph(1.0, 0.0);
-        for (int n = 1; n < n_steps; ++n) {
+        for (int n = 1; n <= n_steps; ++n) {
             if (n % 64 == 0) ph = cd(cos(E * tau * n), -sin(E * tau * n));
             else ph *= step;
             acc[n] += dl_dd[k] * ph;
@@ -170,13 +186,11 @@ int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_
     }
     gbar_out[0] = tau / (2.0 * M_PI) * s0;
     gbar_out[1] = 0.0;
-    for (int n = 1; n < n_steps; ++n) {
-        const double w = 0.5 * (1.0 + cos(M_PI * (double)n / (double)n_steps));
+    for (int n = 1; n <= n_steps; ++n) {
+        const double w = window_weight(window, n, n_steps);
         gbar_out[2 * n] = tau / M_PI * w * acc[n].real();
         gbar_out[2 * n + 1] = tau / M_PI * w * acc[n].imag();
     }
-    gbar_out[2 * n_steps] = 0.0;
-    gbar_out[2 * n_steps + 1] = 0.0;
     return TBPM_OK;
 }
 
@@ -191,7 +205,7 @@ extern "C" int tbpm_bessel_coefficients(double z, double tol, int max_terms, dou
 }
 
 // DOS by Horner evaluation of the windowed sum at each energy:
-//   S(E) = sum_{n=1}^{N-1} w_n C_n u^n,  u = exp(i E tau),
+//   S(E) = sum_{n=1}^{N} w_n C_n u^n,  u = exp(i E tau)  (w_N with the end weight 1/2),
 //   D(E) = (tau / pi) (Re C_0 / 2 + Re S(E)).
 extern "C" int tbpm_dos(const double *corr, int n_steps, double tau, int window,
                         double e_min, double e_max, int n_e, double *energies_out,
@@ -200,13 +214,13 @@ extern "C" int tbpm_dos(const double *corr, int n_steps, double tau, int window,
     if (!corr || n_steps < 1 || !(tau > 0.0) || !(e_max > e_min) || n_e < 1 ||
         !energies_out || !dos_out)
         return TBPM_E_INVALID_ARG;
-    if (window != TBPM_WINDOW_HANN) return TBPM_E_UNSUPPORTED;
+    if (window != TBPM_WINDOW_HANN && window != TBPM_WINDOW_GAUSSIAN &&
+        window != TBPM_WINDOW_EXPONENTIAL)
+        return TBPM_E_UNSUPPORTED;
     typedef std::complex<double> cd;
-    std::vector<cd> wc(n_steps);
-    for (int n = 1; n < n_steps; ++n) {
-        double w = 0.5 * (1.0 + cos(M_PI * (double)n / (double)n_steps));
-        wc[n] = w * cd(corr[2 * n], corr[2 * n + 1]);
-    }
+    std::vector<cd> wc(n_steps + 1);
+    for (int n = 1; n <= n_steps; ++n)
+        wc[n] = tbpm::window_weight(window, n, n_steps) * cd(corr[2 * n], corr[2 * n + 1]);
     const double de = (e_max - e_min) / n_e;
     const double c0 = 0.5 * corr[0];
 #pragma omp parallel for schedule(static)
@@ -214,7 +228,7 @@ extern "C" int tbpm_dos(const double *corr, int n_steps, double tau, int window,
         double E = e_min + (k + 0.5) * de;
         cd u(cos(E * tau), sin(E * tau));
         cd s(0.0, 0.0);
-        for (int n = n_steps - 1; n >= 1; --n) s = (s + wc[n]) * u;
+        for (int n = n_steps; n >= 1; --n) s = (s + wc[n]) * u;
         energies_out[k] = E;
         dos_out[k] = tau / M_PI * (c0 + s.real());
     }
@@ -226,8 +240,10 @@ extern "C" int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, doubl
 {
     if (!dl_dd || n_e < 1 || n_steps < 1 || !(tau > 0.0) || !(e_max > e_min) || !gbar_out)
         return TBPM_E_INVALID_ARG;
-    if (window != TBPM_WINDOW_HANN) return TBPM_E_UNSUPPORTED;
-    return tbpm::dos_adjoint(dl_dd, n_e, n_steps, tau, e_min, e_max, gbar_out);
+    if (window != TBPM_WINDOW_HANN && window != TBPM_WINDOW_GAUSSIAN &&
+        window != TBPM_WINDOW_EXPONENTIAL)
+        return TBPM_E_UNSUPPORTED;
+    return tbpm::dos_adjoint(dl_dd, n_e, n_steps, tau, e_min, e_max, window, gbar_out);
 }
 
 extern "C" int tbpm_fermi_coefficients(double beta_s, double mu_s, int k_max, double *c_out,

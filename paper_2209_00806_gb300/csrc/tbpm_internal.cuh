@@ -285,7 +285,8 @@ int bessel_miller(double z, double tol, int max_terms, double *J, int *n_terms);
 int fermi_coefficients(double beta_s, double mu_s, double tol, int k_max, std::vector<double> &c);
 int ac_conductivity(const double *corr, int n_rows, int n_steps, double tau, double beta,
                     double eta, const double *omegas, int n_omega, double norm, double *sigma);
+double window_weight(int window, int n, int n_steps);
 int dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, double e_min,
-                double e_max, double *gbar_out);
+                double e_max, int window, double *gbar_out);
 
 }  // namespace tbpm

@@ -134,3 +134,36 @@ def test_ac_conductivity_transform_vs_oracle(native):
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
     with pytest.raises(native.TbpmError):
         ac_conductivity(corr, tau, 12.0, 0.01, np.array([0.0]), 1.0)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_dos_windows_vs_oracle(native, kind):
+    from oracle import windows
+    from paper_2209_00806_gb300 import dos
+    gen = np.random.default_rng(11)
+    c = gen.normal(size=257) + 1j * gen.normal(size=257)
+    en, d = dos(c, 0.21, -6.0, 6.0, 401, window=kind)
+    en2, d2 = windows.dos(c, 0.21, -6.0, 6.0, 401, kind)
+    assert np.max(np.abs(en - en2)) < 1e-14
+    assert np.max(np.abs(d - d2)) < 1e-12
+    with pytest.raises(native.TbpmError):
+        dos(c, 0.21, -6.0, 6.0, 401, window=7)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_dos_adjoint_windows_is_the_transpose(native, kind):
+    """dL/dC of L = dl . D(C): the DOS map is linear in (Re C, Im C), so the
+    adjoint is its transpose, built here column by column from the oracle."""
+    from oracle import windows
+    from paper_2209_00806_gb300 import dos_adjoint
+    n, n_e, tau = 40, 97, 0.3
+    dl = np.random.default_rng(12).normal(size=n_e)
+    ref = np.empty(n + 1, dtype=np.complex128)
+    for m in range(n + 1):
+        e = np.zeros(n + 1, dtype=np.complex128)
+        e[m] = 1.0
+        _, d_re = windows.dos(e, tau, -4.0, 4.0, n_e, kind)
+        _, d_im = windows.dos(1j * e, tau, -4.0, 4.0, n_e, kind)
+        ref[m] = dl @ d_re + 1j * (dl @ d_im)
+    g = dos_adjoint(dl, n, tau, -4.0, 4.0, window=kind)
+    assert np.max(np.abs(g - ref)) < 1e-12
