@@ -40,12 +40,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="disordered",
-                    choices=["disordered", "batched", "graphene_dos", "differentiable", "tbg"],
+                    choices=["disordered", "batched", "graphene_dos", "differentiable", "tbg",
+                             "optical", "quasi"],
                     help="disordered: 2048^2 disordered graphene, 4 states, 1024 steps "
                          "(default, the headline); batched: 32 uneven samples x 16 states, "
                          "512 steps; graphene_dos: 64x64 pristine graphene, 1 state, 1024 steps; "
                          "differentiable: 512^2 graphene, DOS loss, FP64 forward + adjoint; "
-                         "tbg: twisted bilayer flake (--side nm), 6 A cutoff, 8 states")
+                         "tbg: twisted bilayer flake (--side nm), 6 A cutoff, 8 states; "
+                         "optical: AC-conductivity correlation of 1024^2 graphene at 300 K; "
+                         "quasi: quasi-eigenstates at 4 energies of 1024^2 disordered graphene")
     ap.add_argument("--side", type=float, default=200.0, help="tbg flake side in nm")
     ap.add_argument("--order", default="auto", choices=["auto", "natural", "rcm", "cluster"],
                     help="row order of the build (auto: cluster for tbg, natural otherwise)")
@@ -546,12 +549,110 @@ def run_differentiable(args):
     return 0
 
 
+def run_observables(args):
+    """One step = the whole optical-conductivity correlation (Fermi-operator
+    preparation in FP64, FP32 propagation of psi, psi_2, psi_1x, psi_1y, the
+    per-step current observer) or the whole quasi-eigenstate computation
+    (forward and backward FP32 runs with the per-step accumulation).  Inputs
+    resident in HBM; the matrix build is inside the step."""
+    import torch
+
+    import paper_2209_00806_gb300 as tb
+    from paper_2209_00806_gb300 import _native as N
+    from tbpm_inputs import lattice, workloads
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    optical = args.workload == "optical"
+    w = workloads.optical_graphene() if optical else workloads.quasi_graphene()
+    smp = w.sample
+    S, NT = w.n_states, w.n_steps
+    theta = torch.as_tensor(w.thetas()[0], device=dev)
+    d = {k: (None if getattr(smp, k) is None else torch.as_tensor(getattr(smp, k), device=dev))
+         for k in ("hop_i", "hop_j", "hop_v", "onsite")}
+    p = tb.Propagator(local, stream.cuda_stream)
+    M = len(tb.tbpm_bessel_coefficients(w.z))
+    beta = 1.0 / (8.617333262e-5 * 300.0)
+    if optical:
+        dr = lattice.bond_vectors(smp)
+        dx = torch.as_tensor(np.ascontiguousarray(dr[:, 0]), device=dev)
+        dy = torch.as_tensor(np.ascontiguousarray(dr[:, 1]), device=dev)
+        K_f = len(tb.fermi_coefficients(beta * w.s, 0.0))
+        out = torch.empty((1, S, 4, NT + 1), dtype=torch.complex128, device=dev)
+        # orbital-Chebyshev products: 4 lanes x (Fermi terms on 4 lanes + steps x (M - 1))
+        units = smp.n_orb * S * 4 * (K_f + NT * (M - 1))
+    else:
+        E = np.array(w.info["energies"])
+        out = torch.empty((E.shape[0], S, smp.n_orb), dtype=torch.complex128, device=dev)
+        norms = np.empty((E.shape[0], S, 1))
+        units = smp.n_orb * S * 2 * NT * (M - 1)
+
+    def one_step():
+        p.build(smp.n_orb, d["onsite"], d["hop_i"], d["hop_j"], d["hop_v"], w.s)
+        p.set_phase_states(theta)
+        if optical:
+            N.tbpm_set_bond_vectors(p.ctx, dx, dy)
+            N.tbpm_ac_correlation(p.ctx, w.z, NT, beta, 0.0, N.TBPM_FP32, out, None,
+                                  N.TBPM_PROP_PROFILE)
+        else:
+            N.tbpm_quasi_eigenstates(p.ctx, w.z, NT, E, N.TBPM_FP32, out, norms, None,
+                                     N.TBPM_PROP_PROFILE)
+
+    p.build(smp.n_orb, d["onsite"], d["hop_i"], d["hop_j"], d["hop_v"], w.s)
+    p.set_phase_states(theta)
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st = p.stats()
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    roof = None
+    if st["ms_term_avg"]:
+        ach = st["bytes_term"] / (st["ms_term_avg"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+                "kernel": "interior Clenshaw term (last run of the step)",
+                "algorithmic_bytes_per_launch": st["bytes_term"],
+                "ms_per_launch": st["ms_term_avg"]}
+    cfg = {"workload": f"{w.name}_{w.info['L']}x{w.info['L']}", "n_orb": int(smp.n_orb),
+           "n_bonds": int(smp.n_hop), "states": S, "time_steps": NT, "z": "pi/2", "s_eV": w.s,
+           "l2": "inputs larger than L2"}
+    if optical:
+        cfg.update(T_kelvin=300.0, mu_eV=0.0, fermi_terms=K_f, lanes="psi, f psi, (1-f) J_x psi, "
+                   "(1-f) J_y psi", correlations="xx, xy, yx, yy")
+    else:
+        cfg.update(energies_eV=w.info["energies"], runs="forward and backward, Hann window")
+    line = {"metric": "orbital-Chebyshev-steps/s", "value": units * args.steps / (ms * 1e-3),
+            "unit": "orbital-Chebyshev-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "reductions": "f64",
+            "data": "synthetic", "config": cfg, "roofline": roof,
+            "ms_propagation_last_run": st["ms_total"],
+            "gpu_launches": int(st["kernel_launches"]), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    p.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "differentiable":
         return run_differentiable(args)
+    if args.workload in ("optical", "quasi"):
+        return run_observables(args)
     return run_gb300(args)
 
 

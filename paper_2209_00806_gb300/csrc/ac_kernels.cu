@@ -24,6 +24,14 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// h x for a stored value h: a full complex product for complex values, two
+// products for real ones (half the FP64 work of the preparation).
+template <bool CX> __device__ __forceinline__ double2 hmul(double2 h, double2 x)
+{
+    if (CX) return cmul(h, x);
+    return make_double2(h.x * x.x, h.x * x.y);
+}
+
 // One stored value as complex double.
 template <typename VT, bool CX> struct HVal;
 template <> struct HVal<double, false> {
@@ -99,7 +107,7 @@ __global__ void k_current4(SellView H, int64_t n_rows, const double *dxe, const 
     for (int k = 0; k < w; ++k) {
         const int64_t e = base + (int64_t)k * kSliceRows + lr;
         const int32_t c = __ldg(H.col + e);
-        const double2 hv = cmul(HVal<VT, CX>::get(H.val, e), v4[(int64_t)c * 4]);
+        const double2 hv = hmul<CX>(HVal<VT, CX>::get(H.val, e), v4[(int64_t)c * 4]);
         const double dx = __ldg(dxe + e), dy = __ldg(dye + e);
         gx.x = fma(dx, hv.x, gx.x);
         gx.y = fma(dx, hv.y, gx.y);
@@ -133,7 +141,7 @@ __global__ void k_cheb_real4(SellView H, int64_t n_rows, double c, double gamma,
         for (int k = 0; k < w; ++k) {
             const int64_t e = base + (int64_t)k * kSliceRows + lr;
             const int32_t cc = __ldg(H.col + e);
-            const double2 hv = cmul(HVal<VT, CX>::get(H.val, e), x[(int64_t)cc * 4 + l]);
+            const double2 hv = hmul<CX>(HVal<VT, CX>::get(H.val, e), x[(int64_t)cc * 4 + l]);
             y.x += hv.x;
             y.y += hv.y;
         }
@@ -216,8 +224,8 @@ __global__ void __launch_bounds__(kAcRows) k_ac_observe(AcArgs a)
     for (int k = 0; k < w; ++k) {
         const int64_t e = base + (int64_t)k * kSliceRows + lr;
         const int32_t c = __ldg(a.H.col + e);
-        const double2 hv = cmul(HVal<V, CX>::get(a.H.val, e),
-                                StateLd<V>::get(a.psi, (int64_t)c * B + l2));
+        const double2 hv = hmul<CX>(HVal<V, CX>::get(a.H.val, e),
+                                    StateLd<V>::get(a.psi, (int64_t)c * B + l2));
         const double dx = __ldg(a.dx + e), dy = __ldg(a.dy + e);
         gx.x = fma(dx, hv.x, gx.x);
         gx.y = fma(dx, hv.y, gx.y);

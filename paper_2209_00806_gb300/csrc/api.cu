@@ -53,7 +53,7 @@ struct tbpm_ctx {
     // propagation state
     int prec = -1;               // precision of the group buffers
     int max_group[2] = {8, 16};  // widest state group per precision
-    int threads[2] = {128, 128}; // threads per block per precision
+    int threads[2] = {64, 64};   // threads per block per precision (fastest on GB300)
     // term-kernel launch variants (FP64, FP32): the fastest on GB300 for
     // graphene-like lattices; tbpm_autotune re-checks for the actual matrix
     int variant[2] = {kVariantZigZag, kVariantZigZag | kVariantWide};
@@ -947,6 +947,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         base.n_rows = c->H.n_rows;
         base.uniform = c->H.uniform;
         base.cplx = c->H.cplx;
+        base.fixed_width = c->H.fixed_width;
         base.h_uniform = c->H.h_uniform;
         base.h_uniform_f = (float)c->H.h_uniform;
         base.psi0 = g.psi0;

@@ -208,8 +208,15 @@ __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int
     }
     const int64_t q = r / kSliceRows;
     const int lr = (int)(r % kSliceRows);
-    const int64_t base = __ldg(a.H.slice_ptr + q);
-    const int w = (int)((__ldg(a.H.slice_ptr + q + 1) - base) / kSliceRows);
+    int64_t base;
+    int w;
+    if (a.fixed_width) {        // no slice-pointer load: one dependent round trip less
+        w = a.fixed_width;
+        base = q * (kSliceRows * (int64_t)w);
+    } else {
+        base = __ldg(a.H.slice_ptr + q);
+        w = (int)((__ldg(a.H.slice_ptr + q + 1) - base) / kSliceRows);
+    }
     const int32_t *colp = a.H.col + base + lr;
     const V *valp = reinterpret_cast<const V *>(a.H.val) + base + lr;
 

@@ -61,6 +61,7 @@ struct TermArgs {
     int reverse;          // walk the blocks from the end (zig-zag order)
     int uniform;          // every off-diagonal value equals h_uniform (no value loads)
     int cplx;             // complex matrix values (re, im) per entry
+    int fixed_width;      // slices all this wide: base = 32 q w, no slice_ptr loads
     double h_uniform;
     float h_uniform_f;
     // closing term only (H.col == nullptr: reduce `out` without computing it)
@@ -264,6 +265,7 @@ struct BuildOutput {
     int64_t n_hop = 0;
     double gershgorin = 0.0;
     int max_width = 0;
+    int fixed_width = 0;             // every slice has this width (0: widths vary)
     int64_t bandwidth = 0;           // max |col - row| over the stored entries
     int uniform = 0;                 // all off-diagonal values are equal
     int cplx = 0;                    // values are complex (re, im) per entry

@@ -135,3 +135,26 @@ def twisted_bilayer_flake(side_nm: float = 100.0, n_states: int = 8, n_steps: in
     return Workload("twisted_bilayer", smp, np.array([0, smp.n_orb], dtype=np.int64), 12.0,
                     Z_STEP, n_states, n_steps, n_energies, (-12.0, 12.0), seed, [seed],
                     dict(side_nm=side_nm))
+
+
+def optical_graphene(L: int = 1024, n_steps: int = 1024, n_states: int = 1) -> Workload:
+    """Optical (AC) conductivity: pristine periodic graphene LxL with bond
+    vectors (the paper's Sec. 4 example at 1024^2 instead of 4096^2), s = 9 eV,
+    T = 300 K, mu = 0, one random state (four propagated lanes)."""
+    seed = master_seed(6)
+    smp = lattice.graphene(L, L, pbc=True, seed=seed, with_pos=True)
+    smp.pos = None                      # the bond vectors carry the geometry
+    return Workload("optical_graphene", smp, np.array([0, smp.n_orb], dtype=np.int64), 9.0,
+                    Z_STEP, n_states, n_steps, 0, (-9.0, 9.0), seed, [seed],
+                    dict(L=L, T_kelvin=300.0, mu=0.0))
+
+
+def quasi_graphene(L: int = 1024, n_steps: int = 512, n_states: int = 4) -> Workload:
+    """Quasi-eigenstates: disordered periodic graphene LxL (Anderson
+    U[-0.5, 0.5] eV, 1% vacancies), s = 9.5 eV, 4 states, energies
+    -2.7, -1, 0.4, 2 eV."""
+    seed = master_seed(7)
+    smp = lattice.graphene(L, L, pbc=True, seed=seed, onsite_w=1.0, vacancy_frac=0.01)
+    return Workload("quasi_graphene", smp, np.array([0, smp.n_orb], dtype=np.int64), 9.5,
+                    Z_STEP, n_states, n_steps, 0, (-9.5, 9.5), seed, [seed],
+                    dict(L=L, energies=[-2.7, -1.0, 0.4, 2.0]))
