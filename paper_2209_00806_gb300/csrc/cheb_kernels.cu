@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 3) : 1) 
 //
 // GB300 runs FP64 at 1/58 of the FP32 rate, so the reduction is shaped to
 // spend few FP64 operations: in the FP32 form the per-row products and the
-// sum over the rows of a warp are formed in FP32 (each warp partial covers
-// at most 32 rows; its rounding is far below that of the FP32 states
-// themselves) and everything from the warp partials up is FP64; in the FP64
+// sum over the rows of a block are formed in FP32 (each block partial covers
+// at most 128 rows; its rounding is far below that of the FP32 states
+// themselves) and everything from the block partials up is FP64; in the FP64
 // form every product and sum is FP64, but rows are summed in a shared-memory
 // tree (one add per value) instead of a butterfly (one add per value and
 // level on every lane).
@@ -356,7 +356,8 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
     constexpr int B = L * SPL;
     constexpr int ROWS = kFinalThreads / L;          // rows per block
     constexpr int NW = kFinalThreads / 32;
-    __shared__ double red[sizeof(V) == 8 ? ROWS * B * 3 : NW * B * 3];
+    __shared__ double red[sizeof(V) == 8 ? ROWS * B * 3 : 1];
+    __shared__ float redf[NW * B * 3];
     __shared__ double grp[8][B * 3];
     __shared__ int last;
     const int64_t bid = block_in_order(a);
@@ -392,21 +393,26 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
                 pnr[j] += __shfl_xor_sync(0xffffffffu, pnr[j], off);
             }
         }
+        // ... and over the block's warps in FP32 too; one FP32 -> FP64
+        // conversion per value and block.  GB300 issues an FP64 instruction,
+        // a conversion included, at a small fraction of the FP32 rate per warp
+        // instruction, whatever the number of active lanes, so the block keeps
+        // them to one warp instruction per value.
         const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
         if (lane < L) {
 #pragma unroll
             for (int j = 0; j < SPL; ++j) {
                 const int b = lane * SPL + j;
-                red[(warp * B + b) * 3 + 0] = (double)pre[j];
-                red[(warp * B + b) * 3 + 1] = (double)pim[j];
-                red[(warp * B + b) * 3 + 2] = (double)pnr[j];
+                redf[(warp * B + b) * 3 + 0] = pre[j];
+                redf[(warp * B + b) * 3 + 1] = pim[j];
+                redf[(warp * B + b) * 3 + 2] = pnr[j];
             }
         }
         __syncthreads();
         if (threadIdx.x < B * 3) {
-            double s = 0.0;
-            for (int w = 0; w < NW; ++w) s += red[w * B * 3 + threadIdx.x];
-            grp[0][threadIdx.x] = s;
+            float s = 0.f;
+            for (int w = 0; w < NW; ++w) s += redf[w * B * 3 + threadIdx.x];
+            grp[0][threadIdx.x] = (double)s;
         }
     } else {
         // FP64: shared-memory tree, 8 groups of rows then the groups
@@ -655,25 +661,25 @@ cudaError_t dispatch_cx(const TermArgs &a, int fp32, int B, int threads, bool co
             }
         }
     }
-    if (!FINAL && !CX && (a.variant & kVariantWide)) {
-        // one thread per row and 32-byte lanes: fewer lanes share the index loads
-        if (!fp32) {
-            switch (B) {
-            case 2: return launch_term_t<double, 1, 2, false>(a, threads, st);
-            case 4: return launch_term_t<double, 2, 2, false>(a, threads, st);
-            case 8: return launch_term_t<double, 4, 2, false>(a, threads, st);
-            }
-        } else {
-            switch (B) {
-            case 4: return launch_term_t<float, 1, 4, false>(a, threads, st);
-            case 8: return launch_term_t<float, 2, 4, false>(a, threads, st);
-            case 16: return launch_term_t<float, 4, 4, false>(a, threads, st);
-            }
-        }
-    }
 #define TBPM_CASE(V, L, SPL)                                                  \
     return FINAL ? launch_final_t<V, L, SPL, CX>(a, threads, compute, st)    \
                  : launch_term_t<V, L, SPL, CX>(a, threads, st)
+    if constexpr (!CX) if (a.variant & kVariantWide) {
+        // one thread per row and 32-byte lanes: fewer lanes share the index loads
+        if (!fp32) {
+            switch (B) {
+            case 2: TBPM_CASE(double, 1, 2);
+            case 4: TBPM_CASE(double, 2, 2);
+            case 8: TBPM_CASE(double, 4, 2);
+            }
+        } else {
+            switch (B) {
+            case 4: TBPM_CASE(float, 1, 4);
+            case 8: TBPM_CASE(float, 2, 4);
+            case 16: TBPM_CASE(float, 4, 4);
+            }
+        }
+    }
     if (!fp32) {
         switch (B) {
         case 1: TBPM_CASE(double, 1, 1);

@@ -212,16 +212,22 @@ def test_gpu_graph_mode_and_determinism(tb):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_gpu_tma_kernel_is_bit_identical(tb, prec):
-    """The TMA-staged term kernel does the same arithmetic in the same order."""
+    """The TMA-staged term kernel does the same arithmetic in the same order;
+    the wide-lane kernels the same arithmetic per row (bit-identical states)
+    with the closing sums grouped by other blocks (C within rounding)."""
     smp = lattice.graphene(33, 31, pbc=True, seed=6, onsite_w=1.0, vacancy_frac=0.02)
     th = rng.phases(12, 4, smp.n_orb)
     outs = []
     for variant in (0, 4, 5, 65):
         c, _, phi, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, cfg=(4, 256, variant),
                                flags=2 if variant == 5 else 0)
-        outs.append((c, phi))
-    for c, phi in outs[1:]:
-        assert np.array_equal(c, outs[0][0]) and np.array_equal(phi, outs[0][1])
+        outs.append((variant, c, phi))
+    for variant, c, phi in outs[1:]:
+        assert np.array_equal(phi, outs[0][2])
+        if variant == 65:
+            assert np.max(np.abs(c - outs[0][1])) < (1e-13 if prec == 0 else 1e-6)
+        else:
+            assert np.array_equal(c, outs[0][1])
 
 
 @pytest.mark.parametrize("prec", [0, 1])
