@@ -210,7 +210,46 @@ __global__ void k_bond_vectors(int64_t n_hop, const int32_t *bond_rows, const in
 
 // ---- observer ------------------------------------------------------------------
 
-template <typename V, bool CX>
+// Complex value in the observer's arithmetic type A (the group's precision).
+template <typename A> struct C2 { A x, y; };
+
+template <typename A, bool CX> __device__ __forceinline__ C2<A> obs_h(const void *v, int64_t e)
+{
+    C2<A> h;
+    if (CX) {
+        if (sizeof(A) == 4) {
+            const float2 f = __ldg(reinterpret_cast<const float2 *>(v) + e);
+            h.x = (A)f.x; h.y = (A)f.y;
+        } else {
+            const double2 d = __ldg(reinterpret_cast<const double2 *>(v) + e);
+            h.x = (A)d.x; h.y = (A)d.y;
+        }
+    } else {
+        h.x = __ldg(reinterpret_cast<const A *>(v) + e);
+        h.y = (A)0;
+    }
+    return h;
+}
+template <typename A> __device__ __forceinline__ C2<A> obs_state(const void *p, int64_t i)
+{
+    C2<A> c;
+    if (sizeof(A) == 4) {
+        const float2 f = __ldg(reinterpret_cast<const float2 *>(p) + i);
+        c.x = (A)f.x; c.y = (A)f.y;
+    } else {
+        const double2 d = __ldg(reinterpret_cast<const double2 *>(p) + i);
+        c.x = (A)d.x; c.y = (A)d.y;
+    }
+    return c;
+}
+
+// Arithmetic in the group's precision A: in the FP32 form the per-row sums,
+// the products and the block's sum over its 128 rows are FP32 (their
+// rounding is that of the FP32 states), with one conversion to FP64 per value
+// and block -- GB300 issues FP64 instructions, conversions included, at a
+// small fraction of the FP32 rate; the FP64 form is FP64 throughout.  Block
+// partials and everything above them are FP64.
+template <typename A, bool CX>
 __global__ void __launch_bounds__(kAcRows) k_ac_observe(AcArgs a)
 {
     const int64_t r = blockIdx.x * (int64_t)kAcRows + threadIdx.x;   // n_rows % 1024 == 0
@@ -220,43 +259,51 @@ __global__ void __launch_bounds__(kAcRows) k_ac_observe(AcArgs a)
     const int64_t q = r / kSliceRows, lr = r % kSliceRows;
     const int64_t base = a.H.slice_ptr[q];
     const int w = (int)((a.H.slice_ptr[q + 1] - base) / kSliceRows);
-    double2 gx = make_double2(0.0, 0.0), gy = make_double2(0.0, 0.0);
+    const A *dxp = reinterpret_cast<const A *>(sizeof(A) == 4 ? (const void *)a.dx32 : (const void *)a.dx);
+    const A *dyp = reinterpret_cast<const A *>(sizeof(A) == 4 ? (const void *)a.dy32 : (const void *)a.dy);
+    C2<A> gx = {(A)0, (A)0}, gy = {(A)0, (A)0};
     for (int k = 0; k < w; ++k) {
         const int64_t e = base + (int64_t)k * kSliceRows + lr;
         const int32_t c = __ldg(a.H.col + e);
-        const double2 hv = hmul<CX>(HVal<V, CX>::get(a.H.val, e),
-                                    StateLd<V>::get(a.psi, (int64_t)c * B + l2));
-        const double dx = __ldg(a.dx + e), dy = __ldg(a.dy + e);
+        const C2<A> h = obs_h<A, CX>(a.H.val, e);
+        const C2<A> x = obs_state<A>(a.psi, (int64_t)c * B + l2);
+        C2<A> hv;
+        hv.x = h.x * x.x;
+        hv.y = h.x * x.y;
+        if (CX) {
+            hv.x = fma(-h.y, x.y, hv.x);
+            hv.y = fma(h.y, x.x, hv.y);
+        }
+        const A dx = __ldg(dxp + e), dy = __ldg(dyp + e);
         gx.x = fma(dx, hv.x, gx.x);
         gx.y = fma(dx, hv.y, gx.y);
         gy.x = fma(dy, hv.x, gy.x);
         gy.y = fma(dy, hv.y, gy.y);
     }
-    double2 u1x = StateLd<V>::get(a.psi, r * B + l2 + 1);
-    double2 u1y = StateLd<V>::get(a.psi, r * B + l2 + 2);
+    C2<A> u1x = obs_state<A>(a.psi, r * B + l2 + 1);
+    C2<A> u1y = obs_state<A>(a.psi, r * B + l2 + 2);
     if (a.scale) {      // FP32 norm carry of the three lanes
         const int smp = a.chunk_sample[r / kChunkRows];
-        const double s2 = a.scale[(int64_t)smp * B + l2];
-        const double sx = a.scale[(int64_t)smp * B + l2 + 1];
-        const double sy = a.scale[(int64_t)smp * B + l2 + 2];
+        const float *sf = a.scale_f + (int64_t)smp * B;
+        const A s2 = (A)sf[l2], sx = (A)sf[l2 + 1], sy = (A)sf[l2 + 2];
         gx.x *= s2; gx.y *= s2; gy.x *= s2; gy.y *= s2;
         u1x.x *= sx; u1x.y *= sx; u1y.x *= sy; u1y.y *= sy;
     }
     // conj(g_a) u_b for ab = xx, xy, yx, yy
-    double v[8];
-    const double2 ga[2] = {gx, gy}, ub[2] = {u1x, u1y};
+    A v[8];
+    const C2<A> ga[2] = {gx, gy}, ub[2] = {u1x, u1y};
 #pragma unroll
     for (int ia = 0; ia < 2; ++ia)
 #pragma unroll
         for (int ib = 0; ib < 2; ++ib) {
-            v[(2 * ia + ib) * 2 + 0] = ga[ia].x * ub[ib].x + ga[ia].y * ub[ib].y;
-            v[(2 * ia + ib) * 2 + 1] = ga[ia].x * ub[ib].y - ga[ia].y * ub[ib].x;
+            v[(2 * ia + ib) * 2 + 0] = fma(ga[ia].x, ub[ib].x, ga[ia].y * ub[ib].y);
+            v[(2 * ia + ib) * 2 + 1] = fma(ga[ia].x, ub[ib].y, -(ga[ia].y * ub[ib].x));
         }
     // block sum: warp butterflies, then the four warps in order
-    __shared__ double red[kAcRows / 32][8];
+    __shared__ A red[kAcRows / 32][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        double x = v[j];
+        A x = v[j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         v[j] = x;
@@ -267,11 +314,18 @@ __global__ void __launch_bounds__(kAcRows) k_ac_observe(AcArgs a)
         for (int j = 0; j < 8; ++j) red[warp][j] = v[j];
     __syncthreads();
     if (threadIdx.x < 8) {
-        double acc = 0.0;
+        A acc = (A)0;
 #pragma unroll
         for (int wp = 0; wp < kAcRows / 32; ++wp) acc += red[wp][threadIdx.x];
-        a.block_partial[((int64_t)blockIdx.x * (B / 4) + quad) * 8 + threadIdx.x] = acc;
+        a.block_partial[((int64_t)blockIdx.x * (B / 4) + quad) * 8 + threadIdx.x] = (double)acc;
     }
+}
+
+// FP32 copy of the per-entry bond vectors (for the FP32 observer).
+__global__ void k_vec_to_f32(int64_t n, const double *src, float *dst)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
 }
 
 // One CTA of 512 threads per (sample, quad): thread (j, k) sums value k of
@@ -377,6 +431,13 @@ cudaError_t launch_ac_observe(const AcArgs &a, int fp32, int cplx, cudaStream_t 
         if (cplx) k_ac_observe<double, true><<<grid, kAcRows, 0, st>>>(a);
         else k_ac_observe<double, false><<<grid, kAcRows, 0, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_to_f32(int64_t n, const double *src, float *dst, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_vec_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, src, dst);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,7 @@ struct tbpm_ctx {
     int64_t norm_ref_len = 0;
     // AC-conductivity correlation
     double *d_bond_dx = nullptr, *d_bond_dy = nullptr;   // [nnz_pad] bond vector per entry
+    float *d_bond_dx32 = nullptr, *d_bond_dy32 = nullptr; // FP32 copies
     bool ac_on = false;
     double2 *d_ac_corr = nullptr;          // [n_samples][n_states / 4][4][n_steps + 1]
     double *d_ac_partial = nullptr;        // [n_rows / kAcRows][4][8]
@@ -95,6 +96,7 @@ struct tbpm_ctx {
     int qe_K = 0;
     double2 *d_qe_acc = nullptr;           // [K][n_rows][n_states]
     const double2 *d_qe_coef = nullptr;    // [n_steps + 1][K] of the current run
+    const float2 *d_qe_coef_f = nullptr;   // its FP32 copy
     bool have_run = false;
     std::vector<cudaEvent_t> events;
     tbpm_stats stats;
@@ -188,9 +190,12 @@ void free_hamiltonian(tbpm_ctx *c)
     cudaFree(c->d_norm_ref);
     cudaFree(c->d_bond_dx);
     cudaFree(c->d_bond_dy);
+    cudaFree(c->d_bond_dx32);
+    cudaFree(c->d_bond_dy32);
     c->d_norm_ref = nullptr;
     c->norm_ref_len = 0;
     c->d_bond_dx = c->d_bond_dy = nullptr;
+    c->d_bond_dx32 = c->d_bond_dy32 = nullptr;
     c->d_block_partial = nullptr;
     c->d_chunk_count = nullptr;
     c->block_partial_len = 0;
@@ -984,6 +989,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 qa.chunk_sample = c->H.chunk_sample;
                 qa.step = c->d_step;
                 qa.coef = c->d_qe_coef;
+                qa.coef_f = c->d_qe_coef_f;
+                qa.scale_f = fp32 ? g.scale_f : nullptr;
                 qa.acc = c->d_qe_acc;
                 qa.n_rows = c->H.n_rows;
                 qa.B = g.B;
@@ -997,6 +1004,9 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             oa.H = Hv;
             oa.dx = c->d_bond_dx;
             oa.dy = c->d_bond_dy;
+            oa.dx32 = c->d_bond_dx32;
+            oa.dy32 = c->d_bond_dy32;
+            oa.scale_f = fp32 ? g.scale_f : nullptr;
             oa.psi = g.buf[bi];
             oa.scale = fp32 ? g.scale : nullptr;
             oa.chunk_sample = c->H.chunk_sample;
@@ -1641,9 +1651,14 @@ extern "C" int tbpm_set_bond_vectors(tbpm_ctx *c, const double *dx, const double
     if (!c->d_bond_dx) {
         rc = dalloc(c, &c->d_bond_dx, nnz);
         if (!rc) rc = dalloc(c, &c->d_bond_dy, nnz);
+        if (!rc) rc = dalloc(c, &c->d_bond_dx32, nnz);
+        if (!rc) rc = dalloc(c, &c->d_bond_dy32, nnz);
         if (rc) {
             cudaFree(c->d_bond_dx);
-            c->d_bond_dx = nullptr;
+            cudaFree(c->d_bond_dy);
+            cudaFree(c->d_bond_dx32);
+            c->d_bond_dx = c->d_bond_dy = nullptr;
+            c->d_bond_dx32 = nullptr;
             return rc;
         }
     }
@@ -1661,6 +1676,8 @@ extern "C" int tbpm_set_bond_vectors(tbpm_ctx *c, const double *dx, const double
     if (!rc && e == cudaSuccess)
         e = launch_bond_vectors(c->H.n_hop, c->H.bond_rows, c->H.slice_ptr, c->H.col, d_x, d_y,
                                 claim, c->d_bond_dx, c->d_bond_dy, c->d_flags, c->st);
+    if (!rc && e == cudaSuccess) e = launch_vec_to_f32((int64_t)nnz, c->d_bond_dx, c->d_bond_dx32, c->st);
+    if (!rc && e == cudaSuccess) e = launch_vec_to_f32((int64_t)nnz, c->d_bond_dy, c->d_bond_dy32, c->st);
     int h_err = 0;
     if (!rc && e == cudaSuccess)
         e = cudaMemcpyAsync(&h_err, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->st);
@@ -1673,7 +1690,10 @@ extern "C" int tbpm_set_bond_vectors(tbpm_ctx *c, const double *dx, const double
     if (h_err) {
         cudaFree(c->d_bond_dx);
         cudaFree(c->d_bond_dy);
+        cudaFree(c->d_bond_dx32);
+        cudaFree(c->d_bond_dy32);
         c->d_bond_dx = c->d_bond_dy = nullptr;
+        c->d_bond_dx32 = c->d_bond_dy32 = nullptr;
         return fail(c, TBPM_E_INVALID_ARG, (h_err & 2) ? "non-finite bond vector"
                                                        : "bond list does not match the Hamiltonian");
     }
@@ -1853,23 +1873,29 @@ extern "C" int tbpm_quasi_eigenstates(tbpm_ctx *c, double z, int n_steps, int n_
                     make_double2(f * cos(energies[k] * t), f * sin(energies[k] * t));
             }
         }
+    std::vector<float2> tab_f(tab.size());
+    for (size_t i = 0; i < tab.size(); ++i) tab_f[i] = make_float2((float)tab[i].x, (float)tab[i].y);
     int rc = enter(c);
     if (rc) return rc;
     double2 *d_tab = nullptr, *d_out = nullptr;
+    float2 *d_tab_f = nullptr;
     double *d_norms = nullptr;
     int64_t *d_off = nullptr;
     auto release = [&]() {
         cudaFree(c->d_qe_acc);
         c->d_qe_acc = nullptr;
         c->d_qe_coef = nullptr;
+        c->d_qe_coef_f = nullptr;
         c->qe_on = false;
         cudaFree(d_tab);
+        cudaFree(d_tab_f);
         cudaFree(d_norms);
         cudaFree(d_off);
         if (where_out == TBPM_HOST) cudaFree(d_out);
     };
     rc = dalloc(c, &c->d_qe_acc, (size_t)K * n_rows * S);
     if (!rc) rc = dalloc(c, &d_tab, tab.size());
+    if (!rc) rc = dalloc(c, &d_tab_f, tab_f.size());
     if (!rc) rc = dalloc(c, &d_norms, (size_t)K * S * c->n_samples);
     if (!rc) rc = dalloc(c, &d_off, (size_t)c->n_samples + 1);
     if (!rc && where_out == TBPM_HOST) rc = dalloc(c, &d_out, (size_t)K * S * n_orb);
@@ -1879,6 +1905,9 @@ extern "C" int tbpm_quasi_eigenstates(tbpm_ctx *c, double z, int n_steps, int n_
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice,
                             c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_tab_f, tab_f.data(), tab_f.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_off, c->sample_off.data(), (c->n_samples + 1) * sizeof(int64_t),
                             cudaMemcpyHostToDevice, c->st);
@@ -1891,9 +1920,11 @@ extern "C" int tbpm_quasi_eigenstates(tbpm_ctx *c, double z, int n_steps, int n_
     c->qe_K = K;
     const int pf = flags & (TBPM_PROP_PROFILE | TBPM_PROP_GRAPH | TBPM_PROP_PERSISTENT);
     c->d_qe_coef = d_tab;
+    c->d_qe_coef_f = d_tab_f;
     rc = tbpm_propagate(c, z, n_steps, precision, nullptr, TBPM_HOST, pf);
     if (!rc) {
         c->d_qe_coef = d_tab + (size_t)(n_steps + 1) * K;
+        c->d_qe_coef_f = d_tab_f + (size_t)(n_steps + 1) * K;
         rc = tbpm_propagate(c, z, n_steps, precision, nullptr, TBPM_HOST, pf | TBPM_PROP_BACKWARD);
     }
     c->qe_on = false;
@@ -1902,7 +1933,8 @@ extern "C" int tbpm_quasi_eigenstates(tbpm_ctx *c, double z, int n_steps, int n_
         release();
         return fail(c, rc, m);
     }
-    e = launch_qe_finish(c->d_qe_acc, K, S, n_rows, n_orb, c->n_samples, c->H.user_to_row,
+    e = launch_qe_finish(c->d_qe_acc, precision == TBPM_FP32, K, S, n_rows, n_orb, c->n_samples,
+                         c->H.user_to_row,
                          c->H.orb_sample, d_off, d_out, d_norms, c->st);
     if (e == cudaSuccess && where_out == TBPM_HOST)
         e = cudaMemcpyAsync(out, d_out, (size_t)K * S * n_orb * sizeof(double2),

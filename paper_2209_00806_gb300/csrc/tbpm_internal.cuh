@@ -105,8 +105,10 @@ constexpr int kAcRows = 128;         // rows per observer block
 struct AcArgs {
     SellView H;                      // values of the group precision
     const double *dx, *dy;           // [nnz_pad] bond vector of each stored entry (nm)
+    const float *dx32, *dy32;        // their FP32 copies (FP32 form)
     const void *psi;                 // current buffer of the group, [row][B]
     const double *scale;             // FP32 norm carry [n_samples][B] or nullptr
+    const float *scale_f;            // its FP32 copy
     const int32_t *chunk_sample;
     int64_t n_rows;
     int B;                           // multiple of 4
@@ -124,19 +126,22 @@ struct AcReduceArgs {
 struct QeArgs {
     const void *psi;                 // current buffer of the group, [row][B]
     const double *scale;             // FP32 norm carry [n_samples][B] or nullptr
+    const float *scale_f;            // its FP32 copy
     const int32_t *chunk_sample;
     const int *step;                 // per sample, already advanced by k_reduce
     const double2 *coef;             // [n_steps + 1][K] (tau / 2 pi) w_n e^{i E_k t_n}
-    double2 *acc;                    // [K][n_rows][S]
+    const float2 *coef_f;            // its FP32 copy
+    void *acc;                       // [K][n_rows][S], complex in the group's precision
     int64_t n_rows;
     int B, s0, S, K;
 };
 cudaError_t launch_qe_acc(const QeArgs &a, int fp32, cudaStream_t st);
-cudaError_t launch_qe_finish(const double2 *acc, int K, int S, int64_t n_rows, int64_t n_orb,
+cudaError_t launch_qe_finish(const void *acc, int fp32, int K, int S, int64_t n_rows, int64_t n_orb,
                              int n_samples, const int32_t *user_to_row, const int32_t *orb_sample,
                              const int64_t *orb_off, double2 *out, double *norms, cudaStream_t st);
 cudaError_t launch_ac_observe(const AcArgs &a, int fp32, int cplx, cudaStream_t st);
 cudaError_t launch_ac_reduce(const AcReduceArgs &a, cudaStream_t st);
+cudaError_t launch_vec_to_f32(int64_t n, const double *src, float *dst, cudaStream_t st);
 // Preparation of the AC states, FP64, four lanes per row ([n_rows][4] complex):
 // lanes 0 and 1 <- psi_p; lanes 2, 3 <- J_x psi_p, J_y psi_p; Fermi Clenshaw
 // terms out = c v + gamma H~ x + zeta z on all four lanes; the result goes
