@@ -565,7 +565,8 @@ def run_observables(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     optical = args.workload == "optical"
-    w = workloads.optical_graphene() if optical else workloads.quasi_graphene()
+    w = (workloads.optical_graphene(n_steps=args.time_steps) if optical
+         else workloads.quasi_graphene(n_steps=args.time_steps // 2))
     smp = w.sample
     S, NT = w.n_states, w.n_steps
     theta = torch.as_tensor(w.thetas()[0], device=dev)
