@@ -314,14 +314,15 @@ __device__ __forceinline__ int64_t block_in_order(const TermArgs &a)
     return a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
 }
 
-// FP32: at most 40 registers (12 blocks of 128 threads per SM; 80 for the
-// wide lanes) -- the kernel is latency-bound, so residency matters; FP64:
-// unconstrained.
+// FP32: at most 40 registers for 16-byte lanes and 64 for the wide lanes
+// (16 blocks of 64 threads per SM, without spills; the 85-register bound
+// before was 5 % slower per term) -- the kernel is latency-bound, so
+// residency matters; FP64: unconstrained.
 // Thread t works on row t / (L RS), lane (t / RS) % L, part t % RS.  Rows are
 // a multiple of 1024, so a warp never straddles the last row (the part
 // shuffles see full warps).
 template <typename V, int L, int SPL, bool CX, int RS>
-__global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 3) : 1) k_term(TermArgs a)
+__global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 4) : 1) k_term(TermArgs a)
 {
     const int64_t t = block_in_order(a) * blockDim.x + threadIdx.x;
     const int64_t r = t / (L * RS);
