@@ -262,6 +262,20 @@ def reduce_max_time(ms, world, device=None):
     return float(t.item())
 
 
+def combine_mean(arr, world, device=None):
+    """Average of a per-rank array over the ranks: the one exchange of the
+    replica decomposition (each rank's DOS comes from its own random states;
+    the DOS is linear in C, so the mean of the ranks' DOS is the DOS of all
+    states).  Outside the timed region."""
+    if world <= 1:
+        return np.asarray(arr, dtype=np.float64)
+    import torch
+    import torch.distributed as dist
+    t = torch.as_tensor(np.ascontiguousarray(arr, dtype=np.float64), device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.cpu().numpy() / world
+
+
 def sample_part(w, k):
     """Sample k of a (possibly batched) workload as its own bond list."""
     from tbpm_inputs import lattice
@@ -430,6 +444,9 @@ def run_gb300(args):
                           w.n_energies, w.e_range, w.seed, [w.sample_seeds[0]])
         cpu, _ = oracle_sample(wp, theta[:, :part.n_orb], 15.0)
 
+    # DOS over the states of every rank (host-side mean of the per-rank DOS)
+    d_all = combine_mean(r0["res"][1], world, dev if world > 1 and dist.get_backend() == "nccl"
+                         else None)
     if rank == 0:
         cfg = config_dict(w, args, world)
         cfg["chebyshev_products_per_step"] = M - 1
@@ -446,6 +463,8 @@ def run_gb300(args):
             "e2e": e2e, "gpu_launches": int(r0["launches"]),
             "clocks": r0["clocks"], "cpu_baseline": cpu,
         }
+        de = float(r0["res"][0][1] - r0["res"][0][0])
+        line["dos_all_ranks"] = {"states": S * world, "integral": float(np.sum(d_all[0]) * de)}
         if head == N.TBPM_FP32:
             line["fp32_renormalisations"] = r0["renorm"]
             line["fp32_max_norm_drift"] = r0["drift"]

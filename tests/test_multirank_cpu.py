@@ -1,6 +1,7 @@
 """The multi-process (replica) path of the benchmark on CPU: two gloo ranks
 draw different states from the same workload recipe, agree on the slowest
-rank's time, and the job value is the units of all ranks over that time."""
+rank's time (the job value is the units of all ranks over that time), and
+combine their DOS into the mean over all ranks' states."""
 import os
 import socket
 
@@ -27,8 +28,9 @@ def _rank(rank, world, port, out):
     args = argparse.Namespace(workload="disordered", L=16, time_steps=8)
     w, theta = bench.workload_inputs(args, rank)
     ms = bench.reduce_max_time(100.0 + 50.0 * rank, world)
+    mean = bench.combine_mean(np.array([[rank + 1.0, 2.0 * rank, 5.0]]), world)
     dist.barrier()
-    out.put((rank, float(theta[0, :4].sum()), w.sample.n_orb, ms))
+    out.put((rank, float(theta[0, :4].sum()), w.sample.n_orb, ms, mean.tolist()))
     dist.destroy_process_group()
 
 
@@ -43,7 +45,8 @@ def test_two_gloo_ranks_replicas():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, th0, n0, ms0), (r1, th1, n1, ms1) = res
+    (r0, th0, n0, ms0, m0), (r1, th1, n1, ms1, m1) = res
     assert n0 == n1                      # same lattice on every rank
     assert th0 != th1                    # independent states per rank (weak scaling)
     assert ms0 == ms1 == 150.0           # both see the slowest rank's time
+    assert m0 == m1 == [[1.5, 1.0, 5.0]]  # the DOS mean over both ranks' states
