@@ -6,7 +6,7 @@
 //   factored out, units eV nm; d_rc = r_c - r_r is the bond vector of the
 //   stored entry, so periodic bonds carry their own image); then the Fermi
 //   operator by Clenshaw's
-//   recurrence on all four lanes, b_k = c_k v + 2 H~ b_{k+1} - b_{k+2},
+//   recurrence on lanes 1 .. 3, b_k = c_k v + 2 H~ b_{k+1} - b_{k+2},
 //   f v = c_0 v / 2 + H~ b_1 - b_2.
 // Observer (after every time step, in the group's precision): per row and
 // lane quad, g_a = sum_c H~_rc d^a_rc psi_2,c and the four products
@@ -119,16 +119,17 @@ __global__ void k_current4(SellView H, int64_t n_rows, const double *dxe, const 
     v4[r * 4 + 3] = make_double2(s * gy.y, -s * gy.x);
 }
 
-// out = c v + gamma (H~ x) + zeta z, one thread per (row, lane); x == nullptr
-// drops the product, z == nullptr the last term; out may alias z.
+// out = c v + gamma (H~ x) + zeta z, one thread per (row, lane) for lanes
+// 1 .. 3 (lane 0 holds psi itself, which needs no Fermi operator); x ==
+// nullptr drops the product, z == nullptr the last term; out may alias z.
 template <typename VT, bool CX>
 __global__ void k_cheb_real4(SellView H, int64_t n_rows, double c, double gamma, double zeta,
                              const double2 *v, const double2 *x, const double2 *z, double2 *out)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n_rows * 4) return;
-    const int64_t r = t >> 2;
-    const int l = (int)(t & 3);
+    if (t >= n_rows * 3) return;
+    const int64_t r = t / 3;
+    const int l = 1 + (int)(t % 3);
     double2 y = make_double2(0.0, 0.0);
     if (x) {
         const double d = diag_of<VT>(H.diag, r);
@@ -391,7 +392,7 @@ cudaError_t launch_cheb_real4(SellView H, int fp32_vals, int cplx, int64_t n_row
                               double gamma, double zeta, const double2 *v, const double2 *x,
                               const double2 *z, double2 *out, cudaStream_t st)
 {
-    const unsigned blocks = (unsigned)((n_rows * 4 + 255) / 256);
+    const unsigned blocks = (unsigned)((n_rows * 3 + 255) / 256);
     if (fp32_vals) {
         if (cplx) k_cheb_real4<float, true><<<blocks, 256, 0, st>>>(H, n_rows, c, gamma, zeta, v, x, z, out);
         else k_cheb_real4<float, false><<<blocks, 256, 0, st>>>(H, n_rows, c, gamma, zeta, v, x, z, out);

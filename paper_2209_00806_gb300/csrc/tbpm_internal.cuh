@@ -144,7 +144,7 @@ cudaError_t launch_ac_reduce(const AcReduceArgs &a, cudaStream_t st);
 cudaError_t launch_vec_to_f32(int64_t n, const double *src, float *dst, cudaStream_t st);
 // Preparation of the AC states, FP64, four lanes per row ([n_rows][4] complex):
 // lanes 0 and 1 <- psi_p; lanes 2, 3 <- J_x psi_p, J_y psi_p; Fermi Clenshaw
-// terms out = c v + gamma H~ x + zeta z on all four lanes; the result goes
+// terms out = c v + gamma H~ x + zeta z on lanes 1 .. 3; the result goes
 // back to the caller's layout as the four states of p.
 cudaError_t launch_ac_load(const double2 *psi_user, int p, int64_t n_orb,
                            const int32_t *user_to_row, double2 *v4, cudaStream_t st);
