@@ -190,10 +190,13 @@ int tbpm_bessel_coefficients(double z, double tol, int max_terms, double *J_out,
  *              (where_out), or NULL to keep C on the device only
  *   flags      TBPM_PROP_*
  * Each time step runs M-1 fused sparse-product terms of the Clenshaw form
- * of the paper's Chebyshev sum and one deterministic FP64 reduction.
- * In FP32 the norm of each state is carried in FP64: when |<phi|phi> - 1|
- * exceeds the renormalisation bound the next step starts from phi / |phi|
- * (tbpm_set_norm_policy).
+ * of the paper's Chebyshev sum and one deterministic reduction (FP64 from
+ * the 128-row block partials up; in the FP32 form the products and the
+ * block sums are FP32).  In FP32 the norm of each state is carried in FP64:
+ * when <phi|phi> drifts from its value at n = 0 by more than the
+ * renormalisation bound (relative) the next step starts from phi rescaled
+ * to that norm (tbpm_set_norm_policy).  The drift checks are relative to
+ * the norm at n = 0 in both forms.
  * Errors: STATE (no Hamiltonian or states), INVALID_ARG, NORM_DRIFT (drift
  * above the hard bound: s too small), NONFINITE, TIMEOUT (a bounded device
  * wait of the TMA or fused kernels expired), CUDA. */
@@ -275,18 +278,20 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
 
-/* Norm policy of the propagation (a5).  FP32: when |<phi|phi> - 1| of a
- * state exceeds renorm_fp32 (default 1e-5) after a step, the next step starts
- * from phi / |phi| (the norm is summed and the factor applied in FP64
- * before rounding to FP32); above hard_fp32 (default 1e-2) the call fails
- * with TBPM_E_NORM_DRIFT.  FP64: above hard_fp64 (default 1e-6) the call
- * fails.  The unitary evolution of Sec. 2.2 keeps the norm; drift means
- * rounding (FP32) or an s below the spectral radius.  Bounds must be > 0. */
+/* Norm policy of the propagation (a5).  The drift of a state is
+ * |<phi|phi> / <phi|phi>_0 - 1| against its squared norm at n = 0 (1 for
+ * normalised states).  FP32: when it exceeds renorm_fp32 (default 1e-5)
+ * after a step, the next step starts from phi rescaled to the initial norm
+ * (the norm is summed and the factor formed in FP64 before rounding to
+ * FP32); above hard_fp32 (default 1e-2) the call fails with
+ * TBPM_E_NORM_DRIFT.  FP64: above hard_fp64 (default 1e-6) the call fails.
+ * The unitary evolution of Sec. 2.2 keeps the norm; drift means rounding
+ * (FP32) or an s below the spectral radius.  Bounds must be > 0. */
 int tbpm_set_norm_policy(tbpm_ctx *ctx, double renorm_fp32, double hard_fp32, double hard_fp64);
 
 /* Autotuner: for the current Hamiltonian and states, time probe_steps
  * (1..64) steps of each candidate launch shape -- state-group width (the
- * block width of the blocked sparse product), threads per block (128, 256)
+ * block width of the blocked sparse product), threads per block (64, 128, 256)
  * and TBPM_VARIANT_* bits -- and keep the fastest as the context's
  * configuration for `precision`.  The chosen values are written to the
  * non-NULL out pointers.  The slice height is fixed at 32 rows (one warp's
