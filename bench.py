@@ -186,26 +186,34 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ reference --
-def oracle_sample(w, theta, budget_s=15.0):
+def oracle_sample(w, theta, budget_s=15.0, rows=False):
     """Time the CPU FP64 oracle, as it stands, on a bounded sample of the same
-    workload: one state, the first k time steps (k sized to ~budget_s)."""
+    workload: one state, the first k time steps (k sized to ~budget_s).
+    rows=False: the plain serial oracle (one core); rows=True: its twin with
+    the paper's OpenMP-over-rows scheme on every core the process may use."""
     import oracle
+    fn = oracle.propagate_rows if rows else oracle.propagate
     psi0 = oracle.phase_states(theta[:1])
     t0 = time.perf_counter()
-    oracle.propagate(w.sample, w.s, w.z, 1, psi0)
+    fn(w.sample, w.s, w.z, 1, psi0)
     one = time.perf_counter() - t0
     k = max(1, min(w.n_steps, int(budget_s / max(one, 1e-9))))
     t0 = time.perf_counter()
-    oracle.propagate(w.sample, w.s, w.z, k, psi0)
+    fn(w.sample, w.s, w.z, k, psi0)
     dt = time.perf_counter() - t0
     M = oracle.n_terms(w.z)
     units = w.sample.n_orb * 1 * k * (M - 1)
-    return dict(value=units / dt, unit="orbital-Chebyshev-steps/s", cores=1, kind="oracle",
+    cores = oracle.threads() if rows else 1
+    how = (f"C, OpenMP over rows, {cores} threads" if rows else "single-threaded C")
+    return dict(value=units / dt, unit="orbital-Chebyshev-steps/s", cores=cores, kind="oracle",
                 sample=f"1 state x {k} time steps of the {w.sample.n_orb}-orbital workload "
-                       f"(single-threaded C, {dt:.1f} s)"), dt
+                       f"({how}, {dt:.1f} s)",
+                affinity_cores=n_cores()), dt
 
 
 def run_reference(args):
+    """The reference arm: the oracle with the paper's OpenMP-over-rows scheme
+    on all host cores, on a bounded sample of the workload per step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -215,20 +223,23 @@ def run_reference(args):
     vals = []
     times = []
     sample_desc = None
+    cores = 1
     for i in range(args.warmup + args.steps):
-        cb, dt = oracle_sample(w, theta, per_step_budget)
+        cb, dt = oracle_sample(w, theta, per_step_budget, rows=True)
         if i >= args.warmup:
             vals.append(cb["value"])
             times.append(dt)
             sample_desc = cb["sample"]
+            cores = cb["cores"]
     v = statistics.mean(vals)
     line = {"impl": "reference", "metric": "orbital-Chebyshev-steps/s", "value": v,
             "unit": "orbital-Chebyshev-steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(w, args, 1),
-            "cpu_baseline": {"value": v, "unit": "orbital-Chebyshev-steps/s", "cores": 1,
-                             "kind": "oracle", "sample": sample_desc},
+            "cpu_baseline": {"value": v, "unit": "orbital-Chebyshev-steps/s", "cores": cores,
+                             "kind": "oracle", "sample": sample_desc,
+                             "affinity_cores": n_cores()},
             "e2e": {"value": v, "unit": "orbital-Chebyshev-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     line["config"]["chebyshev_products_per_step"] = M - 1
@@ -315,7 +326,6 @@ def run_gb300(args):
     M = len(tb.tbpm_bessel_coefficients(w.z))
     units_per_step = smp.n_orb * S * NT * (M - 1)
     prop = tb.Propagator(local, stream.cuda_stream)
-    corr_d = torch.empty((NS, S, NT + 1), dtype=torch.complex128, device=dev)
     # precisions measured per workload: the first one is the headline `value`
     legs = {"disordered": [N.TBPM_FP32, N.TBPM_FP64], "batched": [N.TBPM_FP32],
             "graphene_dos": [N.TBPM_FP64], "tbg": [N.TBPM_FP32]}[args.workload]
@@ -328,8 +338,8 @@ def run_gb300(args):
     def one_step(precision, flags):
         prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets, flags=bflags)
         prop.set_phase_states(d_th)
-        prop.propagate(w.z, NT, precision, out=corr_d, flags=flags)
-        c = corr_d.mean(dim=1).cpu().numpy()          # state average per sample
+        N.tbpm_propagate(prop.ctx, w.z, NT, precision, None, None, flags)   # C kept on the GPU
+        c = prop.correlation()                         # state average per sample (GPU)
         out = [tb.dos(c[k], w.tau, *w.e_range, w.n_energies) for k in range(NS)]
         return out[0][0], np.stack([d for _, d in out])
 
@@ -409,7 +419,7 @@ def run_gb300(args):
         h_hj = torch.from_numpy(np.ascontiguousarray(smp.hop_j)).pin_memory()
         h_hv = torch.from_numpy(np.ascontiguousarray(smp.hop_v)).pin_memory()
         h_th = torch.from_numpy(np.ascontiguousarray(theta)).pin_memory()
-        h_c = torch.empty((NS, S, NT + 1), dtype=torch.complex128).pin_memory()
+        h_c = torch.empty((NS, NT + 1), dtype=torch.complex128).pin_memory()
         offs = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.int64)
 
         def host_step():
@@ -417,9 +427,10 @@ def run_gb300(args):
                                      h_hi.data_ptr(), h_hj.data_ptr(), h_hv.data_ptr(), w.s, NS,
                                      offs, N.TBPM_HOST, bflags)
             N.tbpm_set_phase_states(prop.ctx, S, h_th.data_ptr(), N.TBPM_HOST)
-            N.tbpm_propagate(prop.ctx, w.z, NT, head, h_c.data_ptr(), N.TBPM_HOST,
+            N.tbpm_propagate(prop.ctx, w.z, NT, head, None, N.TBPM_HOST,
                              N.TBPM_PROP_GRAPH if graph else 0)
-            c = h_c.numpy().mean(axis=1)
+            N.tbpm_correlation(prop.ctx, h_c.data_ptr(), N.TBPM_HOST)   # state average (GPU)
+            c = h_c.numpy()
             return [tb.dos(c[k], w.tau, *w.e_range, w.n_energies) for k in range(NS)]
 
         for _ in range(args.warmup):
@@ -431,7 +442,7 @@ def run_gb300(args):
         barrier()
         dt = reduce_max_time(time.perf_counter() - t0, world, dev)
         h2d = sum(x.numel() * x.element_size() for x in (h_on, h_hi, h_hj, h_hv, h_th))
-        d2h = h_c.numel() * h_c.element_size() + NS * S * (NT + 1) * 8   # C + norms
+        d2h = h_c.numel() * h_c.element_size() + NS * S * (NT + 1) * 8   # mean C + norms
         e2e = {"value": total_units / dt, "unit": "orbital-Chebyshev-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * dt / args.steps, "precision": name[head]}
@@ -442,7 +453,9 @@ def run_gb300(args):
         from tbpm_inputs import workloads as _wl
         wp = _wl.Workload(w.name, part, np.array([0, part.n_orb]), w.s, w.z, S, NT,
                           w.n_energies, w.e_range, w.seed, [w.sample_seeds[0]])
-        cpu, _ = oracle_sample(wp, theta[:, :part.n_orb], 15.0)
+        cpu, _ = oracle_sample(wp, theta[:, :part.n_orb], 12.0)
+        allc, _ = oracle_sample(wp, theta[:, :part.n_orb], 8.0, rows=True)
+        cpu["all_cores"] = {k: allc[k] for k in ("value", "cores", "sample")}
 
     # DOS over the states of every rank (host-side mean of the per-rank DOS)
     d_all = combine_mean(r0["res"][1], world, dev if world > 1 and dist.get_backend() == "nccl"
@@ -517,13 +530,12 @@ def run_differentiable(args):
     theta = torch.as_tensor(w.thetas()[0], device=dev)
     d = {k: torch.as_tensor(getattr(smp, k), device=dev) for k in ("hop_i", "hop_j", "hop_v", "onsite")}
     p = tb.Propagator(local, stream.cuda_stream)
-    corr = torch.empty((1, S, NT + 1), dtype=torch.complex128, device=dev)
 
     def dos_of(hv, on):
         p.build(smp.n_orb, on, d["hop_i"], d["hop_j"], hv, w.s)
         p.set_phase_states(theta)
-        p.propagate(w.z, NT, N.TBPM_FP64, out=corr)
-        return tb.dos(corr.mean(dim=1)[0].cpu().numpy(), w.tau, *w.e_range, w.n_energies)[1]
+        N.tbpm_propagate(p.ctx, w.z, NT, N.TBPM_FP64, None)
+        return tb.dos(p.correlation()[0], w.tau, *w.e_range, w.n_energies)[1]
 
     target = dos_of(torch.as_tensor(pw.sample.hop_v, device=dev),
                     torch.zeros(smp.n_orb, dtype=torch.float64, device=dev))
@@ -532,7 +544,7 @@ def run_differentiable(args):
         D = dos_of(d["hop_v"], d["onsite"])
         loss = float(np.sum((D - target) ** 2))
         g = tb.dos_adjoint(2.0 * (D - target), NT, w.tau, *w.e_range)
-        gbar = torch.as_tensor(np.ascontiguousarray(np.broadcast_to(g / S, (1, S, NT + 1))), device=dev)
+        gbar = p.correlation_adjoint(NT, torch.as_tensor(g[None, :], device=dev))
         gh, go = p.adjoint(w.z, NT, gbar, K=64)
         return loss, gh, go
 

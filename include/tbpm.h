@@ -118,6 +118,13 @@ typedef struct tbpm_stats {
 /* Library version, major * 10000 + minor * 100 + patch. */
 int tbpm_version(void);
 
+/* Compute capability the library's kernels were compiled for, as
+ * major * 10 + minor (103 for sm_103a), read from the loaded kernel image of
+ * the current device (cudaFuncGetAttributes).  A build check, not part of
+ * the method.  Errors: INVALID_ARG (NULL), CUDA (no device or no image for
+ * it); the message is read with tbpm_last_error(NULL). */
+int tbpm_kernel_binary_version(int *version);
+
 /* Create a context on CUDA device `device`.  `cuda_stream` (a cudaStream_t,
  * may be NULL for the legacy default stream) is borrowed: the library orders
  * its work after what is already queued there and makes the stream wait for
@@ -190,9 +197,11 @@ int tbpm_bessel_coefficients(double z, double tol, int max_terms, double *J_out,
  *              (where_out), or NULL to keep C on the device only
  *   flags      TBPM_PROP_*
  * Each time step runs M-1 fused sparse-product terms of the Clenshaw form
- * of the paper's Chebyshev sum and one deterministic reduction (FP64 from
- * the 128-row block partials up; in the FP32 form the products and the
- * block sums are FP32).  In FP32 the norm of each state is carried in FP64:
+ * of the paper's Chebyshev sum and one deterministic reduction: FP64 in the
+ * FP64 form; in the FP32 form each row's products are exact float pairs and
+ * a block's rows are summed as float pairs (about 48 significant bits, error
+ * free up to that width), FP64 from the block partials up.  In FP32 the
+ * norm of each state is carried in FP64:
  * when <phi|phi> drifts from its value at n = 0 by more than the
  * renormalisation bound (relative) the next step starts from phi rescaled
  * to that norm (tbpm_set_norm_policy).  The drift checks are relative to
@@ -204,9 +213,21 @@ int tbpm_propagate(tbpm_ctx *ctx, double z, int n_steps, int precision, double *
                    int where_out, int flags);
 
 /* State-averaged correlation of the last propagation (Sec. 2.4, the average
- * over S random states in Eq. dos_tbpm): complex128 [n_samples][n_steps + 1]
- * written to host or device memory. */
+ * over S random states in Eq. dos_tbpm): complex128 [n_samples][n_steps + 1],
+ * C-bar_n = (sum_p C_n^(p)) / S with the states added in order, formed on the
+ * GPU and written to host or device memory (where_out).
+ * Errors: INVALID_ARG, STATE (no propagation), OOM, CUDA. */
 int tbpm_correlation(tbpm_ctx *ctx, double *corr_avg_out, int where_out);
+
+/* Adjoint of tbpm_correlation: from gbar_avg = dL/dRe C-bar_n + i dL/dIm C-bar_n,
+ * complex128 [n_samples][n_steps + 1] (host or device, `where`), the
+ * derivative of L with respect to each state's C_n,
+ *   gbar_out[k][p][n] = gbar_avg[k][n] / S,
+ * complex128 [n_samples][n_states][n_steps + 1] (host or device, where_out),
+ * as tbpm_propagate_adjoint takes it.  S = the states currently set.
+ * Errors: INVALID_ARG, STATE (no Hamiltonian or states), OOM, CUDA. */
+int tbpm_correlation_adjoint(tbpm_ctx *ctx, int n_steps, const double *gbar_avg, int where,
+                             double *gbar_out, int where_out);
 
 /* Current states phi(t) of the last propagation in caller order, complex128
  * [n_states][n_orb] (host or device) -- a checkpoint; tbpm_set_states +
@@ -310,16 +331,22 @@ int tbpm_autotune(tbpm_ctx *ctx, int precision, double z, int probe_steps, int *
  *   corr_out   device complex128 [n_states]: <psi0_s|phi_s>
  *   norm_out   device double [n_states]: <phi_s|phi_s>
  *   cuda_stream the stream to run on (cudaStream_t, may be NULL)
- * Same FP64 sums as the closing reduction of tbpm_propagate.  Allocates
+ * The same quantities as the closing reduction of tbpm_propagate, summed
+ * deterministically in FP64 (each block over a fixed grid-stride set of
+ * rows, then the blocks in order); they agree with tbpm_propagate's to
+ * rounding, not bit for bit, since the summation order differs.  Allocates
  * nothing: its scratch is one fixed device array of 786,496 bytes
- * (n_states <= 16), held by every GPU that loads the library until the
- * process exits.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Calls share the array, so calls that overlap
- * on the GPU race: serialise them.  Asynchronous on cuda_stream; the
- * message of a failure is read with tbpm_last_error(NULL).
+ * (n_states <= 16; rows unlimited), held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks the
+ * array's address up (cudaGetSymbolAddress) with that device current and
+ * caches it per device ordinal for the life of the process; make that
+ * first call before any stream capture.  The cached address belongs to the
+ * device's primary context: calls after cudaDeviceReset, or from a
+ * non-primary context, are not supported.  Calls share the array, so calls
+ * that overlap on the GPU race: serialise them.  Asynchronous on
+ * cuda_stream; the message of a failure is read with tbpm_last_error(NULL).
  * Errors: INVALID_ARG (NULL pointer, n_orb < 1, n_states outside 1..16),
- * CUDA. */
+ * UNSUPPORTED (current device ordinal above 63), CUDA. */
 int tbpm_correlation_noalloc(const double *psi0, const double *phi, int64_t n_orb,
                              int n_states, double *corr_out, double *norm_out,
                              void *cuda_stream);

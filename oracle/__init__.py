@@ -29,17 +29,20 @@ import numpy as np
 
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "tbpm_oracle.c"
+_SRCS = [_SRC, _HERE / "tbpm_oracle_rows.c"]
 _LIB_PATH = _HERE / "_build" / "liboracle.so"
 _lib = None
 
 
 def build(force: bool = False) -> Path:
-    """Compile the oracle with gcc (plain -O2, IEEE arithmetic, no fast-math)."""
+    """Compile the oracle with gcc (plain -O2, IEEE arithmetic, no fast-math,
+    no FMA contraction under -std=c99); OpenMP only in the row-parallel twin."""
     _LIB_PATH.parent.mkdir(exist_ok=True)
-    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+    newest = max(p.stat().st_mtime for p in _SRCS)
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < newest:
         tmp = _LIB_PATH.with_suffix(f".so.{os.getpid()}")
         subprocess.run(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-D_GNU_SOURCE",
-                        "-o", str(tmp), str(_SRC), "-lm"], check=True)
+                        "-fopenmp", "-o", str(tmp), *map(str, _SRCS), "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -64,6 +67,9 @@ def _load():
         lib.oracle_dos.argtypes = [P, i32, f64, f64, f64, i32, P, P]
         lib.oracle_gradient.argtypes = [i64, P, i64, P, P, P, f64, f64, i32, i32, P, P, P, P]
         lib.oracle_dos_adjoint.argtypes = [P, i32, f64, f64, f64, i32, P]
+        lib.oracle_propagate_rows.argtypes = [i64, P, i64, P, P, P, P, f64, f64, i32, i32,
+                                              P, P, P, P]
+        lib.oracle_threads.argtypes = []
         _lib = lib
     return _lib
 
@@ -124,8 +130,20 @@ def phase_states(theta: np.ndarray) -> np.ndarray:
     return out
 
 
+def threads() -> int:
+    """Threads the row-parallel twin uses (OMP_NUM_THREADS, else all cores)."""
+    return int(_load().oracle_threads())
+
+
+def propagate_rows(sample, s: float, z: float, n_steps: int, psi0: np.ndarray,
+                   want_norms: bool = False, want_psi: bool = False):
+    """:func:`propagate` by the paper's OpenMP-over-rows scheme on all host
+    cores: bit-identical states, correlations and norms to about one rounding."""
+    return propagate(sample, s, z, n_steps, psi0, want_norms, want_psi, _rows=True)
+
+
 def propagate(sample, s: float, z: float, n_steps: int, psi0: np.ndarray,
-              want_norms: bool = False, want_psi: bool = False):
+              want_norms: bool = False, want_psi: bool = False, _rows: bool = False):
     """Returns corr [S, n_steps+1] (and norms [S, n_steps+1], psi [S, N])."""
     psi0 = np.ascontiguousarray(np.atleast_2d(psi0), dtype=np.complex128)
     S, n = psi0.shape
@@ -136,8 +154,9 @@ def propagate(sample, s: float, z: float, n_steps: int, psi0: np.ndarray,
     psi = np.empty((S, n), dtype=np.complex128) if want_psi else None
     hi, hj, re, im = _hops(sample)
     ons = _f64(sample.onsite)
-    rc = _load().oracle_propagate(n, _p(ons), sample.n_hop, _p(hi), _p(hj), _p(re), _p(im),
-                                  s, z, n_steps, S, _p(psi0), _p(corr), _p(norms), _p(psi))
+    fn = _load().oracle_propagate_rows if _rows else _load().oracle_propagate
+    rc = fn(n, _p(ons), sample.n_hop, _p(hi), _p(hj), _p(re), _p(im), s, z, n_steps, S,
+            _p(psi0), _p(corr), _p(norms), _p(psi))
     if rc != 0:
         raise RuntimeError(f"oracle_propagate failed ({rc})")
     out = [corr]

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("tbpm_bessel_coefficients", _I32, [_F64, _F64, _I32, P, ctypes.POINTER(_I32)]),
     ("tbpm_propagate", _I32, [P, _F64, _I32, _I32, P, _I32, _I32]),
     ("tbpm_correlation", _I32, [P, P, _I32]),
+    ("tbpm_correlation_adjoint", _I32, [P, _I32, P, _I32, P, _I32]),
+    ("tbpm_kernel_binary_version", _I32, [ctypes.POINTER(_I32)]),
     ("tbpm_get_states", _I32, [P, P, _I32]),
     ("tbpm_get_norms", _I32, [P, P]),
     ("tbpm_dos", _I32, [P, _I32, _F64, _I32, _F64, _F64, _I32, P, P]),
@@ -221,6 +223,21 @@ def tbpm_propagate(ctx, z, n_steps, precision, corr_out=None, where_out=None, fl
 def tbpm_correlation(ctx, out, where_out=None):
     return check(ctx, lib.tbpm_correlation(ctx, ptr(out),
                                            where_of(out) if where_out is None else where_out))
+
+
+def tbpm_correlation_adjoint(ctx, n_steps, gbar_avg, gbar_out, where=None, where_out=None):
+    if where is None:
+        where = where_of(gbar_avg)
+    if where_out is None:
+        where_out = where_of(gbar_out)
+    return check(ctx, lib.tbpm_correlation_adjoint(ctx, n_steps, ptr(gbar_avg), where,
+                                                   ptr(gbar_out), where_out))
+
+
+def tbpm_kernel_binary_version() -> int:
+    v = _I32()
+    check(None, lib.tbpm_kernel_binary_version(ctypes.byref(v)))
+    return v.value
 
 
 def tbpm_get_states(ctx, out, where_out=None):

@@ -8,7 +8,6 @@ Marshalling only; the arithmetic is the library's.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import _native as N
@@ -22,10 +21,9 @@ class _Dos(torch.autograd.Function):
         p.build(spec["n_orb"], onsite.detach().contiguous(), spec["hop_i"], spec["hop_j"],
                 hop_v.detach().contiguous(), spec["s"])
         p.set_phase_states(spec["theta"])
-        S, NT = spec["theta"].shape[0], spec["n_steps"]
-        corr = torch.empty((1, S, NT + 1), dtype=torch.complex128, device=hop_v.device)
-        p.propagate(spec["z"], NT, N.TBPM_FP64, out=corr)
-        cavg = corr.mean(dim=1)[0].cpu().numpy()
+        NT = spec["n_steps"]
+        N.tbpm_propagate(p.ctx, spec["z"], NT, N.TBPM_FP64, None)   # C stays on the GPU
+        cavg = p.correlation()[0]                      # state average, on the GPU
         _, d = dos(cavg, spec["z"] / spec["s"], *spec["e_range"], spec["n_e"])
         ctx.save_for_backward(hop_v, onsite)
         ctx.spec = spec
@@ -36,15 +34,15 @@ class _Dos(torch.autograd.Function):
         hop_v, onsite = ctx.saved_tensors
         spec = ctx.spec
         p = spec["prop"]
-        S, NT = spec["theta"].shape[0], spec["n_steps"]
+        NT = spec["n_steps"]
         g = dos_adjoint(grad_d.detach().cpu().numpy(), NT, spec["z"] / spec["s"],
                         *spec["e_range"])
-        gbar = torch.as_tensor(np.ascontiguousarray(np.broadcast_to(g / S, (1, S, NT + 1))),
-                               device=hop_v.device)
         # the context may have been reused since the forward pass: rebuild
         p.build(spec["n_orb"], onsite.detach().contiguous(), spec["hop_i"], spec["hop_j"],
                 hop_v.detach().contiguous(), spec["s"])
         p.set_phase_states(spec["theta"])
+        # dL/dC-bar -> dL/dC of every state (the adjoint of the state average)
+        gbar = p.correlation_adjoint(NT, torch.as_tensor(g[None, :], device=hop_v.device))
         gh, go = p.adjoint(spec["z"], NT, gbar, spec["K"])
         return gh, go, None
 

@@ -340,7 +340,16 @@ void tbpm::set_thread_error(const std::string &m) { g_last_error = m; }
 
 // ---------------------------------------------------------------------------
 
-extern "C" int tbpm_version(void) { return 10000; }
+extern "C" int tbpm_version(void) { return 10100; }
+
+extern "C" int tbpm_kernel_binary_version(int *version)
+{
+    if (!version) return fail(nullptr, TBPM_E_INVALID_ARG, "version is NULL");
+    cudaError_t e = kernel_binary_version(version);
+    if (e != cudaSuccess)
+        return fail(nullptr, TBPM_E_CUDA, std::string("cudaFuncGetAttributes: ") + cudaGetErrorString(e));
+    return TBPM_OK;
+}
 
 extern "C" const char *tbpm_last_error(const tbpm_ctx *ctx)
 {
@@ -1306,28 +1315,70 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
 extern "C" int tbpm_correlation(tbpm_ctx *c, double *out, int where_out)
 {
     if (!c || !out) return fail(c, TBPM_E_INVALID_ARG, "NULL argument");
+    if (where_out != TBPM_HOST && where_out != TBPM_DEVICE)
+        return fail(c, TBPM_E_INVALID_ARG, "where_out must be TBPM_HOST or TBPM_DEVICE");
     if (!c->have_run) return fail(c, TBPM_E_STATE, "no propagation yet");
     const int n1 = c->corr_steps + 1;
-    const size_t cnt = (size_t)c->n_samples * c->n_states * n1;
-    std::vector<double2> all(cnt);
-    CUDA_OR_FAIL(c, cudaMemcpy(all.data(), c->d_corr, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
-    std::vector<double> avg((size_t)c->n_samples * n1 * 2, 0.0);
-    for (int s = 0; s < c->n_samples; ++s)
-        for (int n = 0; n < n1; ++n) {
-            double re = 0, im = 0;
-            for (int p = 0; p < c->n_states; ++p) {
-                const double2 v = all[((size_t)s * c->n_states + p) * n1 + n];
-                re += v.x;
-                im += v.y;
-            }
-            avg[((size_t)s * n1 + n) * 2] = re / c->n_states;
-            avg[((size_t)s * n1 + n) * 2 + 1] = im / c->n_states;
+    const size_t cnt = (size_t)c->n_samples * n1;
+    int rc = enter(c);
+    if (rc) return rc;
+    double2 *d = nullptr;
+    if (where_out == TBPM_DEVICE) {
+        d = (double2 *)out;
+    } else {
+        rc = dalloc(c, &d, cnt);
+        if (rc) return rc;
+    }
+    CUDA_OR_FAIL(c, launch_corr_mean(c->d_corr, c->n_samples, c->n_states, n1, d, c->st));
+    if (where_out != TBPM_DEVICE) {
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(out, d, cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));
+        cudaFree(d);
+    }
+    c->err.clear();
+    return leave(c);
+}
+
+extern "C" int tbpm_correlation_adjoint(tbpm_ctx *c, int n_steps, const double *gbar_avg,
+                                        int where, double *gbar_out, int where_out)
+{
+    if (!c || !gbar_avg || !gbar_out) return fail(c, TBPM_E_INVALID_ARG, "NULL argument");
+    if (n_steps < 0) return fail(c, TBPM_E_INVALID_ARG, "n_steps < 0");
+    if ((where != TBPM_HOST && where != TBPM_DEVICE) ||
+        (where_out != TBPM_HOST && where_out != TBPM_DEVICE))
+        return fail(c, TBPM_E_INVALID_ARG, "where must be TBPM_HOST or TBPM_DEVICE");
+    if (!c->have_h || c->n_states < 1)
+        return fail(c, TBPM_E_STATE, "build the Hamiltonian and set states first");
+    const int n1 = n_steps + 1;
+    const size_t cnt_in = (size_t)c->n_samples * n1;
+    const size_t cnt_out = cnt_in * c->n_states;
+    int rc = enter(c);
+    if (rc) return rc;
+    const double2 *din = nullptr;
+    bool owned_in = false;
+    rc = stage(c, reinterpret_cast<const double2 *>(gbar_avg), cnt_in, where,
+               const_cast<double2 **>(&din), &owned_in);
+    if (rc) return rc;
+    double2 *dout = nullptr;
+    if (where_out == TBPM_DEVICE) {
+        dout = (double2 *)gbar_out;
+    } else {
+        rc = dalloc(c, &dout, cnt_out);
+        if (rc) {
+            if (owned_in) cudaFree((void *)din);
+            return rc;
         }
-    if (where_out == TBPM_DEVICE)
-        CUDA_OR_FAIL(c, cudaMemcpy(out, avg.data(), avg.size() * sizeof(double), cudaMemcpyHostToDevice));
-    else
-        memcpy(out, avg.data(), avg.size() * sizeof(double));
-    return TBPM_OK;
+    }
+    cudaError_t e = launch_corr_mean_adjoint(din, c->n_samples, c->n_states, n1, dout, c->st);
+    if (e == cudaSuccess && where_out != TBPM_DEVICE)
+        e = cudaMemcpyAsync(gbar_out, dout, cnt_out * sizeof(double2), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (owned_in) cudaFree((void *)din);
+    if (where_out != TBPM_DEVICE) cudaFree(dout);
+    if (e != cudaSuccess)
+        return fail(c, TBPM_E_CUDA, std::string("correlation adjoint: ") + cudaGetErrorString(e));
+    c->err.clear();
+    return leave(c);
 }
 
 extern "C" int tbpm_get_states(tbpm_ctx *c, double *phi_out, int where_out)

@@ -341,14 +341,14 @@ __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 4) : 1) 
 // chunk's block partials in block order.  Every sum has a fixed order, so the
 // result does not depend on which block finishes last.
 //
-// GB300 runs FP64 at 1/58 of the FP32 rate, so the reduction is shaped to
-// spend few FP64 operations: in the FP32 form the per-row products and the
-// sum over the rows of a block are formed in FP32 (each block partial covers
-// at most 128 rows; its rounding is far below that of the FP32 states
-// themselves) and everything from the block partials up is FP64; in the FP64
-// form every product and sum is FP64, but rows are summed in a shared-memory
-// tree (one add per value) instead of a butterfly (one add per value and
-// level on every lane).
+// GB300 runs FP64 at a small fraction of the FP32 rate, so the FP32 form's
+// reduction stays on the FP32 pipe without giving up FP64-grade sums: each
+// row's products are exact float pairs (TwoProduct), the block's rows are
+// added as pairs (TwoSum, Fast2Sum; about 48 significant bits), and one
+// pair -> FP64 conversion per value and block hands over to FP64 from the
+// block partials up.  In the FP64 form every product and sum is FP64, with
+// rows summed in a shared-memory tree (one add per value) instead of a
+// butterfly (one add per value and level on every lane).
 constexpr int kFinalThreads = 128;
 
 template <typename V, int L, int SPL, bool COMPUTE, bool CX>
@@ -356,10 +356,12 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
 {
     constexpr int B = L * SPL;
     constexpr int ROWS = kFinalThreads / L;          // rows per block
-    constexpr int NW = kFinalThreads / 32;
-    __shared__ double red[sizeof(V) == 8 ? ROWS * B * 3 : 1];
-    __shared__ float redf[NW * B * 3];
-    __shared__ double grp[8][B * 3];
+    constexpr int NV = B * 3;                        // (re, im, norm) per state
+    constexpr int P = kFinalThreads / NV;            // FP32: parts per value
+    __shared__ double red[sizeof(V) == 8 ? ROWS * NV : 1];
+    __shared__ FF redf[sizeof(V) == 4 ? ROWS * NV : 1];
+    __shared__ FF redp[sizeof(V) == 4 ? P * NV : 1];
+    __shared__ double grp[8][NV];
     __shared__ int last;
     const int64_t bid = block_in_order(a);
     const int64_t t = bid * kFinalThreads + threadIdx.x;
@@ -375,47 +377,41 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
         o = ld<V, L, SPL>(a.out, r, l);
     }
     const Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
-    V pre[SPL], pim[SPL], pnr[SPL];
-#pragma unroll
-    for (int j = 0; j < SPL; ++j) {
-        pre[j] = fma(p0.re[j], o.re[j], p0.im[j] * o.im[j]);
-        pim[j] = fma(p0.re[j], o.im[j], -(p0.im[j] * o.re[j]));
-        pnr[j] = fma(o.re[j], o.re[j], o.im[j] * o.im[j]);
-    }
     const int lrow = threadIdx.x / L;
-    if (sizeof(V) == 4) {
-        // FP32: butterfly over the rows of the warp, then FP64 per warp
+    if constexpr (sizeof(V) == 4) {
+        // FP32: exact per-row products as float pairs, [row][value] in shared
+        // memory; value v's rows are summed in P fixed parts (rows part,
+        // part + P, ...), then the parts in order
 #pragma unroll
-        for (int off = L; off < 32; off <<= 1) {
-#pragma unroll
-            for (int j = 0; j < SPL; ++j) {
-                pre[j] += __shfl_xor_sync(0xffffffffu, pre[j], off);
-                pim[j] += __shfl_xor_sync(0xffffffffu, pim[j], off);
-                pnr[j] += __shfl_xor_sync(0xffffffffu, pnr[j], off);
-            }
-        }
-        // ... and over the block's warps in FP32 too; one FP32 -> FP64
-        // conversion per value and block.  GB300 issues an FP64 instruction,
-        // a conversion included, at a small fraction of the FP32 rate per warp
-        // instruction, whatever the number of active lanes, so the block keeps
-        // them to one warp instruction per value.
-        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-        if (lane < L) {
-#pragma unroll
-            for (int j = 0; j < SPL; ++j) {
-                const int b = lane * SPL + j;
-                redf[(warp * B + b) * 3 + 0] = pre[j];
-                redf[(warp * B + b) * 3 + 1] = pim[j];
-                redf[(warp * B + b) * 3 + 2] = pnr[j];
-            }
+        for (int j = 0; j < SPL; ++j) {
+            FF re, im, nr;
+            ff_dot3((float)p0.re[j], (float)p0.im[j], (float)o.re[j], (float)o.im[j], re, im, nr);
+            const int v = (l * SPL + j) * 3;
+            redf[lrow * NV + v + 0] = re;
+            redf[lrow * NV + v + 1] = im;
+            redf[lrow * NV + v + 2] = nr;
         }
         __syncthreads();
-        if (threadIdx.x < B * 3) {
-            float s = 0.f;
-            for (int w = 0; w < NW; ++w) s += redf[w * B * 3 + threadIdx.x];
-            grp[0][threadIdx.x] = (double)s;
+        if (threadIdx.x < P * NV) {
+            const int v = threadIdx.x % NV, part = threadIdx.x / NV;
+            FF acc = redf[part * NV + v];
+            for (int row = part + P; row < ROWS; row += P) acc = ff_add(acc, redf[row * NV + v]);
+            redp[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            FF acc = redp[threadIdx.x];
+            for (int part = 1; part < P; ++part) acc = ff_add(acc, redp[part * NV + threadIdx.x]);
+            grp[0][threadIdx.x] = ff_to_double(acc);
         }
     } else {
+        V pre[SPL], pim[SPL], pnr[SPL];
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            pre[j] = fma(p0.re[j], o.re[j], p0.im[j] * o.im[j]);
+            pim[j] = fma(p0.re[j], o.im[j], -(p0.im[j] * o.re[j]));
+            pnr[j] = fma(o.re[j], o.re[j], o.im[j] * o.im[j]);
+        }
         // FP64: shared-memory tree, 8 groups of rows then the groups
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
@@ -425,14 +421,14 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
             red[(lrow * B + b) * 3 + 2] = (double)pnr[j];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 8 * B * 3; idx += kFinalThreads) {
-            const int gidx = idx / (B * 3), v = idx % (B * 3);
+        for (int idx = threadIdx.x; idx < 8 * NV; idx += kFinalThreads) {
+            const int gidx = idx / NV, v = idx % NV;
             double s = 0.0;
-            for (int row = gidx; row < ROWS; row += 8) s += red[row * B * 3 + v];
+            for (int row = gidx; row < ROWS; row += 8) s += red[row * NV + v];
             grp[gidx][v] = s;
         }
         __syncthreads();
-        if (threadIdx.x < B * 3) {
+        if (threadIdx.x < NV) {
             double s = 0.0;
             for (int g2 = 0; g2 < 8; ++g2) s += grp[g2][threadIdx.x];
             grp[0][threadIdx.x] = s;
@@ -596,6 +592,34 @@ __global__ void k_get_states(const void *psi, int64_t n_orb, const int32_t *user
         dst[(int64_t)(g0 + b) * n_orb + u] = StoreC<V, 1>::get(psi, r * B + b);
 }
 
+// State average of the correlation (Sec. 2.4: the mean over the random
+// states in Eq. dos_tbpm): avg[k][n] = (sum_p corr[k][p][n]) / S, the states
+// added in order.
+__global__ void k_corr_mean(const double2 *corr, int n_samples, int S, int n1, double2 *avg)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_samples * n1) return;
+    const int64_t k = i / n1, n = i % n1;
+    double re = 0.0, im = 0.0;
+    for (int p = 0; p < S; ++p) {
+        const double2 v = corr[(k * S + p) * n1 + n];
+        re += v.x;
+        im += v.y;
+    }
+    avg[i] = make_double2(re / S, im / S);
+}
+
+// Its adjoint: each state's C_n gets dL/dC-bar_n / S.
+__global__ void k_corr_mean_adjoint(const double2 *gavg, int n_samples, int S, int n1,
+                                    double2 *g)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_samples * S * n1) return;
+    const int64_t n = i % n1, k = i / ((int64_t)S * n1);
+    const double2 v = gavg[k * n1 + n];
+    g[i] = make_double2(v.x / S, v.y / S);
+}
+
 template <typename V, int L, int SPL, bool CX, int RS = 1>
 cudaError_t launch_term_t(const TermArgs &a, int threads, cudaStream_t st)
 {
@@ -724,6 +748,30 @@ cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaSt
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st)
 {
     k_reduce<<<dim3(a.n_samples, kReduceSplit), 64, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t kernel_binary_version(int *version)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_corr_mean);
+    if (e == cudaSuccess) *version = fa.binaryVersion;
+    return e;
+}
+
+cudaError_t launch_corr_mean(const double2 *corr, int n_samples, int S, int n1, double2 *avg,
+                             cudaStream_t st)
+{
+    const int64_t n = (int64_t)n_samples * n1;
+    k_corr_mean<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(corr, n_samples, S, n1, avg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_mean_adjoint(const double2 *gavg, int n_samples, int S, int n1,
+                                     double2 *g, cudaStream_t st)
+{
+    const int64_t n = (int64_t)n_samples * S * n1;
+    k_corr_mean_adjoint<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gavg, n_samples, S, n1, g);
     return cudaGetLastError();
 }
 

@@ -212,26 +212,33 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_fused(FusedArgs f)
         void *out = f.bufs[tm.out];
         const void *x = tm.x < 0 ? f.psi : f.bufs[tm.x];
         const void *z = tm.z < 0 ? nullptr : f.bufs[tm.z];
-        float fre[SPL], fim[SPL], fnr[SPL];
+        FF fre[SPL], fim[SPL], fnr[SPL];
         double dre[SPL], dim[SPL], dnr[SPL];
         auto zero = [&]() {
 #pragma unroll
             for (int q = 0; q < SPL; ++q) {
-                fre[q] = fim[q] = fnr[q] = 0.f;
+                fre[q] = fim[q] = fnr[q] = FF{0.f, 0.f};
                 dre[q] = dim[q] = dnr[q] = 0.0;
             }
         };
-        // block sum of the per-thread partials (FP32 form: FP32 within the
-        // warp, FP64 from the warp sums up) into `dst` (B*3 doubles)
+        auto shfl_ff = [&](FF &v, int off) {
+            FF w;
+            w.hi = __shfl_xor_sync(0xffffffffu, v.hi, off);
+            w.lo = __shfl_xor_sync(0xffffffffu, v.lo, off);
+            v = ff_add(v, w);
+        };
+        // block sum of the per-thread partials (FP32 form: exact products
+        // and float-pair sums within the warp, FP64 from the warp sums up)
+        // into `dst` (B*3 doubles)
         auto block_sum = [&](double *dst) {
 #pragma unroll
             for (int off = L; off < 32; off <<= 1) {
 #pragma unroll
                 for (int q = 0; q < SPL; ++q) {
                     if (sizeof(V) == 4) {
-                        fre[q] += __shfl_xor_sync(0xffffffffu, fre[q], off);
-                        fim[q] += __shfl_xor_sync(0xffffffffu, fim[q], off);
-                        fnr[q] += __shfl_xor_sync(0xffffffffu, fnr[q], off);
+                        shfl_ff(fre[q], off);
+                        shfl_ff(fim[q], off);
+                        shfl_ff(fnr[q], off);
                     } else {
                         dre[q] += __shfl_xor_sync(0xffffffffu, dre[q], off);
                         dim[q] += __shfl_xor_sync(0xffffffffu, dim[q], off);
@@ -243,9 +250,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_fused(FusedArgs f)
 #pragma unroll
                 for (int q = 0; q < SPL; ++q) {
                     const int b = lane * SPL + q;
-                    red[warp][b * 3 + 0] = sizeof(V) == 4 ? (double)fre[q] : dre[q];
-                    red[warp][b * 3 + 1] = sizeof(V) == 4 ? (double)fim[q] : dim[q];
-                    red[warp][b * 3 + 2] = sizeof(V) == 4 ? (double)fnr[q] : dnr[q];
+                    red[warp][b * 3 + 0] = sizeof(V) == 4 ? ff_to_double(fre[q]) : dre[q];
+                    red[warp][b * 3 + 1] = sizeof(V) == 4 ? ff_to_double(fim[q]) : dim[q];
+                    red[warp][b * 3 + 2] = sizeof(V) == 4 ? ff_to_double(fnr[q]) : dnr[q];
                 }
             }
             __syncthreads();
@@ -269,11 +276,17 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_fused(FusedArgs f)
                 unpf(__ldg(reinterpret_cast<const Lane *>(f.psi0) + r * L + l), p0);
 #pragma unroll
                 for (int q = 0; q < SPL; ++q) {
-                    const V pre = fma(p0.re[q], o.re[q], p0.im[q] * o.im[q]);
-                    const V pim = fma(p0.re[q], o.im[q], -(p0.im[q] * o.re[q]));
-                    const V pnr = fma(o.re[q], o.re[q], o.im[q] * o.im[q]);
-                    if (sizeof(V) == 4) { fre[q] += (float)pre; fim[q] += (float)pim; fnr[q] += (float)pnr; }
-                    else { dre[q] += (double)pre; dim[q] += (double)pim; dnr[q] += (double)pnr; }
+                    if constexpr (sizeof(V) == 4) {
+                        FF pre, pim, pnr;
+                        ff_dot3(p0.re[q], p0.im[q], o.re[q], o.im[q], pre, pim, pnr);
+                        fre[q] = ff_add(fre[q], pre);
+                        fim[q] = ff_add(fim[q], pim);
+                        fnr[q] = ff_add(fnr[q], pnr);
+                    } else {
+                        dre[q] += fma(p0.re[q], o.re[q], p0.im[q] * o.im[q]);
+                        dim[q] += fma(p0.re[q], o.im[q], -(p0.im[q] * o.re[q]));
+                        dnr[q] += fma(o.re[q], o.re[q], o.im[q] * o.im[q]);
+                    }
                 }
                 // a tile of at least one chunk: the chunk's partial is complete here
                 if (R >= kChunkRows && (pass + 1) % passes_per_chunk == 0) {

@@ -4,17 +4,22 @@
 // pool owns the whole device and rejects allocations made behind its back,
 // a plugin that may only allocate at start-up, or a latency-bound loop that
 // cannot afford cudaMalloc/cudaFree, which may synchronise the device.
-// tbpm_correlation_noalloc serves them: it computes the same
-// per-state <psi0|phi> and <phi|phi> as the closing term of tbpm_propagate,
-// with its scratch (per-block partial sums and the finishing tickets) in a
+// tbpm_correlation_noalloc serves them: it computes the same quantities as
+// the closing term of tbpm_propagate, per-state <psi0|phi> and <phi|phi>,
+// summed deterministically in FP64 but in its own order (caller-order rows,
+// grid-stride per block), so the two agree to rounding, not bit for bit.
+// Its scratch (per-block partial sums and the finishing tickets) lives in a
 // fixed, file-scope device array instead of buffers from cudaMalloc.
 //
 // The array is a static __device__ symbol, so every GPU that loads this
 // library holds it (kScratchBytes, under 1 MB) until the process exits.  In
 // host code the symbol's name is only a host-side stand-in: the device
 // address is looked up with cudaGetSymbolAddress once per device, on the
-// first call made on that device (with that device current), and cached.
-// Make that first call before any stream capture begins.  All calls share
+// first call made on that device (with that device current), and cached
+// per device ordinal for the life of the process.  Make that first call
+// before any stream capture begins.  The cached address is the one of the
+// device's primary context: after cudaDeviceReset, or under a non-primary
+// context, it would be stale, so neither is supported.  All calls share
 // the one array, so calls whose kernels overlap on the GPU (different
 // streams, or different host threads on one device) race and must be
 // serialised by the caller.
@@ -48,7 +53,9 @@ NoAllocScratch *g_na_addr[64] = {nullptr};   // device address per device ordina
 // (complex128).  Block b of state s takes rows b*T + t, b*T + t + B*T, ...
 // (fixed assignment), sums them in FP64, reduces the block in a fixed tree,
 // and the last block of the state (ticket after a fence) adds the block sums
-// in block order.  Same arithmetic as the closing term's reduction.
+// in block order.  Deterministic, FP64 throughout; the order differs from
+// the closing term's (which sums internally ordered rows in 1024-row
+// chunks), so the results agree with it to rounding.
 __global__ void __launch_bounds__(kNaThreads) k_corr_noalloc(NoAllocScratch *scr,
                                                            const double2 *psi0,
                                                            const double2 *phi, int64_t n,
@@ -111,8 +118,8 @@ int na_fail(int code, const std::string &m)
 
 using namespace tbpm;
 
-// Same results as the closing reduction of tbpm_propagate, for caller-held
-// device vectors, with no device allocation.  Declared in include/tbpm.h.
+// The closing reduction's quantities for caller-held device vectors, with
+// no device allocation.  Declared in include/tbpm.h.
 extern "C" int tbpm_correlation_noalloc(const double *psi0, const double *phi, int64_t n_orb,
                                         int n_states, double *corr_out, double *norm_out,
                                         void *cuda_stream)
@@ -126,9 +133,12 @@ extern "C" int tbpm_correlation_noalloc(const double *psi0, const double *phi, i
                            std::to_string(kScratchBytes) + " bytes)");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64)
+    if (e != cudaSuccess)
         return na_fail(TBPM_E_CUDA, std::string("tbpm_correlation_noalloc: no current device: ") +
                                         cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64)
+        return na_fail(TBPM_E_UNSUPPORTED, "tbpm_correlation_noalloc: device ordinal " +
+                                               std::to_string(dev) + " exceeds 63");
     NoAllocScratch *scr = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_na_mutex);

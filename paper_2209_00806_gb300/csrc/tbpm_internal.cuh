@@ -22,6 +22,44 @@ constexpr int kMaxStates = 64;
 constexpr int kMaxTerms = 128;
 constexpr int kMaxGroups = 64;
 
+// Error-free FP32 transformations for the reductions of the FP32 form.  A
+// float pair (hi, lo) with |lo| <= ulp(hi) / 2 carries about 48 significant
+// bits: the product of two floats is exactly hi + lo (TwoProduct by FMA),
+// and two pairs add with Knuth's TwoSum of the high parts, the low parts
+// and the sum's error folded in, then renormalised (Fast2Sum).  Sums of
+// FP32 products thus accumulate at FP64-grade accuracy on the FP32 pipe;
+// GB300 issues FP64 instructions at a small fraction of the FP32 rate.  The
+// _rn intrinsics keep the compiler from contracting or reassociating them.
+#ifdef __CUDACC__
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return FF{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, t);
+    return FF{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+// <a|o> = conj(a) o and |o|^2 of one complex pair, each as an exact pair sum.
+__device__ __forceinline__ void ff_dot3(float are, float aim, float ore, float oim, FF &re,
+                                        FF &im, FF &nr)
+{
+    re = ff_add(ff_prod(are, ore), ff_prod(aim, oim));
+    im = ff_add(ff_prod(are, oim), ff_neg(ff_prod(aim, ore)));
+    nr = ff_add(ff_prod(ore, ore), ff_prod(oim, oim));
+}
+#endif
+
 // Launch variants of the term kernels (bits of TermArgs::variant).
 constexpr int kVariantZigZag = 1;       // alternate the traversal direction per launch
 constexpr int kVariantStreamHints = 2;  // evict-first loads of the own-row streams
@@ -181,6 +219,14 @@ struct AdjArgs {
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
+// State average of the correlations (and its adjoint, a broadcast of
+// dL/dC-bar / S), complex128 [n_samples][S][n1] <-> [n_samples][n1].
+// Compute capability (major * 10 + minor) the library's kernels were built for.
+cudaError_t kernel_binary_version(int *version);
+cudaError_t launch_corr_mean(const double2 *corr, int n_samples, int S, int n1, double2 *avg,
+                             cudaStream_t st);
+cudaError_t launch_corr_mean_adjoint(const double2 *gavg, int n_samples, int S, int n1,
+                                     double2 *g, cudaStream_t st);
 cudaError_t launch_phase_user(const double *theta, int64_t n_orb, int n_states,
                               const double *inv_sqrt_n, const int32_t *orb_sample,
                               double2 *psi_user, cudaStream_t st);

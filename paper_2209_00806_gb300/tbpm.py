@@ -114,9 +114,27 @@ class Propagator:
                                  None, flags)
         return out, norms
 
-    def correlation(self):
-        out = np.empty((self.n_samples, self.stats()["n_steps"] + 1), dtype=np.complex128)
+    def correlation(self, out=None):
+        """State-averaged C [n_samples, n_steps + 1] of the last propagation
+        (numpy unless ``out``, which may be a CUDA tensor)."""
+        if out is None:
+            out = np.empty((self.n_samples, self.stats()["n_steps"] + 1), dtype=np.complex128)
         N.tbpm_correlation(self.ctx, out)
+        return out
+
+    def correlation_adjoint(self, n_steps, gbar_avg, out=None):
+        """dL/dC per state [n_samples, n_states, n_steps + 1] from dL/dC-bar
+        [n_samples, n_steps + 1] (the adjoint of the state average)."""
+        if out is None:
+            if N.where_of(gbar_avg) == N.TBPM_DEVICE:
+                import torch
+                out = torch.empty((self.n_samples, self.n_states, n_steps + 1),
+                                  dtype=torch.complex128, device=gbar_avg.device)
+            else:
+                out = np.empty((self.n_samples, self.n_states, n_steps + 1), dtype=np.complex128)
+        if isinstance(gbar_avg, np.ndarray):
+            gbar_avg = np.ascontiguousarray(gbar_avg, dtype=np.complex128)
+        N.tbpm_correlation_adjoint(self.ctx, int(n_steps), gbar_avg, out)
         return out
 
     def states(self):

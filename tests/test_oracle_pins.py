@@ -227,3 +227,22 @@ def test_oracle_dos_graphene_vs_bloch_spectrum():
     assert np.max(np.abs(d - ref)) < 1e-9
     # area over [-s, s] is 1 up to the window's leakage
     assert abs(d.sum() * (en[1] - en[0]) - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("kind", ["disordered", "complex"])
+def test_oracle_row_parallel_twin_equals_the_serial_oracle(kind):
+    """The OpenMP-over-rows twin (the paper's thread scheme) performs the
+    serial oracle's operations row by row: bit-identical states; its blocked
+    compensated sums give C and norms within one rounding."""
+    smp = lattice.graphene(150, 149, pbc=True, seed=4, onsite_w=1.0, vacancy_frac=0.02)
+    if kind == "complex":
+        smp = lattice.peierls(lattice.graphene(90, 80, pbc=False, seed=4, onsite_w=0.6,
+                                               with_pos=True), 150.0)
+    th = rng.phases(8, 2, smp.n_orb)           # > 65,536 rows: several sum blocks
+    psi0 = oracle.phase_states(th)
+    a = oracle.propagate(smp, 9.5, Z, 12, psi0, want_norms=True, want_psi=True)
+    b = oracle.propagate_rows(smp, 9.5, Z, 12, psi0, want_norms=True, want_psi=True)
+    assert np.array_equal(a[2], b[2])
+    assert np.max(np.abs(a[0] - b[0])) < 1e-15
+    assert np.max(np.abs(a[1] - b[1])) < 1e-15
+    assert oracle.threads() >= 1

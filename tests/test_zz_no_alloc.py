@@ -46,6 +46,42 @@ def test_noalloc_correlation_matches_propagate_twice():
         torch.cuda.synchronize(dev)
         assert np.max(np.abs(corr.cpu().numpy() - c_ref)) < 1e-10
         assert np.max(np.abs(norm.cpu().numpy() - n_ref)) < 1e-10
+        # and, independently of the library, against numpy's inner products
+        a, b = psi0.cpu().numpy(), phi.cpu().numpy()
+        for k in range(S):
+            assert abs(corr[k].item() - np.vdot(a[k], b[k])) < 1e-12
+            assert abs(norm[k].item() - np.vdot(b[k], b[k]).real) < 1e-12
+
+
+def test_noalloc_many_rows_and_all_sixteen_states_twice():
+    """More rows than one pass of the fixed grid covers (2048 blocks x 256
+    threads = 524,288), so every thread loops and every partial slot is
+    used, with the 16 states the scratch holds; two calls in a row (the
+    tickets must start from zero again), against numpy's FP64 sums."""
+    import torch
+
+    import paper_2209_00806_gb300 as tb
+    N = tb._native
+    n, S = 600_001, 16
+    gen = np.random.default_rng(2024)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    corr = torch.empty(S, dtype=torch.complex128, device=dev)
+    norm = torch.empty(S, dtype=torch.float64, device=dev)
+    for call in range(2):
+        a = gen.normal(size=(S, n)) + 1j * gen.normal(size=(S, n))
+        b = gen.normal(size=(S, n)) + 1j * gen.normal(size=(S, n))
+        da, db = torch.as_tensor(a, device=dev), torch.as_tensor(b, device=dev)
+        rc = N.lib.tbpm_correlation_noalloc(N.ptr(da), N.ptr(db), n, S, N.ptr(corr),
+                                            N.ptr(norm), ctypes.c_void_p(stream))
+        assert rc == N.TBPM_OK, N.tbpm_last_error(None)
+        torch.cuda.synchronize(dev)
+        c, nn = corr.cpu().numpy(), norm.cpu().numpy()
+        for k in range(S):
+            ref = np.vdot(a[k], b[k])
+            nref = np.vdot(b[k], b[k]).real
+            assert abs(c[k] - ref) < 1e-12 * np.sum(np.abs(a[k]) * np.abs(b[k])), (call, k)
+            assert abs(nn[k] - nref) < 1e-12 * nref, (call, k)
 
 
 def test_noalloc_rejects_too_many_states():
