@@ -50,8 +50,14 @@ def parse():
                          "optical: AC-conductivity correlation of 1024^2 graphene at 300 K; "
                          "quasi: quasi-eigenstates at 4 energies of 1024^2 disordered graphene")
     ap.add_argument("--side", type=float, default=200.0, help="tbg flake side in nm")
-    ap.add_argument("--order", default="auto", choices=["auto", "natural", "rcm", "cluster"],
-                    help="row order of the build (auto: cluster for tbg, natural otherwise)")
+    ap.add_argument("--order", default="auto",
+                    choices=["auto", "natural", "rcm", "cluster", "morton", "layers"],
+                    help="row order of the build (auto: natural); tbg: 'morton' (default) or "
+                         "'layers' numbering of the generated flake, or 'rcm'/'cluster' "
+                         "reordering of the layer numbering")
+    ap.add_argument("--no-halo", action="store_true",
+                    help="tbg without --autotune: the plain wide-lane kernel instead of the "
+                         "staged-gather one")
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
@@ -510,6 +516,126 @@ def run_gb300(args):
     return 0
 
 
+def run_tbg(args):
+    """Large twisted bilayer: the flake of side --side nm (1.05 degrees, 6 A
+    Slater-Koster cutoff, ~68 entries per row, s = 12 eV, 8 FP32 states)
+    generated on the GPU by lattice enumeration, numbered along a Morton
+    curve of 0.5 nm cells (--order morton, the default; 'layers' is the
+    layer-by-layer numbering), built FP32-only without the bond map.  One
+    step = build + states + --time-steps steps + correlation + DOS; `value`
+    is the propagation rate (the time-step loop is uniform, so a truncated
+    run measures the full run's rate), the build is reported on its own."""
+    import torch
+
+    import paper_2209_00806_gb300 as tb
+    from paper_2209_00806_gb300 import _native as N
+    from tbpm_inputs import rng, tbg, workloads
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    order = args.order if args.order in ("morton", "layers") else "morton"
+    bflags = N.TBPM_BUILD_NO_FP64 | N.TBPM_BUILD_NO_BOND_MAP
+    if args.order in ("rcm", "cluster"):
+        order = "layers"
+        bflags |= {"rcm": N.TBPM_BUILD_REORDER_RCM, "cluster": N.TBPM_BUILD_REORDER_CLUSTER}[args.order]
+    seed = workloads.master_seed(5)
+    S, NT, s, z = 8, args.time_steps, 12.0, workloads.Z_STEP
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ds = tbg.twisted_bilayer(args.side, order=order, device=dev)
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    theta = rng.phases_torch(seed + 7919 * rank, S, ds.n_orb, device=dev)
+    torch.cuda.empty_cache()
+    M = len(tb.tbpm_bessel_coefficients(z))
+    units_per_step = ds.n_orb * S * NT * (M - 1)
+    prop = tb.Propagator(local, stream.cuda_stream)
+    variant = N.TBPM_VARIANT_ZIGZAG | (N.TBPM_VARIANT_HALO if not args.no_halo else N.TBPM_VARIANT_WIDE)
+    tau = z / s
+
+    def build():
+        prop.build(ds.n_orb, None, ds.hop_i, ds.hop_j, ds.hop_v, s, flags=bflags)
+        prop.set_phase_states(theta)
+
+    build()
+    st0 = prop.stats()
+    if args.no_autotune:
+        prop.launch_config(N.TBPM_FP32, 8, 64, variant)
+        tuned = {"group": 8, "threads": 64, "variant": variant}
+    else:
+        tuned = prop.autotune(z, precision=N.TBPM_FP32, probe_steps=2)
+
+    def one_step():
+        e_b0, e_b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_b0.record(stream)
+        build()
+        e_b1.record(stream)
+        N.tbpm_propagate(prop.ctx, z, NT, N.TBPM_FP32, None, None, N.TBPM_PROP_PROFILE)
+        c = prop.correlation()
+        en, d = tb.dos(c[0], tau, -s, s, 4096)
+        return e_b0, e_b1, prop.stats(), d
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    acc = {"ms_prop": 0.0, "ms_build": 0.0, "ms_term": 0.0, "n_term": 0, "launches": 0, "drift": 0.0}
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            b0, b1, st, d = one_step()
+            b1.synchronize()
+            acc["ms_build"] += b0.elapsed_time(b1)
+            acc["ms_prop"] += st["ms_total"]
+            acc["ms_term"] += st["ms_term_avg"] * st["term_launches"]
+            acc["n_term"] += st["term_launches"]
+            acc["launches"] += st["kernel_launches"]
+            acc["drift"] = max(acc["drift"], st["max_norm_drift"])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    ms_term = acc["ms_term"] / acc["n_term"] if acc["n_term"] else None
+    roof = None
+    if ms_term:
+        ach = st["bytes_term"] / (ms_term * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+                "kernel": "interior Clenshaw term", "algorithmic_bytes_per_launch": st["bytes_term"],
+                "ms_per_launch": ms_term}
+    value = units_per_step * args.steps / (acc["ms_prop"] * 1e-3)
+    line = {"metric": "orbital-Chebyshev-steps/s", "value": value,
+            "unit": "orbital-Chebyshev-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "reductions": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"twisted_bilayer_{args.side:g}nm", "n_orb": int(ds.n_orb),
+                       "n_bonds": int(ds.n_hop),
+                       "entries_per_row": round(st0["nnz_true"] / ds.n_orb, 2),
+                       "stored_entries_incl_padding": int(st0["nnz"]), "twist_deg": 1.05,
+                       "cutoff_A": 6, "s_eV": s, "z": "pi/2", "states": S, "time_steps": NT,
+                       "chebyshev_products_per_step": M - 1, "dos_bins": 4096,
+                       "numbering": {"morton": "Morton curve of 0.5 nm cells, both layers",
+                                     "layers": "layer by layer"}[order],
+                       "row_order": args.order if args.order in ("rcm", "cluster") else "natural",
+                       "launch": tuned, "build_flags": "FP32 only, no bond map",
+                       "value_is": "propagation rate (time-step loop, CUDA events); build separate",
+                       "l2": f"inputs larger than L2 (state vectors {8 * S * ds.n_orb / 1e6:.0f} MB)"},
+            "roofline": roof,
+            "build_ms_per_step": acc["ms_build"] / args.steps,
+            "generator_s": gen_s,
+            "value_including_build": units_per_step * args.steps / (ms * 1e-3),
+            "fp32_max_norm_drift": acc["drift"],
+            "gpu_launches": int(acc["launches"]), "clocks": clk.summary(),
+            "dos_integral": float(np.sum(d) * (2 * s / 4096))}
+    print(json.dumps(line), flush=True)
+    prop.close()
+    return 0
+
+
 def run_differentiable(args):
     """One step = the DOS loss and its gradient with respect to every hopping
     and onsite energy: FP64 forward, host DOS and DOS adjoint, checkpointed
@@ -685,6 +811,8 @@ def main():
         return run_differentiable(args)
     if args.workload in ("optical", "quasi"):
         return run_observables(args)
+    if args.workload == "tbg":
+        return run_tbg(args)
     return run_gb300(args)
 
 

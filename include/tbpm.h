@@ -74,6 +74,9 @@ extern "C" {
 #define TBPM_BUILD_COMPLEX_HOPS 32 /* hop_v holds complex hoppings, (re, im) double
                                       pairs (complex128): Peierls phases of a
                                       magnetic field (Sec. 2.1) */
+#define TBPM_BUILD_NO_BOND_MAP 128 /* keep no bond -> row map (8 bytes per bond):
+                                      tbpm_set_bond_vectors and the adjoint then
+                                      return TBPM_E_STATE; for the largest samples */
 
 /* ---- flags of tbpm_propagate -------------------------------------------- */
 #define TBPM_PROP_PROFILE 1   /* time the kernels with CUDA events (tbpm_stats) */
@@ -296,6 +299,14 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
 #define TBPM_VARIANT_SPLIT2 128      /* each row's entries split over 2 threads (long
                                         rows: more gathers in flight); real values */
 #define TBPM_VARIANT_SPLIT4 256      /* the same over 4 threads (not with SPLIT2) */
+#define TBPM_VARIANT_HALO 512        /* staged gathers: a block of 128 rows copies the
+                                        states of every row its entries reference (its
+                                        halo) into shared memory, then gathers there by
+                                        16-bit positions; real values, FP32 groups of
+                                        4-16 / FP64 of 2-8 states; for long rows.  The
+                                        halo lists are built on first use; a matrix
+                                        with a block referencing over 2048 other rows
+                                        keeps the plain kernel */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
 

@@ -43,6 +43,7 @@ TBPM_BUILD_REORDER_RCM = 8
 TBPM_BUILD_NO_UNIFORM = 16
 TBPM_BUILD_COMPLEX_HOPS = 32
 TBPM_BUILD_REORDER_CLUSTER = 64
+TBPM_BUILD_NO_BOND_MAP = 128
 TBPM_PROP_PROFILE = 1
 TBPM_PROP_GRAPH = 2
 TBPM_PROP_RESUME = 4
@@ -55,6 +56,7 @@ TBPM_VARIANT_FUSED = 8
 TBPM_VARIANT_WIDE = 64
 TBPM_VARIANT_SPLIT2 = 128
 TBPM_VARIANT_SPLIT4 = 256
+TBPM_VARIANT_HALO = 512
 
 
 class TbpmError(RuntimeError):

@@ -520,7 +520,8 @@ extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *
     in.cplx = cplx ? 1 : 0;
     std::string msg;
     rc = build_sell(in, !(flags & TBPM_BUILD_NO_FP64), !(flags & TBPM_BUILD_NO_FP32),
-                    !(flags & TBPM_BUILD_NO_UNIFORM), c->H, c->st, msg);
+                    !(flags & TBPM_BUILD_NO_UNIFORM), !(flags & TBPM_BUILD_NO_BOND_MAP), c->H,
+                    c->st, msg);
     cudaStreamSynchronize(c->st);
     release();
     if (rc) {
@@ -624,7 +625,7 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
         return fail(c, TBPM_E_INVALID_ARG, "threads must be 64, 128 or 256");
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
                                   (3 << kVariantFusedTileShift) | kVariantWide | kVariantSplit2 |
-                                  kVariantSplit4) ||
+                                  kVariantSplit4 | kVariantHalo) ||
         ((variant >> kVariantFusedTileShift) & 3) == 3 ||
         ((variant & kVariantSplit2) && (variant & kVariantSplit4)))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
@@ -911,6 +912,16 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
 
     const size_t cs = fp32 ? 8 : 16;
     const int threads = c->threads[precision];
+    // staged-gather variant: halo lists built on first use; a matrix whose
+    // row blocks reference too many other rows keeps the plain kernels
+    bool halo = (c->variant[precision] & kVariantHalo) && !c->H.cplx &&
+                !(c->variant[precision] & (kVariantTma | kVariantFused));
+    if (halo && !c->H.halo_ptr) {
+        std::string msg;
+        rc = build_halo(c->H, c->st, msg);
+        if (rc == TBPM_E_UNSUPPORTED) halo = false;
+        else if (rc) return fail(c, rc, msg);
+    }
     SellView Hv;
     Hv.slice_ptr = c->H.slice_ptr;
     Hv.col = c->H.col;
@@ -968,6 +979,12 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         base.partial = c->d_partial;
         base.block_partial = c->d_block_partial;
         base.chunk_count = c->d_chunk_count;
+        if (halo) {
+            base.halo_ptr = c->H.halo_ptr;
+            base.halo_rows = c->H.halo_rows;
+            base.lcol = c->H.lcol;
+            base.halo_max = c->H.halo_max;
+        }
         ReduceArgs ra;
         ra.partial = c->d_partial;
         ra.partial2 = c->d_partial2;
@@ -1161,6 +1178,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 t.variant = c->variant[precision];
                 // complex values have the plain term kernels only (16-byte lanes)
                 if (c->H.cplx) t.variant &= kVariantZigZag | kVariantStreamHints;
+                if (!halo) t.variant &= ~kVariantHalo;
                 t.reverse = (t.variant & kVariantZigZag) ? (int)(k & 1) : 0;
                 t.x = L.x < 0 ? g.buf[cur] : g.buf[L.x];
                 t.x_is_psi = L.x < 0;
@@ -1268,10 +1286,18 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         for (auto &g : c->groups) vb += (double)c->n_orb * 4.0 * g.B * cs;
         vb /= c->groups.size();
         // matrix: a column (and a value, unless one value serves all) per
-        // stored entry, and the diagonal
+        // stored entry, and the diagonal; the staged-gather kernel reads a
+        // 16-bit halo position per entry instead of the 32-bit column, plus
+        // the halo lists
         const double valb = fp32 ? 4.0 : 8.0;
-        const double entry = 4.0 + (c->H.uniform ? 0.0 : valb * (c->H.cplx ? 2 : 1));
+        bool halo_used = halo;
+        for (auto &g : c->groups)
+            halo_used = halo_used && halo_launchable(fp32, g.B, false, c->H.halo_max);
+        const double idxb = halo_used ? 2.0 : 4.0;
+        const double entry = idxb + (c->H.uniform ? 0.0 : valb * (c->H.cplx ? 2 : 1));
         S.bytes_term = vb + (double)c->H.nnz_true * entry + (double)c->n_orb * valb;
+        if (halo_used)
+            S.bytes_term += 4.0 * (double)c->H.halo_total + 8.0 * (double)(c->H.n_rows / kHaloRows + 1);
     }
     if (profile) {
         float ms = 0.f;
@@ -1664,12 +1690,24 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                                 kVariantZigZag | kVariantWide | kVariantSplit4,
                                 kVariantTma, kVariantTma | kVariantZigZag, kVariantFused,
                                 kVariantFused | (1 << kVariantFusedTileShift),
-                                kVariantFused | (2 << kVariantFusedTileShift)};
+                                kVariantFused | (2 << kVariantFusedTileShift),
+                                kVariantHalo, kVariantZigZag | kVariantHalo};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
     for (int B : widths)
         for (int T : thread_opts)
             for (int V : variant_opts) {
+                // the staged-gather kernel sets its own block size; it needs real
+                // values and a matrix whose halo lists fit
+                if ((V & kVariantHalo) && (T != thread_opts[0] || c->H.cplx ||
+                                           !halo_launchable(precision == TBPM_FP32, B, false, 0)))
+                    continue;
+                if ((V & kVariantHalo) && !c->H.halo_ptr) {
+                    std::string msg;
+                    const int hr = build_halo(c->H, c->st, msg);
+                    if (hr == TBPM_E_UNSUPPORTED) continue;
+                    if (hr) return fail(c, hr, msg);
+                }
                 int rc = tbpm_set_launch_config(c, precision, B, T, V);
                 if (rc) return rc;
                 rc = tbpm_propagate(c, z, probe_steps, precision, nullptr, TBPM_HOST,
@@ -1693,6 +1731,8 @@ extern "C" int tbpm_set_bond_vectors(tbpm_ctx *c, const double *dx, const double
 {
     if (!c) return fail(nullptr, TBPM_E_INVALID_ARG, "ctx is NULL");
     if (!c->have_h) return fail(c, TBPM_E_STATE, "build the Hamiltonian first");
+    if (c->H.n_hop > 0 && !c->H.bond_rows)
+        return fail(c, TBPM_E_STATE, "the Hamiltonian was built without the bond map");
     if (c->H.n_hop > 0 && (!dx || !dy)) return fail(c, TBPM_E_INVALID_ARG, "bond vectors missing");
     if (where != TBPM_HOST && where != TBPM_DEVICE)
         return fail(c, TBPM_E_INVALID_ARG, "where must be TBPM_HOST or TBPM_DEVICE");

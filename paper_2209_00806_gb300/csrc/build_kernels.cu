@@ -14,7 +14,9 @@
 
 #include <string.h>
 
+#include <algorithm>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "tbpm_internal.cuh"
@@ -158,10 +160,11 @@ int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st,
     return rc;
 }
 
-// Values are VW doubles per entry: 1 (real hoppings) or 2 (complex, re/im).
-template <int VW>
+// Values are VW numbers of type T (double, or float when only the FP32 copy
+// is kept) per entry: 1 (real hoppings) or 2 (complex, re/im).
+template <int VW, typename T>
 __global__ void k_pad_fill(int64_t n_rows, const int64_t *slice_ptr, int32_t *col,
-                           double *val)
+                           T *val)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_rows) return;
@@ -171,14 +174,14 @@ __global__ void k_pad_fill(int64_t n_rows, const int64_t *slice_ptr, int32_t *co
     int w = (int)((slice_ptr[q + 1] - base) / kSliceRows);
     for (int k = 0; k < w; ++k) {
         col[base + (int64_t)k * kSliceRows + lr] = (int32_t)r;
-        for (int q = 0; q < VW; ++q) val[(base + (int64_t)k * kSliceRows + lr) * VW + q] = 0.0;
+        for (int q = 0; q < VW; ++q) val[(base + (int64_t)k * kSliceRows + lr) * VW + q] = (T)0;
     }
 }
 
-template <int VW>
+template <int VW, typename T>
 __global__ void k_fill(int64_t n_hop, const int64_t *hi, const int64_t *hj, const double *hv,
                        double inv_s, const int32_t *user_to_row, const int64_t *slice_ptr,
-                       int32_t *fill, int32_t *col, double *val)
+                       int32_t *fill, int32_t *col, T *val)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= n_hop) return;
@@ -189,12 +192,12 @@ __global__ void k_fill(int64_t n_hop, const int64_t *hi, const int64_t *hj, cons
     int pj = atomicAdd(&fill[rj], 1);
     int64_t ej = slice_ptr[rj / kSliceRows] + (int64_t)pj * kSliceRows + rj % kSliceRows;
     col[ej] = ri;
-    // H_ij = t, H_ji = conj(t)
-    val[ei * VW] = hv[b * VW] * inv_s;
-    val[ej * VW] = hv[b * VW] * inv_s;
+    // H_ij = t, H_ji = conj(t), scaled in FP64 and rounded once to T
+    val[ei * VW] = (T)(hv[b * VW] * inv_s);
+    val[ej * VW] = (T)(hv[b * VW] * inv_s);
     if (VW == 2) {
-        val[ei * VW + 1] = hv[b * VW + 1] * inv_s;
-        val[ej * VW + 1] = -(hv[b * VW + 1] * inv_s);
+        val[ei * VW + 1] = (T)(hv[b * VW + 1] * inv_s);
+        val[ej * VW + 1] = (T)(-(hv[b * VW + 1] * inv_s));
     }
 }
 
@@ -210,9 +213,9 @@ __global__ void k_diag(int64_t n_orb, const double *onsite, double inv_s,
 // product's summation order is independent of the fill order; then the
 // Gershgorin row bound |d_r| + sum |H~_rc|, max-reduced as the bit pattern of
 // a non-negative double (which orders like an unsigned integer).
-template <int VW>
+template <int VW, typename T>
 __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int32_t *deg,
-                            const double *diag, int32_t *col, double *val,
+                            const double *diag, int32_t *col, T *val,
                             unsigned long long *gersh_bits, unsigned long long *band)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -222,11 +225,11 @@ __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int3
     auto E = [&](int k) { return base + (int64_t)k * kSliceRows; };
     for (int a = 1; a < d; ++a) {
         int32_t c = col[E(a)];
-        double v0 = val[E(a) * VW], v1 = VW == 2 ? val[E(a) * VW + 1] : 0.0;
+        T v0 = val[E(a) * VW], v1 = VW == 2 ? val[E(a) * VW + 1] : (T)0;
         int b = a - 1;
         while (b >= 0) {
             int32_t cb = col[E(b)];
-            double w0 = val[E(b) * VW], w1 = VW == 2 ? val[E(b) * VW + 1] : 0.0;
+            T w0 = val[E(b) * VW], w1 = VW == 2 ? val[E(b) * VW + 1] : (T)0;
             if (cb < c || (cb == c && (w0 < v0 || (w0 == v0 && w1 <= v1)))) break;
             col[E(b + 1)] = cb;
             val[E(b + 1) * VW] = w0;
@@ -240,7 +243,8 @@ __global__ void k_sort_rows(int64_t n_rows, const int64_t *slice_ptr, const int3
     double g = fabs(diag[r]);
     long long bw = 0;
     for (int a = 0; a < d; ++a) {
-        g += VW == 2 ? hypot(val[E(a) * VW], val[E(a) * VW + 1]) : fabs(val[E(a) * VW]);
+        g += VW == 2 ? hypot((double)val[E(a) * VW], (double)val[E(a) * VW + 1])
+                     : fabs((double)val[E(a) * VW]);
         const long long dist = (long long)col[base + (int64_t)a * kSliceRows] - (long long)r;
         bw = max(bw, dist < 0 ? -dist : dist);
     }
@@ -273,6 +277,176 @@ __global__ void k_to_f32(int64_t n, const double *src, float *dst)
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// ---- halo lists of the staged-gather term kernel --------------------------
+// For each block of kHaloRows consecutive rows: the block's own rows (halo
+// positions 0 .. kHaloRows-1, in order), then the distinct other rows its
+// stored entries reference, ascending; and per stored entry the 16-bit
+// position of its column in that list.  Distinct columns are found with an
+// open-addressing set in shared memory (bounded probes) and sorted by a
+// bitonic sort, so the lists do not depend on thread timing.
+constexpr int kHaloHash = 4096;          // set slots per block (load <= 1/2)
+constexpr int kHaloThreads = 256;
+
+__device__ __forceinline__ unsigned halo_slot(int32_t c)
+{
+    return ((unsigned)c * 2654435761u) >> (32 - 12);      // 12 bits: kHaloHash slots
+}
+
+// Collect the distinct external columns of block hb into ext[0 .. *n_ext),
+// sorted.  Sets *overflow when more than kHaloMaxExt are met.
+__device__ void halo_collect(int64_t hb, const int64_t *slice_ptr, const int32_t *col,
+                             int32_t *keys, int32_t *ext, int *n_ext, int *overflow)
+{
+    const int tid = threadIdx.x;
+    for (int k = tid; k < kHaloHash; k += kHaloThreads) keys[k] = -1;
+    if (tid == 0) { *n_ext = 0; *overflow = 0; }
+    __syncthreads();
+    const int64_t r0 = hb * kHaloRows;
+    const int64_t q0 = r0 / kSliceRows, q1 = q0 + kHaloRows / kSliceRows;
+    const int64_t e0 = slice_ptr[q0], e1 = slice_ptr[q1];
+    for (int64_t e = e0 + tid; e < e1; e += kHaloThreads) {
+        const int32_t c = col[e];
+        if (c >= r0 && c < r0 + kHaloRows) continue;       // own rows come first
+        unsigned h = halo_slot(c);
+        for (int probe = 0; probe < kHaloHash; ++probe) {  // bounded: the set has kHaloHash slots
+            const int32_t prev = atomicCAS(&keys[h], -1, c);
+            if (prev == -1) {
+                const int at = atomicAdd(n_ext, 1);
+                if (at < kHaloMaxExt) ext[at] = c; else *overflow = 1;
+                break;
+            }
+            if (prev == c) break;
+            h = (h + 1) & (kHaloHash - 1);
+            if (probe == kHaloHash - 1) *overflow = 1;
+        }
+    }
+    __syncthreads();
+    const int n = min(*n_ext, kHaloMaxExt);
+    int n2 = 32;
+    while (n2 < n) n2 <<= 1;
+    for (int k = n + tid; k < n2; k += kHaloThreads) ext[k] = INT32_MAX;
+    __syncthreads();
+    // bitonic sort of ext[0 .. n2)
+    for (int size = 2; size <= n2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = tid; k < n2 / 2; k += kHaloThreads) {
+                const int lo = 2 * k - (k & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const int32_t x = ext[lo], y = ext[hi];
+                if ((x > y) == up) { ext[lo] = y; ext[hi] = x; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Pass 1: halo size of every block (kHaloRows + distinct external rows), or
+// -1 when the block overflows the set.
+__global__ void __launch_bounds__(kHaloThreads) k_halo_count(const int64_t *slice_ptr,
+                                                             const int32_t *col, int64_t *size)
+{
+    __shared__ int32_t keys[kHaloHash];
+    __shared__ int32_t ext[kHaloMaxExt];
+    __shared__ int n_ext, overflow;
+    halo_collect(blockIdx.x, slice_ptr, col, keys, ext, &n_ext, &overflow);
+    if (threadIdx.x == 0)
+        size[blockIdx.x] = overflow ? -1 : (int64_t)kHaloRows + n_ext;
+}
+
+// Pass 2: the lists (at halo_ptr[hb]) and the per-entry positions.
+__global__ void __launch_bounds__(kHaloThreads) k_halo_fill(const int64_t *slice_ptr,
+                                                            const int32_t *col,
+                                                            const int64_t *halo_ptr,
+                                                            int32_t *halo_rows, uint16_t *lcol)
+{
+    __shared__ int32_t keys[kHaloHash];
+    __shared__ int32_t ext[kHaloMaxExt];
+    __shared__ int n_ext, overflow;
+    const int64_t hb = blockIdx.x;
+    halo_collect(hb, slice_ptr, col, keys, ext, &n_ext, &overflow);
+    const int n = n_ext;
+    const int64_t r0 = hb * kHaloRows;
+    int32_t *out = halo_rows + halo_ptr[hb];
+    for (int k = threadIdx.x; k < kHaloRows + n; k += kHaloThreads)
+        out[k] = k < kHaloRows ? (int32_t)(r0 + k) : ext[k - kHaloRows];
+    const int64_t q0 = r0 / kSliceRows, q1 = q0 + kHaloRows / kSliceRows;
+    const int64_t e0 = slice_ptr[q0], e1 = slice_ptr[q1];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kHaloThreads) {
+        const int32_t c = col[e];
+        int pos;
+        if (c >= r0 && c < r0 + kHaloRows) {
+            pos = (int)(c - r0);
+        } else {
+            int lo = 0, hi = n - 1;                         // ext is sorted and holds c
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ext[mid] < c) lo = mid + 1; else hi = mid;
+            }
+            pos = kHaloRows + lo;
+        }
+        lcol[e] = (uint16_t)pos;
+    }
+}
+
+}  // namespace
+
+int build_halo(BuildOutput &b, cudaStream_t st, std::string &msg)
+{
+    if (b.halo_ptr) return TBPM_OK;
+    if (b.n_rows % kHaloRows) { msg = "rows are not a multiple of the halo block"; return TBPM_E_UNSUPPORTED; }
+    const int64_t nb = b.n_rows / kHaloRows;
+    int64_t *size = nullptr;
+    CK(cudaMalloc(&size, (nb + 1) * sizeof(int64_t)));
+    k_halo_count<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, size);
+    CK(cudaGetLastError());
+    std::vector<int64_t> hs(nb);
+    CK(cudaMemcpyAsync(hs.data(), size, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t mx = 0;
+    for (int64_t k = 0; k < nb; ++k) {
+        if (hs[k] < 0) {
+            cudaFree(size);
+            msg = "a row block references more than " + std::to_string(kHaloMaxExt) +
+                  " other rows: no halo lists for this matrix";
+            return TBPM_E_UNSUPPORTED;
+        }
+        mx = std::max(mx, hs[k]);
+    }
+    int64_t *ptr = nullptr;
+    CK(cudaMalloc(&ptr, (nb + 1) * sizeof(int64_t)));
+    int rc = scan_exclusive(size, ptr, nb, st, msg);
+    cudaFree(size);
+    if (rc) { cudaFree(ptr); return rc; }
+    int64_t total = 0;
+    CK(cudaMemcpyAsync(&total, ptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int32_t *rows = nullptr;
+    uint16_t *lc = nullptr;
+    cudaError_t e = cudaMalloc(&rows, total * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&lc, (b.nnz_pad > 0 ? b.nnz_pad : 1) * sizeof(uint16_t));
+    if (e != cudaSuccess) {
+        cudaFree(ptr); cudaFree(rows); cudaFree(lc);
+        msg = std::string("halo lists: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? TBPM_E_OOM : TBPM_E_CUDA;
+    }
+    k_halo_fill<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, ptr, rows, lc);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(ptr); cudaFree(rows); cudaFree(lc);
+        msg = std::string("halo lists: ") + cudaGetErrorString(e);
+        return TBPM_E_CUDA;
+    }
+    b.halo_ptr = ptr;
+    b.halo_rows = rows;
+    b.lcol = lc;
+    b.halo_max = (int)mx;
+    b.halo_total = total;
+    return TBPM_OK;
+}
+
+namespace {
 }  // namespace
 
 void free_build(BuildOutput &b)
@@ -287,11 +461,14 @@ void free_build(BuildOutput &b)
     cudaFree(b.diag32);
     cudaFree(b.chunk_sample);
     cudaFree(b.bond_rows);
+    cudaFree(b.halo_ptr);
+    cudaFree(b.halo_rows);
+    cudaFree(b.lcol);
     b = BuildOutput();
 }
 
 int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
-               BuildOutput &out, cudaStream_t st, std::string &msg)
+               int keep_bond_map, BuildOutput &out, cudaStream_t st, std::string &msg)
 {
     const int T = 256;
     const int vw = in.cplx ? 2 : 1;      // doubles per stored value
@@ -371,36 +548,43 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
 
     int64_t nnz_alloc = out.nnz_pad > 0 ? out.nnz_pad : 1;
     CK(cudaMalloc(&out.col, nnz_alloc * sizeof(int32_t)));
-    CK(cudaMalloc(&out.val64, nnz_alloc * vw * sizeof(double)));
+    // values go straight to their kept precision: FP64 (and FP32 converted
+    // from it afterwards) or, without the FP64 copy, FP32 only
+    const bool direct32 = !keep64;
+    if (direct32)
+        CK(cudaMalloc(&out.val32, nnz_alloc * vw * sizeof(float)));
+    else
+        CK(cudaMalloc(&out.val64, nnz_alloc * vw * sizeof(double)));
     out.cplx = in.cplx;
     CK(cudaMalloc(&out.diag64, n_rows * sizeof(double)));
     CK(cudaMemsetAsync(out.diag64, 0, n_rows * sizeof(double), st));
-    if (vw == 2)
-        k_pad_fill<2><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, out.val64);
-    else
-        k_pad_fill<1><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, out.val64);
-    CK(cudaGetLastError());
-    if (in.n_hop > 0) {
+    auto fill_all = [&](auto *val) -> cudaError_t {
+        typedef typename std::remove_pointer<decltype(val)>::type VT;
         if (vw == 2)
-            k_fill<2><<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j, in.hop_v,
-                                                             in.inv_s, out.user_to_row,
-                                                             out.slice_ptr, fill, out.col, out.val64);
+            k_pad_fill<2, VT><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, val);
         else
-            k_fill<1><<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j, in.hop_v,
-                                                             in.inv_s, out.user_to_row,
-                                                             out.slice_ptr, fill, out.col, out.val64);
-        CK(cudaGetLastError());
-    }
-    k_diag<<<blocks_for(in.n_orb, T), T, 0, st>>>(in.n_orb, in.onsite, in.inv_s,
-                                                  out.user_to_row, out.diag64);
-    CK(cudaGetLastError());
-    if (vw == 2)
-        k_sort_rows<2><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, deg, out.diag64,
-                                                            out.col, out.val64, gbits, gbits + 1);
-    else
-        k_sort_rows<1><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, deg, out.diag64,
-                                                            out.col, out.val64, gbits, gbits + 1);
-    CK(cudaGetLastError());
+            k_pad_fill<1, VT><<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.slice_ptr, out.col, val);
+        if (in.n_hop > 0) {
+            if (vw == 2)
+                k_fill<2, VT><<<blocks_for(in.n_hop, T), T, 0, st>>>(
+                    in.n_hop, in.hop_i, in.hop_j, in.hop_v, in.inv_s, out.user_to_row,
+                    out.slice_ptr, fill, out.col, val);
+            else
+                k_fill<1, VT><<<blocks_for(in.n_hop, T), T, 0, st>>>(
+                    in.n_hop, in.hop_i, in.hop_j, in.hop_v, in.inv_s, out.user_to_row,
+                    out.slice_ptr, fill, out.col, val);
+        }
+        k_diag<<<blocks_for(in.n_orb, T), T, 0, st>>>(in.n_orb, in.onsite, in.inv_s,
+                                                      out.user_to_row, out.diag64);
+        if (vw == 2)
+            k_sort_rows<2, VT><<<blocks_for(n_rows, T), T, 0, st>>>(
+                n_rows, out.slice_ptr, deg, out.diag64, out.col, val, gbits, gbits + 1);
+        else
+            k_sort_rows<1, VT><<<blocks_for(n_rows, T), T, 0, st>>>(
+                n_rows, out.slice_ptr, deg, out.diag64, out.col, val, gbits, gbits + 1);
+        return cudaGetLastError();
+    };
+    CK(direct32 ? fill_all(out.val32) : fill_all(out.val64));
     unsigned long long hg[2] = {0, 0};
     CK(cudaMemcpyAsync(hg, gbits, sizeof(hg), cudaMemcpyDeviceToHost, st));
 
@@ -429,16 +613,16 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
         out.uniform = same != 0;
         out.h_uniform = v0 * in.inv_s;
     }
-    if (in.n_hop > 0) {      // bond -> rows: the adjoint's gradients, the bond vectors
+    if (in.n_hop > 0 && keep_bond_map) {  // bond -> rows: the adjoint's gradients, the bond vectors
         CK(cudaMalloc(&out.bond_rows, 2 * in.n_hop * sizeof(int32_t)));
         k_bond_rows<<<blocks_for(in.n_hop, T), T, 0, st>>>(in.n_hop, in.hop_i, in.hop_j,
                                                            out.user_to_row, out.bond_rows);
         CK(cudaGetLastError());
     }
     if (keep32) {
-        CK(cudaMalloc(&out.val32, nnz_alloc * vw * sizeof(float)));
+        if (!direct32) CK(cudaMalloc(&out.val32, nnz_alloc * vw * sizeof(float)));
         CK(cudaMalloc(&out.diag32, n_rows * sizeof(float)));
-        if (out.nnz_pad > 0)
+        if (out.nnz_pad > 0 && !direct32)
             k_to_f32<<<blocks_for(out.nnz_pad * vw, T), T, 0, st>>>(out.nnz_pad * vw, out.val64,
                                                                     out.val32);
         k_to_f32<<<blocks_for(n_rows, T), T, 0, st>>>(n_rows, out.diag64, out.diag32);

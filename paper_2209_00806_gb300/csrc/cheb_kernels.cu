@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tbpm_internal.cuh"
 
 namespace tbpm {
@@ -351,33 +353,22 @@ __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 4) : 1) 
 // butterfly (one add per value and level on every lane).
 constexpr int kFinalThreads = 128;
 
-template <typename V, int L, int SPL, bool COMPUTE, bool CX>
-__global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
+// Block reduction of the closing term: block `bid` covers ROWS rows, thread
+// (lrow, l) holds the lane values o of its row and psi0's p0.  Writes the
+// block partial; the chunk's last block adds the chunk's partials in order.
+template <typename V, int L, int SPL, int ROWS>
+__device__ __forceinline__ void final_reduce(const TermArgs &a, int64_t bid, int lrow, int l,
+                                             const Cv<V, SPL> &o, const Cv<V, SPL> &p0)
 {
     constexpr int B = L * SPL;
-    constexpr int ROWS = kFinalThreads / L;          // rows per block
+    constexpr int NT = ROWS * L;                     // threads of the block
     constexpr int NV = B * 3;                        // (re, im, norm) per state
-    constexpr int P = kFinalThreads / NV;            // FP32: parts per value
+    constexpr int P = NT / NV;                       // FP32: parts per value
     __shared__ double red[sizeof(V) == 8 ? ROWS * NV : 1];
     __shared__ FF redf[sizeof(V) == 4 ? ROWS * NV : 1];
     __shared__ FF redp[sizeof(V) == 4 ? P * NV : 1];
     __shared__ double grp[8][NV];
     __shared__ int last;
-    const int64_t bid = block_in_order(a);
-    const int64_t t = bid * kFinalThreads + threadIdx.x;
-    const int64_t r = t / L;
-    const int l = (int)(t % L);
-    const V *sc = Coef<V>::scale(a);
-    if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * B;
-    Cv<V, SPL> o;
-    if (COMPUTE) {
-        o = term_row<V, L, SPL, CX>(a, r, l, sc);
-        st<V, L, SPL>(a.out, r, l, o);
-    } else {
-        o = ld<V, L, SPL>(a.out, r, l);
-    }
-    const Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
-    const int lrow = threadIdx.x / L;
     if constexpr (sizeof(V) == 4) {
         // FP32: exact per-row products as float pairs, [row][value] in shared
         // memory; value v's rows are summed in P fixed parts (rows part,
@@ -405,23 +396,16 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
             grp[0][threadIdx.x] = ff_to_double(acc);
         }
     } else {
-        V pre[SPL], pim[SPL], pnr[SPL];
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-            pre[j] = fma(p0.re[j], o.re[j], p0.im[j] * o.im[j]);
-            pim[j] = fma(p0.re[j], o.im[j], -(p0.im[j] * o.re[j]));
-            pnr[j] = fma(o.re[j], o.re[j], o.im[j] * o.im[j]);
-        }
         // FP64: shared-memory tree, 8 groups of rows then the groups
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
-            const int b = l * SPL + j;
-            red[(lrow * B + b) * 3 + 0] = (double)pre[j];
-            red[(lrow * B + b) * 3 + 1] = (double)pim[j];
-            red[(lrow * B + b) * 3 + 2] = (double)pnr[j];
+            const int v = (l * SPL + j) * 3;
+            red[lrow * NV + v + 0] = fma(p0.re[j], o.re[j], p0.im[j] * o.im[j]);
+            red[lrow * NV + v + 1] = fma(p0.re[j], o.im[j], -(p0.im[j] * o.re[j]));
+            red[lrow * NV + v + 2] = fma(o.re[j], o.re[j], o.im[j] * o.im[j]);
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 8 * NV; idx += kFinalThreads) {
+        for (int idx = threadIdx.x; idx < 8 * NV; idx += NT) {
             const int gidx = idx / NV, v = idx % NV;
             double s = 0.0;
             for (int row = gidx; row < ROWS; row += 8) s += red[row * NV + v];
@@ -439,7 +423,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
     const int64_t chunk = bid / per_chunk;
     if (threadIdx.x == 0) {
         // one writer, one fence, one ticket per block
-        for (int v = 0; v < B * 3; ++v) a.block_partial[bid * (B * 3) + v] = grp[0][v];
+        for (int v = 0; v < NV; ++v) a.block_partial[bid * NV + v] = grp[0][v];
         __threadfence();
         const int ticket = atomicAdd(a.chunk_count + chunk, 1);
         last = (ticket == per_chunk - 1);
@@ -447,15 +431,223 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
     __syncthreads();
     if (last) {
         __threadfence();
-        if (threadIdx.x < B * 3) {
+        if (threadIdx.x < NV) {
             double s = 0.0;
             const int64_t b0 = chunk * per_chunk;
             for (int k = 0; k < per_chunk; ++k)
-                s += __ldcg(a.block_partial + (b0 + k) * (B * 3) + threadIdx.x);
-            a.partial[chunk * (B * 3) + threadIdx.x] = s;
+                s += __ldcg(a.block_partial + (b0 + k) * NV + threadIdx.x);
+            a.partial[chunk * NV + threadIdx.x] = s;
         }
         if (threadIdx.x == 0) a.chunk_count[chunk] = 0;     // ready for the next launch
     }
+}
+
+template <typename V, int L, int SPL, bool COMPUTE, bool CX>
+__global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
+{
+    constexpr int B = L * SPL;
+    const int64_t bid = block_in_order(a);
+    const int64_t t = bid * kFinalThreads + threadIdx.x;
+    const int64_t r = t / L;
+    const int l = (int)(t % L);
+    const V *sc = Coef<V>::scale(a);
+    if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * B;
+    Cv<V, SPL> o;
+    if (COMPUTE) {
+        o = term_row<V, L, SPL, CX>(a, r, l, sc);
+        st<V, L, SPL>(a.out, r, l, o);
+    } else {
+        o = ld<V, L, SPL>(a.out, r, l);
+    }
+    const Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
+    final_reduce<V, L, SPL, kFinalThreads / L>(a, bid, threadIdx.x / L, l, o, p0);
+}
+
+// ---- staged-gather term (TBPM_VARIANT_HALO) --------------------------------
+// A block of kHaloRows rows first copies its halo -- the x lanes of its own
+// rows, then of every other row its entries reference -- into shared memory
+// with 16-byte asynchronous copies, then gathers from that copy by the 16-bit
+// positions lcol: long rows (the twisted bilayer's ~68 entries) then read
+// their neighbours' states from shared memory instead of L1/L2 lines.  The
+// 16-byte chunks of a row are XOR-permuted by the row's position so that
+// rows sharing a 128-byte bank line spread their chunks over all banks.
+// Real values and 32-byte lanes (two chunks per lane); the arithmetic and
+// its order are term_row's, so the states are bit-identical to it.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Chunk permutation of halo row h for C chunks per row (C = 2, 4, 8).
+template <int C> __device__ __forceinline__ int halo_swz(int h)
+{
+    return (h >> (C == 2 ? 2 : C == 4 ? 1 : 0)) & (C - 1);
+}
+
+template <typename V, int L, int SPL>
+__device__ __forceinline__ Cv<V, SPL> ld_halo(const unsigned char *xs, int h, int l)
+{
+    constexpr int C = 2 * L;
+    typedef typename LaneT<V, SPL>::type Lane;
+    const int sw = halo_swz<C>(h);
+    Lane v;
+    typedef typename std::conditional<sizeof(V) == 4, float4, double2>::type Half;
+    Half *hv = reinterpret_cast<Half *>(&v);
+    hv[0] = *reinterpret_cast<const Half *>(xs + (h * C + ((2 * l) ^ sw)) * 16);
+    hv[1] = *reinterpret_cast<const Half *>(xs + (h * C + ((2 * l + 1) ^ sw)) * 16);
+    Cv<V, SPL> o;
+    unpack(v, o);
+    return o;
+}
+
+// 64 registers a thread (1024 resident threads per SM, no spills).
+template <typename V, int L, int SPL, bool FINAL>
+__global__ void __launch_bounds__(kHaloRows * L, 8 / L) k_term_halo(TermArgs a)
+{
+    extern __shared__ __align__(16) unsigned char xs[];
+    constexpr int C = 2 * L;                     // 16-byte chunks per row of x
+    constexpr int NT = kHaloRows * L;
+    const int64_t hb = block_in_order(a);
+    const int tid = threadIdx.x;
+    const int lr = tid / L, l = tid % L;
+    const int64_t r = hb * kHaloRows + lr;
+    // own-row streams first: in flight while the halo arrives
+    Cv<V, SPL> p = ld_ro<V, L, SPL>(a.psi, r, l), zz;
+    if (a.z) {
+        zz = ld<V, L, SPL>(a.z, r, l);
+    } else {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
+    }
+    const V *sc = Coef<V>::scale(a);
+    if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
+    const int64_t h0 = a.halo_ptr[hb];
+    const int H = (int)(a.halo_ptr[hb + 1] - h0);
+    const unsigned char *xg = reinterpret_cast<const unsigned char *>(a.x);
+    for (int idx = tid; idx < H * C; idx += NT) {
+        const int h = idx / C, c = idx % C;
+        const int64_t g = __ldg(a.halo_rows + h0 + h);
+        cp_async16(xs + (h * C + (c ^ halo_swz<C>(h))) * 16, xg + (g * C + c) * 16);
+    }
+    const int64_t q = r / kSliceRows;
+    int64_t base;
+    int w;
+    if (a.fixed_width) {
+        w = a.fixed_width;
+        base = q * (kSliceRows * (int64_t)w);
+    } else {
+        base = __ldg(a.H.slice_ptr + q);
+        w = (int)((__ldg(a.H.slice_ptr + q + 1) - base) / kSliceRows);
+    }
+    const uint16_t *lcp = a.lcol + base + (r % kSliceRows);
+    const V *valp = reinterpret_cast<const V *>(a.H.val) + base + (r % kSliceRows);
+    const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+    cp_async_wait_all();
+    __syncthreads();
+
+    Cv<V, SPL> y = ld_halo<V, L, SPL>(xs, lr, l);
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
+    for (int k = 0; k < w; k += 4) {
+        int hp[4];
+        V h[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int ku = k + u;
+            ok[u] = ku < w;
+            hp[u] = ok[u] ? (int)__ldg(lcp + (int64_t)ku * kSliceRows) : lr;
+            if (a.uniform) {
+                ok[u] = ok[u] && hp[u] != lr;        // padded slots point at the own row
+                h[u] = Coef<V>::hu(a);
+            } else {
+                h[u] = ok[u] ? __ldg(valp + (int64_t)ku * kSliceRows) : (V)0;
+            }
+        }
+        Cv<V, SPL> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_halo<V, L, SPL>(xs, hp[u], l);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
+                    y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                }
+            }
+        }
+    }
+    if (sc) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const V s = sc[l * SPL + j];
+            p.re[j] *= s;
+            p.im[j] *= s;
+            if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
+        }
+    }
+    const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
+    Cv<V, SPL> o;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+        V re = fma(g, y.im[j], zz.re[j]);
+        V im = fma(-g, y.re[j], zz.im[j]);
+        if (sizeof(V) == 4) {
+            re = fma(cl, p.re[j], re);
+            im = fma(cl, p.im[j], im);
+        }
+        o.re[j] = fma(ch, p.re[j], re);
+        o.im[j] = fma(ch, p.im[j], im);
+    }
+    st<V, L, SPL>(a.out, r, l, o);
+    if constexpr (FINAL) {
+        const Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
+        final_reduce<V, L, SPL, kHaloRows>(a, hb, lr, l, o, p0);
+    }
+}
+
+template <typename V, int L, int SPL, bool FINAL>
+cudaError_t launch_halo_t(const TermArgs &a, cudaStream_t st)
+{
+    static int configured = -1;              // dynamic shared bytes already allowed
+    const int smem = a.halo_max * (2 * L) * 16;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_term_halo<V, L, SPL, FINAL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    const unsigned blocks = (unsigned)(a.n_rows / kHaloRows);
+    k_term_halo<V, L, SPL, FINAL><<<blocks, kHaloRows * L, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Interior terms: FP32 groups of 4, 8, 16 states, FP64 of 2, 4, 8; the
+// closing term up to 8 (FP32) / 4 (FP64) states, whose reduction scratch
+// for 128 rows stays within the static shared-memory limit.
+template <bool FINAL>
+cudaError_t dispatch_halo(const TermArgs &a, int fp32, int B, cudaStream_t st)
+{
+    if (!fp32) {
+        switch (B) {
+        case 2: return launch_halo_t<double, 1, 2, FINAL>(a, st);
+        case 4: return launch_halo_t<double, 2, 2, FINAL>(a, st);
+        case 8: if constexpr (!FINAL) return launch_halo_t<double, 4, 2, FINAL>(a, st); break;
+        }
+    } else {
+        switch (B) {
+        case 4: return launch_halo_t<float, 1, 4, FINAL>(a, st);
+        case 8: return launch_halo_t<float, 2, 4, FINAL>(a, st);
+        case 16: if constexpr (!FINAL) return launch_halo_t<float, 4, 4, FINAL>(a, st); break;
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 // Sum of the chunk partials of each sample, spread over kReduceSplit blocks
@@ -735,13 +927,28 @@ cudaError_t dispatch(const TermArgs &a, int fp32, int B, int threads, bool compu
 
 }  // namespace
 
+bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
+{
+    // the shared copy (halo rows x B states) must leave room for the
+    // reduction scratch and a second resident block
+    if ((int64_t)halo_max * B * (fp32 ? 8 : 16) > kHaloSmemMax) return false;
+    if (final_term) return fp32 ? (B == 4 || B == 8) : (B == 2 || B == 4);
+    return fp32 ? (B == 4 || B == 8 || B == 16) : (B == 2 || B == 4 || B == 8);
+}
+
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    if ((a.variant & kVariantHalo) && a.lcol && !a.cplx &&
+        halo_launchable(fp32, B, false, a.halo_max))
+        return dispatch_halo<false>(a, fp32, B, st);
     return dispatch<false>(a, fp32, B, threads, true, st);
 }
 
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    if ((a.variant & kVariantHalo) && a.lcol && !a.cplx && a.H.col &&
+        halo_launchable(fp32, B, true, a.halo_max))
+        return dispatch_halo<true>(a, fp32, B, st);
     return dispatch<true>(a, fp32, B, threads, a.H.col != nullptr, st);
 }
 

@@ -69,6 +69,14 @@ constexpr int kVariantFusedTileShift = 4;  // bits 4-5: fused tile rows x 4^k
 constexpr int kVariantWide = 64;        // term kernel with 32-byte lanes
 constexpr int kVariantSplit2 = 128;     // each row's entries over 2 threads
 constexpr int kVariantSplit4 = 256;     // each row's entries over 4 threads
+constexpr int kVariantHalo = 512;       // gathers from a shared-memory copy of the block's halo
+
+// Staged-gather term kernel: rows per block, and the most other rows one
+// block may reference (16-bit positions; the shared copy is sized by the
+// longest list of the matrix).
+constexpr int kHaloRows = 128;
+constexpr int kHaloMaxExt = 2048;
+constexpr int kHaloSmemMax = 160 * 1024;   // largest shared copy of a halo (bytes)
 
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.
@@ -102,6 +110,11 @@ struct TermArgs {
     int fixed_width;      // slices all this wide: base = 32 q w, no slice_ptr loads
     double h_uniform;
     float h_uniform_f;
+    // staged-gather variant: halo lists and 16-bit column positions
+    const int64_t *halo_ptr;
+    const int32_t *halo_rows;
+    const uint16_t *lcol;
+    int halo_max;
     // closing term only (H.col == nullptr: reduce `out` without computing it)
     const void *psi0;
     double *partial;        // [n_chunks][B][3]
@@ -217,6 +230,9 @@ struct AdjArgs {
 // Kernel launchers (cheb_kernels.cu).  `fp32` selects the value precision,
 // B the states per row (a group).  Return cudaError_t of the launch.
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
+// The staged-gather kernel serves this group width in this precision with
+// halo lists of at most halo_max rows.
+bool halo_launchable(int fp32, int B, bool final_term, int halo_max);
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 // State average of the correlations (and its adjoint, a broadcast of
@@ -321,12 +337,22 @@ struct BuildOutput {
     int uniform = 0;                 // all off-diagonal values are equal
     int cplx = 0;                    // values are complex (re, im) per entry
     double h_uniform = 0.0;          // that value (H~ units)
+    // halo lists of the staged-gather term kernel (built on first use)
+    int64_t *halo_ptr = nullptr;     // [n_rows / kHaloRows + 1]
+    int32_t *halo_rows = nullptr;    // own rows, then the other referenced rows
+    uint16_t *lcol = nullptr;        // [nnz_pad] halo position of each entry's column
+    int halo_max = 0;                // longest list
+    int64_t halo_total = 0;          // entries of all lists
 };
+
+// Halo lists for TBPM_VARIANT_HALO (build_kernels.cu); TBPM_E_UNSUPPORTED
+// when a block references more than kHaloMaxExt other rows.
+int build_halo(BuildOutput &b, cudaStream_t st, std::string &msg);
 
 // Returns TBPM status; fills msg on failure.  Allocations in `out` are owned
 // by the caller afterwards (freed with free_build).
 int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
-               BuildOutput &out, cudaStream_t st, std::string &msg);
+               int keep_bond_map, BuildOutput &out, cudaStream_t st, std::string &msg);
 void free_build(BuildOutput &b);
 
 // Thread-local message returned by tbpm_last_error(NULL) (api.cu).

@@ -87,3 +87,29 @@ def phases(seed: int, n_states: int, n_orb: int) -> np.ndarray:
     for p in range(n_states):
         out[p] = 2.0 * np.pi * uniform(seed, PHASE0 + p, n_orb)
     return out
+
+
+def phases_torch(seed: int, n_states: int, n_orb: int, device="cpu"):
+    """:func:`phases` computed with torch on ``device`` (the same numbers: the
+    mixing runs on int64 with wrap-around products and masked logical shifts)."""
+    import torch
+
+    def s64(v: int) -> int:
+        v &= 0xFFFFFFFFFFFFFFFF
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    def lsr(x, k):
+        return (x >> k) & ((1 << (64 - k)) - 1)
+
+    def mix(x):
+        y = (x ^ lsr(x, 30)) * s64(int(C1))
+        z = (y ^ lsr(y, 27)) * s64(int(C2))
+        return z ^ lsr(z, 31)
+
+    out = torch.empty((n_states, n_orb), dtype=torch.float64, device=device)
+    i1 = torch.arange(1, n_orb + 1, dtype=torch.int64, device=device)
+    for p in range(n_states):
+        k = s64(int(stream_key(seed, PHASE0 + p)))
+        u = mix(i1 * s64(int(GAMMA)) + k)
+        out[p] = lsr(u, 11).to(torch.float64) * (2.0 ** -53) * (2.0 * np.pi)
+    return out

@@ -491,3 +491,70 @@ def test_gpu_state_average_and_its_adjoint(tb):
         lhs = np.sum((g.conj() * x.mean(axis=1)).real)
         rhs = np.sum((gs.conj() * x).real)
         assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+def _tbg_sample(side, order="morton"):
+    from tbpm_inputs import tbg
+    return tbg.to_numpy_sample(tbg.twisted_bilayer(side, order=order))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kind", ["tbg", "random", "graphene"])
+def test_gpu_halo_variant_is_bit_identical(tb, prec, kind):
+    """TBPM_VARIANT_HALO gathers from a shared-memory copy of each 128-row
+    block's halo with the plain kernel's arithmetic: the same states bit for
+    bit (C within rounding of the reduction's block grouping), on every
+    group width it serves, and the oracle's results."""
+    if kind == "tbg":
+        smp, s = _tbg_sample(8.0), 12.0
+    elif kind == "random":
+        smp = lattice.random_graph(3000, 12000, seed=17, onsite_w=2.0)
+        s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(exact.dense_h(smp))))
+    else:
+        smp, s = lattice.graphene(30, 27, pbc=True, seed=8, onsite_w=1.0, vacancy_frac=0.02), 9.5
+    th = rng.phases(91, 16 if prec else 8, smp.n_orb)
+    ref = run_oracle(smp, s, th[:2], 30)
+    tol = 1e-10 if prec == 0 else 2e-5
+    widths = (2, 4, 8) if prec == 0 else (4, 8, 16)
+    for B in widths:
+        c0, _, phi0, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, 65))
+        c1, st, phi1, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, 513))
+        assert np.array_equal(phi0, phi1), B
+        assert np.max(np.abs(c0 - c1)) < 1e-12, B
+        assert np.max(np.abs(c1[0, :2] - ref)) < tol, B
+
+
+def test_gpu_halo_variant_twisted_bilayer_20nm_fp32(tb):
+    """A 20 nm twisted-bilayer flake (Morton numbering, ~45,000 orbitals,
+    ~68 entries per row) with 8 FP32 states: the staged-gather kernel against
+    the plain kernel (bit-identical states) and the oracle (first state)."""
+    smp = _tbg_sample(20.0)
+    th = rng.phases(93, 8, smp.n_orb)
+    c0, _, phi0, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 65))
+    c1, _, phi1, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 513))
+    assert np.array_equal(phi0, phi1)
+    ref = oracle.propagate_rows(smp, 12.0, Z, 12, oracle.phase_states(th[:1]))
+    assert np.max(np.abs(c1[0, 0] - ref[0])) < 2e-5
+
+
+def test_gpu_lean_build_without_fp64_and_bond_map(tb):
+    """TBPM_BUILD_NO_FP64 | TBPM_BUILD_NO_BOND_MAP (the largest samples):
+    FP32 values filled directly give the default build's FP32 results bit
+    for bit; what needs the dropped parts returns TBPM_E_STATE."""
+    N = tb._native
+    smp = lattice.graphene(25, 22, pbc=True, seed=4, onsite_w=1.0, vacancy_frac=0.02)
+    smp.hop_v = smp.hop_v * (1.0 + 0.01 * rng.phases(5, 1, smp.n_hop)[0])   # non-uniform
+    th = rng.phases(94, 4, smp.n_orb)
+    a, _, pa, _ = run_gpu(tb, smp, 9.5, th, 25, precision=1)
+    b, _, pb, _ = run_gpu(tb, smp, 9.5, th, 25, precision=1,
+                          bflags=N.TBPM_BUILD_NO_FP64 | N.TBPM_BUILD_NO_BOND_MAP)
+    assert np.array_equal(pa, pb) and np.array_equal(a, b)
+    with tb.Propagator() as p:
+        p.build_sample(smp, 9.5, flags=N.TBPM_BUILD_NO_FP64 | N.TBPM_BUILD_NO_BOND_MAP)
+        p.set_phase_states(th)
+        with pytest.raises(N.TbpmError) as e:
+            p.propagate(Z, 3, 0)
+        assert e.value.code == N.TBPM_E_STATE
+        with pytest.raises(N.TbpmError) as e:
+            p.set_bond_vectors(np.ones((smp.n_hop, 2)))
+        assert e.value.code == N.TBPM_E_STATE

@@ -135,3 +135,60 @@ def test_graphene_bond_vectors():
     assert np.allclose(np.linalg.norm(per.dr, axis=1), a_cc, rtol=1e-4)
     wrapped = np.linalg.norm(per.pos[per.hop_j] - per.pos[per.hop_i], axis=1) > 2 * a_cc
     assert wrapped.sum() == 6 + 5       # one wrapped bond per edge cell
+
+
+def _pair_keys(smp):
+    a = np.minimum(smp.hop_i, smp.hop_j).astype(np.int64)
+    b = np.maximum(smp.hop_i, smp.hop_j).astype(np.int64)
+    k = a * smp.n_orb + b
+    o = np.argsort(k)
+    return k[o], smp.hop_v[o]
+
+
+@pytest.mark.parametrize("side", [5.0, 13.0])
+def test_tbg_lattice_generator_equals_kd_tree_generator(side):
+    """The lattice-enumeration twisted-bilayer generator (torch, any device)
+    gives the k-d tree generator's sample: same orbitals, same bonds, the
+    same hoppings to rounding; the Morton numbering is a relabelling of it."""
+    pytest.importorskip("torch")
+    from tbpm_inputs import tbg
+    ref = lattice.twisted_bilayer(side)
+    lay = tbg.to_numpy_sample(tbg.twisted_bilayer(side, order="layers", chunk=3000))
+    assert lay.n_orb == ref.n_orb and lay.n_hop == ref.n_hop
+    ka, va = _pair_keys(ref)
+    kb, vb = _pair_keys(lay)
+    assert np.array_equal(ka, kb)
+    assert np.max(np.abs(va - vb)) < 1e-12
+    mor = tbg.to_numpy_sample(tbg.twisted_bilayer(side, order="morton"))
+    assert mor.n_orb == ref.n_orb and mor.n_hop == ref.n_hop
+    # same multiset of (degree, sorted hoppings) per orbital: a relabelling
+    deg_l = np.bincount(np.concatenate([lay.hop_i, lay.hop_j]), minlength=lay.n_orb)
+    deg_m = np.bincount(np.concatenate([mor.hop_i, mor.hop_j]), minlength=mor.n_orb)
+    assert np.array_equal(np.sort(deg_l), np.sort(deg_m))
+    assert np.allclose(np.sort(lay.hop_v), np.sort(mor.hop_v), rtol=0, atol=1e-15)
+    assert np.all(mor.hop_i != mor.hop_j)
+
+
+def test_tbg_morton_numbering_is_local():
+    """Consecutive orbitals of the Morton numbering are neighbours in space: a
+    block of 128 rows references a few hundred distinct rows (its halo),
+    against thousands in the layer-by-layer numbering."""
+    pytest.importorskip("torch")
+    from tbpm_inputs import tbg
+
+    def mean_halo(smp, R=128):
+        i = np.concatenate([smp.hop_i, smp.hop_j])
+        j = np.concatenate([smp.hop_j, smp.hop_i])
+        u = np.unique((i // R) * smp.n_orb + j)
+        return np.bincount(u // smp.n_orb).mean()
+
+    mor = tbg.to_numpy_sample(tbg.twisted_bilayer(30.0, order="morton"))
+    lay = tbg.to_numpy_sample(tbg.twisted_bilayer(30.0, order="layers"))
+    assert mean_halo(mor) < 600 < mean_halo(lay)
+
+
+def test_phases_torch_equals_numpy():
+    pytest.importorskip("torch")
+    a = rng.phases(987654321, 3, 70001)
+    b = rng.phases_torch(987654321, 3, 70001).numpy()
+    assert np.array_equal(a, b)
