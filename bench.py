@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-halo", action="store_true",
                     help="tbg without --autotune: the plain wide-lane kernel instead of the "
                          "staged-gather one")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="tbg: launch variant bits (TBPM_VARIANT_*) instead of the autotuner")
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
@@ -551,7 +553,8 @@ def run_tbg(args):
     M = len(tb.tbpm_bessel_coefficients(z))
     units_per_step = ds.n_orb * S * NT * (M - 1)
     prop = tb.Propagator(local, stream.cuda_stream)
-    variant = N.TBPM_VARIANT_ZIGZAG | (N.TBPM_VARIANT_HALO if not args.no_halo else N.TBPM_VARIANT_WIDE)
+    variant = N.TBPM_VARIANT_ZIGZAG | (N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE
+                                       if not args.no_halo else N.TBPM_VARIANT_WIDE)
     tau = z / s
 
     def build():
@@ -560,7 +563,9 @@ def run_tbg(args):
 
     build()
     st0 = prop.stats()
-    if args.no_autotune:
+    if args.variant is not None or args.no_autotune:
+        if args.variant is not None:
+            variant = args.variant
         prop.launch_config(N.TBPM_FP32, 8, 64, variant)
         tuned = {"group": 8, "threads": 64, "variant": variant}
     else:

@@ -74,6 +74,7 @@ extern "C" {
 #define TBPM_BUILD_COMPLEX_HOPS 32 /* hop_v holds complex hoppings, (re, im) double
                                       pairs (complex128): Peierls phases of a
                                       magnetic field (Sec. 2.1) */
+#define TBPM_BUILD_NO_SPECTRAL_CHECK 256 /* skip the Lanczos check of s (below) */
 #define TBPM_BUILD_NO_BOND_MAP 128 /* keep no bond -> row map (8 bytes per bond):
                                       tbpm_set_bond_vectors and the adjoint then
                                       return TBPM_E_STATE; for the largest samples */
@@ -116,6 +117,8 @@ typedef struct tbpm_stats {
                                 (plus a value unless one value serves all),
                                 the diagonal */
     double max_norm_drift;   /* max over steps and states of |<phi|phi> - 1| */
+    double lanczos_radius;   /* the build's Lanczos estimate of the spectral radius
+                                of H~ (0 when the Gershgorin bound sufficed) */
 } tbpm_stats;
 
 /* Library version, major * 10000 + minor * 100 + patch. */
@@ -164,13 +167,32 @@ const char *tbpm_last_error(const tbpm_ctx *ctx);
  *   flags          TBPM_BUILD_*
  * Replaces any previous Hamiltonian and drops any states.  Runs on the GPU:
  * counting, slice layout (sliced ELLPACK, 32-row slices), fill, per-row
- * column sort (deterministic), Gershgorin bound.  Errors: INVALID_ARG (sizes,
- * indices out of range, i == j, bond across samples), SPECTRAL_BOUND (with
- * TBPM_BUILD_STRICT_BOUND), OOM, CUDA. */
+ * column sort (deterministic), Gershgorin bound.  The expansion of Sec. 2.2
+ * needs the spectrum of H~ inside [-1, 1]: unless the Gershgorin bound
+ * already gives ||H~|| <= 1/1.01 or TBPM_BUILD_NO_SPECTRAL_CHECK is set, 64
+ * Lanczos steps (tbpm_spectral_bounds) estimate the spectral radius rho of H,
+ * and s < 1.01 rho fails with SPECTRAL_BOUND (the estimate is a lower bound;
+ * the margin covers its shortfall).  Errors: INVALID_ARG (sizes, indices out
+ * of range, i == j, bond across samples), SPECTRAL_BOUND (the Lanczos check,
+ * or the Gershgorin bound with TBPM_BUILD_STRICT_BOUND), OOM, CUDA. */
 int tbpm_build_hamiltonian(tbpm_ctx *ctx, int64_t n_orb, const double *onsite,
                            int64_t n_hop, const int64_t *hop_i, const int64_t *hop_j,
                            const double *hop_v, double s, int n_samples,
                            const int64_t *sample_offsets, int where, int flags);
+
+/* Spectral bound of the built H (the rescaling of Sec. 2.2 needs ||H|| <= s):
+ * n_iter (1 .. 10000) Lanczos steps from a fixed start vector -- components
+ * (U_2u - 1/2) + i (U_2u+1 - 1/2) in caller order u, normalised, U_k the
+ * k-th uniform draw (top 53 bits) of the SplitMix64 output function keyed
+ * by seed 220900806 and stream 200 as key = mix(seed + G (stream + 1)),
+ * U_k = mix(key + G (k + 1)), G = 0x9E3779B97F4A7C15 -- each step one sparse
+ * product and deterministic FP64 sums on the GPU; then the extreme
+ * eigenvalues of the Lanczos tridiagonal matrix by bisection on the host.
+ *   e_min, e_max  the extreme Ritz values in eV: inside the spectrum of H,
+ *                 approaching its ends as n_iter grows
+ *   steps         steps taken (fewer when the Krylov space closes), or NULL
+ * Errors: INVALID_ARG, STATE (no Hamiltonian), NONFINITE, OOM, CUDA. */
+int tbpm_spectral_bounds(tbpm_ctx *ctx, int n_iter, double *e_min, double *e_max, int *steps);
 
 /* Initial states (Sec. 2.2, Eq. ini_state).  psi0 is complex128
  * [n_states][n_orb] (host or device); state p of sample k is the slice
@@ -307,6 +329,12 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
                                         halo lists are built on first use; a matrix
                                         with a block referencing over 2048 other rows
                                         keeps the plain kernel */
+#define TBPM_VARIANT_PIPE 1024       /* with TBPM_VARIANT_HALO, interior terms: a
+                                        persistent grid (one block per SM) with two
+                                        shared-memory stages, the next block's halo,
+                                        positions and values copied while the current
+                                        one computes; FP32 groups of 4 or 8, FP64 of 2
+                                        or 4 states, within 224 KB of shared memory */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
 

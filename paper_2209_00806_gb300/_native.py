@@ -44,6 +44,7 @@ TBPM_BUILD_NO_UNIFORM = 16
 TBPM_BUILD_COMPLEX_HOPS = 32
 TBPM_BUILD_REORDER_CLUSTER = 64
 TBPM_BUILD_NO_BOND_MAP = 128
+TBPM_BUILD_NO_SPECTRAL_CHECK = 256
 TBPM_PROP_PROFILE = 1
 TBPM_PROP_GRAPH = 2
 TBPM_PROP_RESUME = 4
@@ -57,6 +58,7 @@ TBPM_VARIANT_WIDE = 64
 TBPM_VARIANT_SPLIT2 = 128
 TBPM_VARIANT_SPLIT4 = 256
 TBPM_VARIANT_HALO = 512
+TBPM_VARIANT_PIPE = 1024
 
 
 class TbpmError(RuntimeError):
@@ -74,7 +76,7 @@ class tbpm_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_term_avg", ctypes.c_double),
                 ("ms_final_avg", ctypes.c_double), ("ms_reduce_avg", ctypes.c_double),
                 ("term_launches", ctypes.c_int64), ("bytes_term", ctypes.c_double),
-                ("max_norm_drift", ctypes.c_double)]
+                ("max_norm_drift", ctypes.c_double), ("lanczos_radius", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +96,8 @@ SIGNATURES = [
     ("tbpm_destroy", None, [P]),
     ("tbpm_last_error", ctypes.c_char_p, [P]),
     ("tbpm_build_hamiltonian", _I32, [P, _I64, P, _I64, P, P, P, _F64, _I32, P, _I32, _I32]),
+    ("tbpm_spectral_bounds", _I32, [P, _I32, ctypes.POINTER(_F64), ctypes.POINTER(_F64),
+                                     ctypes.POINTER(_I32)]),
     ("tbpm_set_states", _I32, [P, _I32, P, _I32]),
     ("tbpm_set_phase_states", _I32, [P, _I32, P, _I32]),
     ("tbpm_bessel_coefficients", _I32, [_F64, _F64, _I32, P, ctypes.POINTER(_I32)]),
@@ -196,6 +200,13 @@ def tbpm_build_hamiltonian(ctx, n_orb, onsite, n_hop, hop_i, hop_j, hop_v, s, n_
     return check(ctx, lib.tbpm_build_hamiltonian(ctx, n_orb, ptr(onsite), n_hop, ptr(hop_i),
                                                  ptr(hop_j), ptr(hop_v), s, n_samples,
                                                  ptr(offs), where, flags))
+
+
+def tbpm_spectral_bounds(ctx, n_iter=64):
+    lo, hi, m = _F64(), _F64(), _I32()
+    check(ctx, lib.tbpm_spectral_bounds(ctx, n_iter, ctypes.byref(lo), ctypes.byref(hi),
+                                        ctypes.byref(m)))
+    return lo.value, hi.value, m.value
 
 
 def tbpm_set_states(ctx, n_states, psi0, where=None):

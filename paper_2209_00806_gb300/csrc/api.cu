@@ -558,6 +558,27 @@ extern "C" int tbpm_build_hamiltonian(tbpm_ctx *c, int64_t n_orb, const double *
         free_hamiltonian(c);
         return fail(c, TBPM_E_SPECTRAL_BOUND, buf);
     }
+    c->stats.lanczos_radius = 0.0;
+    if (!(flags & TBPM_BUILD_NO_SPECTRAL_CHECK) && c->H.gershgorin > 1.0 / 1.01) {
+        // the Gershgorin bound does not clear s: estimate the spectral radius
+        double lo = 0, hi = 0;
+        int steps = 0;
+        std::string msg;
+        rc = lanczos_extremes(c->H, kLanczosSteps, c->st, &lo, &hi, &steps, msg);
+        if (rc) { free_hamiltonian(c); return fail(c, rc, msg); }
+        const double rho = std::max(std::fabs(lo), std::fabs(hi));
+        c->stats.lanczos_radius = rho;
+        if (1.01 * rho > 1.0) {
+            char buf[240];
+            snprintf(buf, sizeof buf,
+                     "s = %.6g eV is below 1.01 x the Lanczos estimate %.6g eV of the spectral "
+                     "radius of H (extreme Ritz values %.6g, %.6g eV): the Chebyshev series "
+                     "would diverge",
+                     s, rho * s, lo * s, hi * s);
+            free_hamiltonian(c);
+            return fail(c, TBPM_E_SPECTRAL_BOUND, buf);
+        }
+    }
     c->err.clear();
     return leave(c);
 }
@@ -602,6 +623,26 @@ static int set_states_common(tbpm_ctx *c, int n_states, const double *src, int w
     return leave(c);
 }
 
+extern "C" int tbpm_spectral_bounds(tbpm_ctx *c, int n_iter, double *e_min, double *e_max,
+                                    int *steps)
+{
+    if (!c || !e_min || !e_max) return fail(c, TBPM_E_INVALID_ARG, "NULL argument");
+    if (!c->have_h) return fail(c, TBPM_E_STATE, "build the Hamiltonian first");
+    if (n_iter < 1 || n_iter > 10000) return fail(c, TBPM_E_INVALID_ARG, "n_iter must be 1..10000");
+    int rc = enter(c);
+    if (rc) return rc;
+    double lo = 0, hi = 0;
+    int m = 0;
+    std::string msg;
+    rc = lanczos_extremes(c->H, n_iter, c->st, &lo, &hi, &m, msg);
+    if (rc) return fail(c, rc, msg);
+    *e_min = lo * c->s;
+    *e_max = hi * c->s;
+    if (steps) *steps = m;
+    c->err.clear();
+    return leave(c);
+}
+
 extern "C" int tbpm_set_states(tbpm_ctx *c, int n_states, const double *psi0, int where)
 {
     return set_states_common(c, n_states, psi0, where, false);
@@ -625,7 +666,7 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
         return fail(c, TBPM_E_INVALID_ARG, "threads must be 64, 128 or 256");
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
                                   (3 << kVariantFusedTileShift) | kVariantWide | kVariantSplit2 |
-                                  kVariantSplit4 | kVariantHalo) ||
+                                  kVariantSplit4 | kVariantHalo | kVariantPipe) ||
         ((variant >> kVariantFusedTileShift) & 3) == 3 ||
         ((variant & kVariantSplit2) && (variant & kVariantSplit4)))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
@@ -984,6 +1025,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             base.halo_rows = c->H.halo_rows;
             base.lcol = c->H.lcol;
             base.halo_max = c->H.halo_max;
+            base.halo_ent_max = c->H.halo_ent_max;
+            base.num_sms = c->num_sms;
         }
         ReduceArgs ra;
         ra.partial = c->d_partial;
@@ -1691,7 +1734,9 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                                 kVariantTma, kVariantTma | kVariantZigZag, kVariantFused,
                                 kVariantFused | (1 << kVariantFusedTileShift),
                                 kVariantFused | (2 << kVariantFusedTileShift),
-                                kVariantHalo, kVariantZigZag | kVariantHalo};
+                                kVariantHalo, kVariantZigZag | kVariantHalo,
+                                kVariantHalo | kVariantPipe,
+                                kVariantZigZag | kVariantHalo | kVariantPipe};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
     for (int B : widths)

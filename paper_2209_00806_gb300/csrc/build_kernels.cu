@@ -344,14 +344,18 @@ __device__ void halo_collect(int64_t hb, const int64_t *slice_ptr, const int32_t
 // Pass 1: halo size of every block (kHaloRows + distinct external rows), or
 // -1 when the block overflows the set.
 __global__ void __launch_bounds__(kHaloThreads) k_halo_count(const int64_t *slice_ptr,
-                                                             const int32_t *col, int64_t *size)
+                                                             const int32_t *col, int64_t *size,
+                                                             int64_t *ent)
 {
     __shared__ int32_t keys[kHaloHash];
     __shared__ int32_t ext[kHaloMaxExt];
     __shared__ int n_ext, overflow;
     halo_collect(blockIdx.x, slice_ptr, col, keys, ext, &n_ext, &overflow);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         size[blockIdx.x] = overflow ? -1 : (int64_t)kHaloRows + n_ext;
+        const int64_t q0 = blockIdx.x * (int64_t)(kHaloRows / kSliceRows);
+        ent[blockIdx.x] = slice_ptr[q0 + kHaloRows / kSliceRows] - slice_ptr[q0];
+    }
 }
 
 // Pass 2: the lists (at halo_ptr[hb]) and the per-entry positions.
@@ -396,13 +400,18 @@ int build_halo(BuildOutput &b, cudaStream_t st, std::string &msg)
     if (b.halo_ptr) return TBPM_OK;
     if (b.n_rows % kHaloRows) { msg = "rows are not a multiple of the halo block"; return TBPM_E_UNSUPPORTED; }
     const int64_t nb = b.n_rows / kHaloRows;
-    int64_t *size = nullptr;
+    int64_t *size = nullptr, *ent = nullptr;
     CK(cudaMalloc(&size, (nb + 1) * sizeof(int64_t)));
-    k_halo_count<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, size);
+    CK(cudaMalloc(&ent, nb * sizeof(int64_t)));
+    k_halo_count<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, size, ent);
     CK(cudaGetLastError());
-    std::vector<int64_t> hs(nb);
+    std::vector<int64_t> hs(nb), he(nb);
     CK(cudaMemcpyAsync(hs.data(), size, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(he.data(), ent, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    cudaFree(ent);
+    int64_t emx = 0;
+    for (int64_t k = 0; k < nb; ++k) emx = std::max(emx, he[k]);
     int64_t mx = 0;
     for (int64_t k = 0; k < nb; ++k) {
         if (hs[k] < 0) {
@@ -442,6 +451,7 @@ int build_halo(BuildOutput &b, cudaStream_t st, std::string &msg)
     b.halo_rows = rows;
     b.lcol = lc;
     b.halo_max = (int)mx;
+    b.halo_ent_max = (int)std::min<int64_t>(emx, INT32_MAX);
     b.halo_total = total;
     return TBPM_OK;
 }
@@ -480,6 +490,7 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
     const int64_t n_slices = n_rows / kSliceRows;
     out.n_rows = n_rows;
     out.n_slices = n_slices;
+    out.n_orb_user = in.n_orb;
 
     CK(cudaMalloc(&out.user_to_row, in.n_orb * sizeof(int32_t)));
     CK(cudaMalloc(&out.orb_sample, in.n_orb * sizeof(int32_t)));

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "tbpm_internal.cuh"
@@ -628,6 +629,207 @@ cudaError_t launch_halo_t(const TermArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ---- pipelined staged-gather term (TBPM_VARIANT_HALO | TBPM_VARIANT_PIPE) ----
+// A persistent grid (one block per SM) walks the 128-row halo blocks; while
+// it computes block i from one shared-memory stage, the 16-byte asynchronous
+// copies of block i+1 fill the other stage: the x lanes of its halo rows,
+// and its 16-bit positions and values, each one contiguous range (the
+// block's four slices).  No global load then sits between an entry and its
+// gather.  Lanes are 16 bytes (two FP32 or one FP64 state), C lanes per row
+// of x; same arithmetic and order as term_row, so the states are
+// bit-identical to the plain kernel.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename V, int C>
+__device__ __forceinline__ Cv<V, 16 / (2 * sizeof(V))> ld_halo16(const unsigned char *xs, int h,
+                                                                  int l)
+{
+    constexpr int SPL = 16 / (2 * sizeof(V));
+    typedef typename LaneT<V, SPL>::type Lane;
+    const Lane v = *reinterpret_cast<const Lane *>(xs + (h * C + (l ^ halo_swz<C>(h))) * 16);
+    Cv<V, SPL> o;
+    unpack(v, o);
+    return o;
+}
+
+struct PipeShape {
+    int halo_bytes;     // halo_max x C x 16
+    int lcol_bytes;     // ent_max x 2, rounded up to 16
+    int val_bytes;      // ent_max x value bytes (0 in the one-value form)
+    int stage_bytes;
+    int n_hb;           // halo blocks
+};
+
+template <typename V, int C>
+__global__ void __launch_bounds__(kHaloRows * C, 1) k_term_halo_pipe(TermArgs a, PipeShape ps)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int SPL = 16 / (2 * sizeof(V));
+    constexpr int NT = kHaloRows * C;
+    const int tid = threadIdx.x;
+    const int lr = tid / C, l = tid % C;
+    const unsigned char *xg = reinterpret_cast<const unsigned char *>(a.x);
+    const int64_t G = gridDim.x;
+    auto block_at = [&](int64_t i) -> int64_t {        // i-th block of this CTA, or -1
+        const int64_t k = blockIdx.x + i * G;
+        if (k >= ps.n_hb) return -1;
+        return a.reverse ? ps.n_hb - 1 - k : k;
+    };
+    auto ent_range = [&](int64_t q, int64_t *e0, int *w) {
+        if (a.fixed_width) {
+            *w = a.fixed_width;
+            *e0 = q * (kSliceRows * (int64_t)a.fixed_width);
+        } else {
+            *e0 = __ldg(a.H.slice_ptr + q);
+            *w = (int)((__ldg(a.H.slice_ptr + q + 1) - *e0) / kSliceRows);
+        }
+    };
+    auto issue = [&](int64_t hb, int s) {
+        unsigned char *stg = sm + (int64_t)s * ps.stage_bytes;
+        const int64_t h0 = a.halo_ptr[hb];
+        const int H = (int)(a.halo_ptr[hb + 1] - h0);
+        for (int idx = tid; idx < H * C; idx += NT) {
+            const int h = idx / C, c = idx % C;
+            const int64_t g = __ldg(a.halo_rows + h0 + h);
+            cp_async16(stg + (h * C + (c ^ halo_swz<C>(h))) * 16, xg + (g * C + c) * 16);
+        }
+        int64_t e0, e1;
+        int w;
+        ent_range(hb * (kHaloRows / kSliceRows), &e0, &w);
+        if (a.fixed_width) e1 = e0 + (int64_t)kHaloRows * w;
+        else e1 = __ldg(a.H.slice_ptr + (hb + 1) * (kHaloRows / kSliceRows));
+        const int E = (int)(e1 - e0);                    // a multiple of 32
+        unsigned char *lc = stg + ps.halo_bytes;
+        for (int idx = tid; idx < E / 8; idx += NT)
+            cp_async16(lc + idx * 16, a.lcol + e0 + idx * 8);
+        if (!a.uniform) {
+            constexpr int per = 16 / sizeof(V);
+            unsigned char *vs = lc + ps.lcol_bytes;
+            for (int idx = tid; idx < E / per; idx += NT)
+                cp_async16(vs + idx * 16, reinterpret_cast<const V *>(a.H.val) + e0 + idx * per);
+        }
+        cp_async_commit();
+    };
+
+    int64_t hb = block_at(0);
+    if (hb >= 0) issue(hb, 0);
+    for (int64_t i = 0; hb >= 0; ++i) {
+        const int64_t nxt = block_at(i + 1);
+        if (nxt >= 0) issue(nxt, (int)((i + 1) & 1));
+        else cp_async_commit();                          // an empty group keeps the count
+        // own-row streams of block i, in flight while its stage lands
+        const int64_t r = hb * kHaloRows + lr;
+        Cv<V, SPL> p = ld_ro<V, C, SPL>(a.psi, r, l), zz;
+        if (a.z) {
+            zz = ld<V, C, SPL>(a.z, r, l);
+        } else {
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
+        }
+        const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+        int64_t eb, eq;
+        int wb, w;
+        ent_range(hb * (kHaloRows / kSliceRows), &eb, &wb);
+        ent_range(r / kSliceRows, &eq, &w);
+        cp_async_wait_group<1>();
+        __syncthreads();
+        const unsigned char *stg = sm + (int64_t)(i & 1) * ps.stage_bytes;
+        const uint16_t *lcs = reinterpret_cast<const uint16_t *>(stg + ps.halo_bytes) + (eq - eb) +
+                              (r % kSliceRows);
+        const V *vs = reinterpret_cast<const V *>(stg + ps.halo_bytes + ps.lcol_bytes) + (eq - eb) +
+                      (r % kSliceRows);
+        Cv<V, SPL> y = ld_halo16<V, C>(stg, lr, l);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
+        for (int k = 0; k < w; k += 4) {
+            int hp[4];
+            V h[4];
+            bool ok[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ku = k + u;
+                ok[u] = ku < w;
+                hp[u] = ok[u] ? (int)lcs[ku * kSliceRows] : lr;
+                if (a.uniform) {
+                    ok[u] = ok[u] && hp[u] != lr;
+                    h[u] = Coef<V>::hu(a);
+                } else {
+                    h[u] = ok[u] ? vs[ku * kSliceRows] : (V)0;
+                }
+            }
+            Cv<V, SPL> xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(stg, hp[u], l);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (ok[u]) {
+#pragma unroll
+                    for (int j = 0; j < SPL; ++j) {
+                        y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
+                        y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                    }
+                }
+            }
+        }
+        const V *sc = Coef<V>::scale(a);
+        if (sc) {
+            sc += (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL);
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                const V s = sc[l * SPL + j];
+                p.re[j] *= s;
+                p.im[j] *= s;
+                if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
+            }
+        }
+        const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
+        Cv<V, SPL> o;
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            V re = fma(g, y.im[j], zz.re[j]);
+            V im = fma(-g, y.re[j], zz.im[j]);
+            if (sizeof(V) == 4) {
+                re = fma(cl, p.re[j], re);
+                im = fma(cl, p.im[j], im);
+            }
+            o.re[j] = fma(ch, p.re[j], re);
+            o.im[j] = fma(ch, p.im[j], im);
+        }
+        st<V, C, SPL>(a.out, r, l, o);
+        __syncthreads();                                 // stage i & 1 may be refilled now
+        hb = nxt;
+    }
+    cp_async_wait_group<0>();
+}
+
+int g_pipe_configured[2][2] = {{-1, -1}, {-1, -1}};   // dynamic shared bytes allowed, [fp32][C/4]
+
+template <typename V, int C>
+cudaError_t launch_pipe_t(const TermArgs &a, int num_sms, cudaStream_t st)
+{
+    PipeShape ps;
+    ps.halo_bytes = a.halo_max * C * 16;
+    ps.lcol_bytes = (a.halo_ent_max * 2 + 15) / 16 * 16;
+    ps.val_bytes = a.uniform ? 0 : a.halo_ent_max * (int)sizeof(V);
+    ps.stage_bytes = ps.halo_bytes + ps.lcol_bytes + ps.val_bytes;
+    ps.n_hb = (int)(a.n_rows / kHaloRows);
+    const int smem = 2 * ps.stage_bytes;
+    int &conf = g_pipe_configured[sizeof(V) == 4][C / 4];
+    if (smem > conf) {
+        cudaError_t e = cudaFuncSetAttribute(k_term_halo_pipe<V, C>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        conf = smem;
+    }
+    const int grid = std::min<int64_t>(num_sms, ps.n_hb);
+    k_term_halo_pipe<V, C><<<grid, kHaloRows * C, smem, st>>>(a, ps);
+    return cudaGetLastError();
+}
+
 // Interior terms: FP32 groups of 4, 8, 16 states, FP64 of 2, 4, 8; the
 // closing term up to 8 (FP32) / 4 (FP64) states, whose reduction scratch
 // for 128 rows stays within the static shared-memory limit.
@@ -927,6 +1129,19 @@ cudaError_t dispatch(const TermArgs &a, int fp32, int B, int threads, bool compu
 
 }  // namespace
 
+int pipe_smem_bytes(int fp32, int B, int halo_max, int ent_max, int uniform)
+{
+    const int C = B * (fp32 ? 8 : 16) / 16;
+    return 2 * (halo_max * C * 16 + (ent_max * 2 + 15) / 16 * 16 +
+                (uniform ? 0 : ent_max * (fp32 ? 4 : 8)));
+}
+
+bool pipe_launchable(int fp32, int B, int halo_max, int ent_max, int uniform)
+{
+    const bool shape = fp32 ? (B == 4 || B == 8) : (B == 2 || B == 4);
+    return shape && pipe_smem_bytes(fp32, B, halo_max, ent_max, uniform) <= kPipeSmemMax;
+}
+
 bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 {
     // the shared copy (halo rows x B states) must leave room for the
@@ -938,6 +1153,13 @@ bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
+        pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
+        if (fp32) return B == 4 ? launch_pipe_t<float, 2>(a, a.num_sms, st)
+                                : launch_pipe_t<float, 4>(a, a.num_sms, st);
+        return B == 2 ? launch_pipe_t<double, 2>(a, a.num_sms, st)
+                      : launch_pipe_t<double, 4>(a, a.num_sms, st);
+    }
     if ((a.variant & kVariantHalo) && a.lcol && !a.cplx &&
         halo_launchable(fp32, B, false, a.halo_max))
         return dispatch_halo<false>(a, fp32, B, st);

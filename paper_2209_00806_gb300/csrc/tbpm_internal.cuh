@@ -70,6 +70,7 @@ constexpr int kVariantWide = 64;        // term kernel with 32-byte lanes
 constexpr int kVariantSplit2 = 128;     // each row's entries over 2 threads
 constexpr int kVariantSplit4 = 256;     // each row's entries over 4 threads
 constexpr int kVariantHalo = 512;       // gathers from a shared-memory copy of the block's halo
+constexpr int kVariantPipe = 1024;      // with kVariantHalo: persistent, two stages in flight
 
 // Staged-gather term kernel: rows per block, and the most other rows one
 // block may reference (16-bit positions; the shared copy is sized by the
@@ -77,6 +78,7 @@ constexpr int kVariantHalo = 512;       // gathers from a shared-memory copy of 
 constexpr int kHaloRows = 128;
 constexpr int kHaloMaxExt = 2048;
 constexpr int kHaloSmemMax = 160 * 1024;   // largest shared copy of a halo (bytes)
+constexpr int kPipeSmemMax = 224 * 1024;   // two stages of the pipelined form (bytes)
 
 // Device-side sliced-ELLPACK matrix of H~ (off-diagonal part) plus its
 // diagonal, one copy per value precision.
@@ -115,6 +117,8 @@ struct TermArgs {
     const int32_t *halo_rows;
     const uint16_t *lcol;
     int halo_max;
+    int halo_ent_max;     // most stored entries of one halo block (pipelined form)
+    int num_sms;          // grid of the persistent pipelined form
     // closing term only (H.col == nullptr: reduce `out` without computing it)
     const void *psi0;
     double *partial;        // [n_chunks][B][3]
@@ -233,6 +237,8 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
 // The staged-gather kernel serves this group width in this precision with
 // halo lists of at most halo_max rows.
 bool halo_launchable(int fp32, int B, bool final_term, int halo_max);
+// The pipelined form serves this shape within the shared-memory budget.
+bool pipe_launchable(int fp32, int B, int halo_max, int ent_max, int uniform);
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 // State average of the correlations (and its adjoint, a broadcast of
@@ -319,6 +325,7 @@ struct BuildInput {
 
 struct BuildOutput {
     int64_t n_rows = 0, n_slices = 0, nnz_pad = 0, nnz_true = 0;
+    int64_t n_orb_user = 0;          // caller orbitals (n_rows counts padding too)
     int32_t *user_to_row = nullptr;  // [n_orb]
     int32_t *orb_sample = nullptr;   // [n_orb]
     int64_t *slice_ptr = nullptr;    // [n_slices + 1]
@@ -342,8 +349,19 @@ struct BuildOutput {
     int32_t *halo_rows = nullptr;    // own rows, then the other referenced rows
     uint16_t *lcol = nullptr;        // [nnz_pad] halo position of each entry's column
     int halo_max = 0;                // longest list
+    int halo_ent_max = 0;            // most stored entries of one block
     int64_t halo_total = 0;          // entries of all lists
 };
+
+// Lanczos estimate of the extreme eigenvalues of H~ (lanczos.cu): n_iter
+// steps from the SplitMix64 start vector of (kLanczosSeed, kLanczosStream);
+// lo, hi are the extreme Ritz values (inside the spectrum), steps the
+// steps taken (fewer at an invariant subspace).
+constexpr uint64_t kLanczosSeed = 220900806ull;
+constexpr int kLanczosStream = 200;
+constexpr int kLanczosSteps = 64;          // the build's check
+int lanczos_extremes(const BuildOutput &H, int n_iter, cudaStream_t st, double *lo, double *hi,
+                     int *steps, std::string &msg);
 
 // Halo lists for TBPM_VARIANT_HALO (build_kernels.cu); TBPM_E_UNSUPPORTED
 // when a block references more than kHaloMaxExt other rows.

@@ -58,7 +58,7 @@ def test_gpu_fp64_disordered_vacancies_several_groups(tb):
 def test_gpu_fp64_ragged_rows_launch_shapes(tb, cfg):
     smp = lattice.random_graph(3001, 9000, seed=3, onsite_w=2.0)   # degrees 0 .. ~15
     H = exact.dense_h(smp)
-    s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(H)))
+    s = 1.02 * np.max(np.abs(np.linalg.eigvalsh(H)))
     th = rng.phases(4, 5, smp.n_orb)
     c, st, _, _ = run_gpu(tb, smp, s, th, 60, cfg=cfg)
     ref = run_oracle(smp, s, th, 60)
@@ -100,7 +100,7 @@ def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
 def test_gpu_fp32_launch_shapes(tb, cfg):
     smp = lattice.random_graph(2500, 7000, seed=9, onsite_w=2.0)
     H = exact.dense_h(smp)
-    s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(H)))
+    s = 1.02 * np.max(np.abs(np.linalg.eigvalsh(H)))
     th = rng.phases(8, 16, smp.n_orb)
     c, st, _, _ = run_gpu(tb, smp, s, th, 40, precision=1, cfg=cfg)
     ref = run_oracle(smp, s, th, 40)
@@ -242,7 +242,7 @@ def test_gpu_fused_step(tb, prec, kind):
         s, S, parts = 9.5, 7, None
     elif kind == "random":
         smp = lattice.random_graph(6000, 15000, seed=12, onsite_w=2.0)   # bandwidth ~ n
-        s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(exact.dense_h(smp))))
+        s = 1.02 * np.max(np.abs(np.linalg.eigvalsh(exact.dense_h(smp))))
         S, parts = 3, None
     else:
         parts = [lattice.graphene(L, L, pbc=True, seed=30 + L, onsite_w=0.5) for L in (7, 30, 12)]
@@ -309,8 +309,12 @@ def test_gpu_errors_are_statuses(tb):
     with pytest.raises(N.TbpmError) as e:
         p.build_sample(smp, 5.0, flags=N.TBPM_BUILD_STRICT_BOUND)
     assert e.value.code == N.TBPM_E_SPECTRAL_BOUND
-    # s well below the spectral radius: the Chebyshev series diverges
-    p.build_sample(smp, 3.0)
+    # s well below the spectral radius: the build's Lanczos check refuses it ...
+    with pytest.raises(N.TbpmError) as e:
+        p.build_sample(smp, 3.0)
+    assert e.value.code == N.TBPM_E_SPECTRAL_BOUND and "Lanczos" in str(e.value)
+    # ... and without the check the Chebyshev series diverges
+    p.build_sample(smp, 3.0, flags=N.TBPM_BUILD_NO_SPECTRAL_CHECK)
     p.set_phase_states(rng.phases(1, 1, smp.n_orb))
     with pytest.raises(N.TbpmError) as e:
         p.propagate(Z, 40)
@@ -509,7 +513,7 @@ def test_gpu_halo_variant_is_bit_identical(tb, prec, kind):
         smp, s = _tbg_sample(8.0), 12.0
     elif kind == "random":
         smp = lattice.random_graph(3000, 12000, seed=17, onsite_w=2.0)
-        s = 1.01 * np.max(np.abs(np.linalg.eigvalsh(exact.dense_h(smp))))
+        s = 1.02 * np.max(np.abs(np.linalg.eigvalsh(exact.dense_h(smp))))
     else:
         smp, s = lattice.graphene(30, 27, pbc=True, seed=8, onsite_w=1.0, vacancy_frac=0.02), 9.5
     th = rng.phases(91, 16 if prec else 8, smp.n_orb)
@@ -518,10 +522,11 @@ def test_gpu_halo_variant_is_bit_identical(tb, prec, kind):
     widths = (2, 4, 8) if prec == 0 else (4, 8, 16)
     for B in widths:
         c0, _, phi0, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, 65))
-        c1, st, phi1, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, 513))
-        assert np.array_equal(phi0, phi1), B
-        assert np.max(np.abs(c0 - c1)) < 1e-12, B
-        assert np.max(np.abs(c1[0, :2] - ref)) < tol, B
+        for variant in (513, 1537):         # halo; halo + pipelined persistent, zig-zag
+            c1, st, phi1, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, variant))
+            assert np.array_equal(phi0, phi1), (B, variant)
+            assert np.max(np.abs(c0 - c1)) < 1e-12, (B, variant)
+            assert np.max(np.abs(c1[0, :2] - ref)) < tol, (B, variant)
 
 
 def test_gpu_halo_variant_twisted_bilayer_20nm_fp32(tb):
@@ -531,10 +536,11 @@ def test_gpu_halo_variant_twisted_bilayer_20nm_fp32(tb):
     smp = _tbg_sample(20.0)
     th = rng.phases(93, 8, smp.n_orb)
     c0, _, phi0, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 65))
-    c1, _, phi1, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 513))
-    assert np.array_equal(phi0, phi1)
     ref = oracle.propagate_rows(smp, 12.0, Z, 12, oracle.phase_states(th[:1]))
-    assert np.max(np.abs(c1[0, 0] - ref[0])) < 2e-5
+    for variant in (513, 1536):
+        c1, _, phi1, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, variant))
+        assert np.array_equal(phi0, phi1), variant
+        assert np.max(np.abs(c1[0, 0] - ref[0])) < 2e-5, variant
 
 
 def test_gpu_lean_build_without_fp64_and_bond_map(tb):
@@ -558,3 +564,52 @@ def test_gpu_lean_build_without_fp64_and_bond_map(tb):
         with pytest.raises(N.TbpmError) as e:
             p.set_bond_vectors(np.ones((smp.n_hop, 2)))
         assert e.value.code == N.TBPM_E_STATE
+
+
+@pytest.mark.parametrize("kind", ["graphene", "random", "field", "fp32_only"])
+def test_gpu_spectral_bounds_match_the_oracle(tb, kind):
+    """tbpm_spectral_bounds: the Lanczos extremes of the oracle's process from
+    the same SplitMix64 start vector, in caller order (RCM rows inside)."""
+    from oracle import lanczos
+    N = tb._native
+    flags, tol = 0, 1e-9
+    if kind == "graphene":
+        smp = lattice.graphene(40, 36, pbc=True, seed=2, onsite_w=1.0, vacancy_frac=0.02)
+        flags = N.TBPM_BUILD_REORDER_RCM
+    elif kind == "random":
+        smp = lattice.random_graph(2000, 7000, seed=3, onsite_w=2.0)
+    elif kind == "field":
+        smp = lattice.peierls(lattice.graphene(30, 28, pbc=False, seed=5, onsite_w=0.5,
+                                               with_pos=True), 200.0)
+    else:
+        smp = lattice.graphene(30, 30, pbc=True, seed=9, onsite_w=1.0)
+        flags, tol = N.TBPM_BUILD_NO_FP64, 1e-6
+    with tb.Propagator() as p:
+        p.build_sample(smp, 20.0, flags=flags)
+        lo, hi, m = N.tbpm_spectral_bounds(p.ctx, 64)
+    rlo, rhi, rm = lanczos.extremes(smp, 64)
+    assert m == rm
+    scale = max(abs(rlo), abs(rhi))
+    assert abs(lo - rlo) < tol * scale and abs(hi - rhi) < tol * scale
+
+
+def test_gpu_build_refuses_s_below_the_lanczos_radius(tb):
+    """The 5 nm twisted-bilayer flake (spectrum [-11.64, 6.92] eV by exact
+    diagonalisation): s = 10 eV is refused, s = 12 eV accepted; pristine
+    graphene (edges +-8.1 eV): s = 7.9 refused, s = 8.3 accepted."""
+    N = tb._native
+    tbg = workloads.twisted_bilayer_flake(side_nm=5.0).sample
+    ev = np.linalg.eigvalsh(exact.dense_h(tbg))
+    assert 11.6 < -ev[0] < 11.7
+    gr = lattice.graphene(20, 20, pbc=True)
+    with tb.Propagator() as p:
+        for smp, s_bad, s_ok in ((tbg, 10.0, 12.0), (gr, 7.9, 8.3)):
+            with pytest.raises(N.TbpmError) as e:
+                p.build_sample(smp, s_bad)
+            assert e.value.code == N.TBPM_E_SPECTRAL_BOUND
+            p.build_sample(smp, s_ok)
+            p.set_phase_states(rng.phases(4, 1, smp.n_orb))
+            c = p.propagate(Z, 20, 0)
+            assert abs(p.norms()[0, 0, -1] - 1) < 1e-12
+        st = p.stats()
+    assert st["lanczos_radius"] == 0.0 or st["lanczos_radius"] < 1 / 1.01
