@@ -494,15 +494,20 @@ def run_gb300(args):
             en, d32 = r0["res"]
             _, d64 = r64["res"]
             # the FP64 term is bound by GB300's FP64 pipe: 10 flops per lane-row
-            # (diagonal 2, combine 8) plus 4 per stored entry
+            # (diagonal 2, combine 8) plus 4 per stored entry; the peak is the
+            # FP64 FMA rate measured here by the library's probe
             st64 = r64["stats"]
             flops = float(smp.n_orb * S * 10 + st64["nnz_true"] * S * 4)
             alu = None
             if r64["ms_term"]:
                 ach = flops / (r64["ms_term"] * 1e-3) / 1e9
-                alu = {"bound": "alu", "achieved": ach, "peak": 1250.0, "unit": "GFLOP/s",
-                       "frac": ach / 1250.0, "traffic": None,
-                       "peak_source": "nominal FP64 FMA rate of GB300 (1.25 TFLOP/s)",
+                with ClockSampler(local) as pclk:
+                    tf, pms = N.tbpm_fp64_fma_rate(local, 400000)
+                peak = tf * 1e3
+                alu = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
+                       "frac": ach / peak, "traffic": None,
+                       "peak_source": f"measured: FP64 FMA probe (tbpm_fp64_fma_rate, "
+                                      f"{pms:.0f} ms, SM clock {pclk.summary().get('sm_mhz')} MHz)",
                        "flops_per_launch": flops}
             line["fp64_form"] = {"value": vals[N.TBPM_FP64], "ms_per_step": r64["ms"] / args.steps,
                                  "dtype": "f64", "roofline": roofline(r64, "fp64"),
@@ -553,8 +558,8 @@ def run_tbg(args):
     M = len(tb.tbpm_bessel_coefficients(z))
     units_per_step = ds.n_orb * S * NT * (M - 1)
     prop = tb.Propagator(local, stream.cuda_stream)
-    variant = N.TBPM_VARIANT_ZIGZAG | (N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE
-                                       if not args.no_halo else N.TBPM_VARIANT_WIDE)
+    variant = N.TBPM_VARIANT_ZIGZAG | N.TBPM_VARIANT_SPLIT2 | (
+        N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE if not args.no_halo else N.TBPM_VARIANT_WIDE)
     tau = z / s
 
     def build():

@@ -131,6 +131,14 @@ int tbpm_version(void);
  * it); the message is read with tbpm_last_error(NULL). */
 int tbpm_kernel_binary_version(int *version);
 
+/* FP64 fused multiply-add throughput of `device` in TFLOP/s (2 flops per
+ * FMA): a grid of 8 blocks x 256 threads per SM, each thread running 8
+ * independent FMA chains for n_iter rounds, timed with CUDA events (*ms, may
+ * be NULL).  A measurement, not part of the method: the FP64 form's term
+ * kernel is bound by this rate on GB300, and the benchmark reports against
+ * it.  Errors: INVALID_ARG, CUDA (message via tbpm_last_error(NULL)). */
+int tbpm_fp64_fma_rate(int device, int n_iter, double *tflops, double *ms);
+
 /* Create a context on CUDA device `device`.  `cuda_stream` (a cudaStream_t,
  * may be NULL for the legacy default stream) is borrowed: the library orders
  * its work after what is already queued there and makes the stream wait for

@@ -105,6 +105,7 @@ SIGNATURES = [
     ("tbpm_correlation", _I32, [P, P, _I32]),
     ("tbpm_correlation_adjoint", _I32, [P, _I32, P, _I32, P, _I32]),
     ("tbpm_kernel_binary_version", _I32, [ctypes.POINTER(_I32)]),
+    ("tbpm_fp64_fma_rate", _I32, [_I32, _I32, ctypes.POINTER(_F64), ctypes.POINTER(_F64)]),
     ("tbpm_get_states", _I32, [P, P, _I32]),
     ("tbpm_get_norms", _I32, [P, P]),
     ("tbpm_dos", _I32, [P, _I32, _F64, _I32, _F64, _F64, _I32, P, P]),
@@ -251,6 +252,12 @@ def tbpm_kernel_binary_version() -> int:
     v = _I32()
     check(None, lib.tbpm_kernel_binary_version(ctypes.byref(v)))
     return v.value
+
+
+def tbpm_fp64_fma_rate(device=0, n_iter=200000):
+    t, ms = _F64(), _F64()
+    check(None, lib.tbpm_fp64_fma_rate(device, n_iter, ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def tbpm_get_states(ctx, out, where_out=None):

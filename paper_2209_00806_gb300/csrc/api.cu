@@ -1736,7 +1736,8 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                                 kVariantFused | (2 << kVariantFusedTileShift),
                                 kVariantHalo, kVariantZigZag | kVariantHalo,
                                 kVariantHalo | kVariantPipe,
-                                kVariantZigZag | kVariantHalo | kVariantPipe};
+                                kVariantZigZag | kVariantHalo | kVariantPipe,
+                                kVariantZigZag | kVariantHalo | kVariantPipe | kVariantSplit2};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
     for (int B : widths)

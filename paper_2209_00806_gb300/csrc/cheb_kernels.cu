@@ -664,14 +664,16 @@ struct PipeShape {
     int n_hb;           // halo blocks
 };
 
-template <typename V, int C>
-__global__ void __launch_bounds__(kHaloRows * C, 1) k_term_halo_pipe(TermArgs a, PipeShape ps)
+// RS threads share a row (entries part, part + RS, ... as in term_row's
+// row split, so the states equal the plain split kernel's bit for bit).
+template <typename V, int C, int RS>
+__global__ void __launch_bounds__(kHaloRows * C * RS, 1) k_term_halo_pipe(TermArgs a, PipeShape ps)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     constexpr int SPL = 16 / (2 * sizeof(V));
-    constexpr int NT = kHaloRows * C;
+    constexpr int NT = kHaloRows * C * RS;
     const int tid = threadIdx.x;
-    const int lr = tid / C, l = tid % C;
+    const int l = tid % C, part = (tid / C) % RS, lr = tid / (C * RS);
     const unsigned char *xg = reinterpret_cast<const unsigned char *>(a.x);
     const int64_t G = gridDim.x;
     auto block_at = [&](int64_t i) -> int64_t {        // i-th block of this CTA, or -1
@@ -723,14 +725,16 @@ __global__ void __launch_bounds__(kHaloRows * C, 1) k_term_halo_pipe(TermArgs a,
         else cp_async_commit();                          // an empty group keeps the count
         // own-row streams of block i, in flight while its stage lands
         const int64_t r = hb * kHaloRows + lr;
-        Cv<V, SPL> p = ld_ro<V, C, SPL>(a.psi, r, l), zz;
-        if (a.z) {
-            zz = ld<V, C, SPL>(a.z, r, l);
-        } else {
+        Cv<V, SPL> p, zz;
+        if (part == 0) {
+            p = ld_ro<V, C, SPL>(a.psi, r, l);
+            if (a.z) zz = ld<V, C, SPL>(a.z, r, l);
+        }
+        if (part != 0 || !a.z) {
 #pragma unroll
             for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
         }
-        const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+        const V d = part == 0 ? __ldg(reinterpret_cast<const V *>(a.H.diag) + r) : (V)0;
         int64_t eb, eq;
         int wb, w;
         ent_range(hb * (kHaloRows / kSliceRows), &eb, &wb);
@@ -745,13 +749,13 @@ __global__ void __launch_bounds__(kHaloRows * C, 1) k_term_halo_pipe(TermArgs a,
         Cv<V, SPL> y = ld_halo16<V, C>(stg, lr, l);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
-        for (int k = 0; k < w; k += 4) {
+        for (int k = part; k < w; k += 4 * RS) {
             int hp[4];
             V h[4];
             bool ok[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int ku = k + u;
+                const int ku = k + u * RS;
                 ok[u] = ku < w;
                 hp[u] = ok[u] ? (int)lcs[ku * kSliceRows] : lr;
                 if (a.uniform) {
@@ -775,40 +779,51 @@ __global__ void __launch_bounds__(kHaloRows * C, 1) k_term_halo_pipe(TermArgs a,
                 }
             }
         }
-        const V *sc = Coef<V>::scale(a);
-        if (sc) {
-            sc += (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL);
+        if (RS > 1) {           // add the row's parts (lanes C apart in the warp)
+#pragma unroll
+            for (int o = C; o < C * RS; o <<= 1)
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    y.re[j] += __shfl_xor_sync(0xffffffffu, y.re[j], o);
+                    y.im[j] += __shfl_xor_sync(0xffffffffu, y.im[j], o);
+                }
+        }
+        if (part == 0) {
+            const V *sc = Coef<V>::scale(a);
+            if (sc) {
+                sc += (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL);
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    const V s = sc[l * SPL + j];
+                    p.re[j] *= s;
+                    p.im[j] *= s;
+                    if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
+                }
+            }
+            const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
+            Cv<V, SPL> o;
 #pragma unroll
             for (int j = 0; j < SPL; ++j) {
-                const V s = sc[l * SPL + j];
-                p.re[j] *= s;
-                p.im[j] *= s;
-                if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
+                V re = fma(g, y.im[j], zz.re[j]);
+                V im = fma(-g, y.re[j], zz.im[j]);
+                if (sizeof(V) == 4) {
+                    re = fma(cl, p.re[j], re);
+                    im = fma(cl, p.im[j], im);
+                }
+                o.re[j] = fma(ch, p.re[j], re);
+                o.im[j] = fma(ch, p.im[j], im);
             }
+            st<V, C, SPL>(a.out, r, l, o);
         }
-        const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
-        Cv<V, SPL> o;
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-            V re = fma(g, y.im[j], zz.re[j]);
-            V im = fma(-g, y.re[j], zz.im[j]);
-            if (sizeof(V) == 4) {
-                re = fma(cl, p.re[j], re);
-                im = fma(cl, p.im[j], im);
-            }
-            o.re[j] = fma(ch, p.re[j], re);
-            o.im[j] = fma(ch, p.im[j], im);
-        }
-        st<V, C, SPL>(a.out, r, l, o);
         __syncthreads();                                 // stage i & 1 may be refilled now
         hb = nxt;
     }
     cp_async_wait_group<0>();
 }
 
-int g_pipe_configured[2][2] = {{-1, -1}, {-1, -1}};   // dynamic shared bytes allowed, [fp32][C/4]
+int g_pipe_configured[2][2][2] = {};   // dynamic shared bytes allowed, [fp32][C/4][RS-1]
 
-template <typename V, int C>
+template <typename V, int C, int RS>
 cudaError_t launch_pipe_t(const TermArgs &a, int num_sms, cudaStream_t st)
 {
     PipeShape ps;
@@ -818,16 +833,25 @@ cudaError_t launch_pipe_t(const TermArgs &a, int num_sms, cudaStream_t st)
     ps.stage_bytes = ps.halo_bytes + ps.lcol_bytes + ps.val_bytes;
     ps.n_hb = (int)(a.n_rows / kHaloRows);
     const int smem = 2 * ps.stage_bytes;
-    int &conf = g_pipe_configured[sizeof(V) == 4][C / 4];
+    int &conf = g_pipe_configured[sizeof(V) == 4][C / 4][RS - 1];
     if (smem > conf) {
-        cudaError_t e = cudaFuncSetAttribute(k_term_halo_pipe<V, C>,
+        cudaError_t e = cudaFuncSetAttribute(k_term_halo_pipe<V, C, RS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         conf = smem;
     }
     const int grid = std::min<int64_t>(num_sms, ps.n_hb);
-    k_term_halo_pipe<V, C><<<grid, kHaloRows * C, smem, st>>>(a, ps);
+    k_term_halo_pipe<V, C, RS><<<grid, kHaloRows * C * RS, smem, st>>>(a, ps);
     return cudaGetLastError();
+}
+
+template <int RS>
+cudaError_t dispatch_pipe(const TermArgs &a, int fp32, int B, cudaStream_t st)
+{
+    if (fp32) return B == 4 ? launch_pipe_t<float, 2, RS>(a, a.num_sms, st)
+                            : launch_pipe_t<float, 4, RS>(a, a.num_sms, st);
+    return B == 2 ? launch_pipe_t<double, 2, RS>(a, a.num_sms, st)
+                  : launch_pipe_t<double, 4, RS>(a, a.num_sms, st);
 }
 
 // Interior terms: FP32 groups of 4, 8, 16 states, FP64 of 2, 4, 8; the
@@ -1154,12 +1178,9 @@ bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
     if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
-        pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
-        if (fp32) return B == 4 ? launch_pipe_t<float, 2>(a, a.num_sms, st)
-                                : launch_pipe_t<float, 4>(a, a.num_sms, st);
-        return B == 2 ? launch_pipe_t<double, 2>(a, a.num_sms, st)
-                      : launch_pipe_t<double, 4>(a, a.num_sms, st);
-    }
+        pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform))
+        return (a.variant & kVariantSplit2) ? dispatch_pipe<2>(a, fp32, B, st)
+                                            : dispatch_pipe<1>(a, fp32, B, st);
     if ((a.variant & kVariantHalo) && a.lcol && !a.cplx &&
         halo_launchable(fp32, B, false, a.halo_max))
         return dispatch_halo<false>(a, fp32, B, st);
@@ -1168,6 +1189,16 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
 
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
+        a.H.col && pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
+        // the pipelined term writes `out`, then the closing reduction reads it
+        cudaError_t e = (a.variant & kVariantSplit2) ? dispatch_pipe<2>(a, fp32, B, st)
+                                                     : dispatch_pipe<1>(a, fp32, B, st);
+        if (e != cudaSuccess) return e;
+        TermArgs r = a;
+        r.H.col = nullptr;
+        return dispatch<true>(r, fp32, B, threads, false, st);
+    }
     if ((a.variant & kVariantHalo) && a.lcol && !a.cplx && a.H.col &&
         halo_launchable(fp32, B, true, a.halo_max))
         return dispatch_halo<true>(a, fp32, B, st);

@@ -521,12 +521,16 @@ def test_gpu_halo_variant_is_bit_identical(tb, prec, kind):
     tol = 1e-10 if prec == 0 else 2e-5
     widths = (2, 4, 8) if prec == 0 else (4, 8, 16)
     for B in widths:
-        c0, _, phi0, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, 65))
-        for variant in (513, 1537):         # halo; halo + pipelined persistent, zig-zag
-            c1, st, phi1, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, variant))
-            assert np.array_equal(phi0, phi1), (B, variant)
-            assert np.max(np.abs(c0 - c1)) < 1e-12, (B, variant)
-            assert np.max(np.abs(c1[0, :2] - ref)) < tol, (B, variant)
+        # halo and halo + pipelined persistent (zig-zag) against the plain wide
+        # kernel; their row-split forms against the plain row-split kernel
+        for plain, variants in ((65, (513, 1537)), (193, (1665,))):
+            c0, _, phi0, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, plain))
+            for variant in variants:
+                c1, st, phi1, _ = run_gpu(tb, smp, s, th, 30, precision=prec,
+                                          cfg=(B, 64, variant))
+                assert np.array_equal(phi0, phi1), (B, variant)
+                assert np.max(np.abs(c0 - c1)) < 1e-12, (B, variant)
+                assert np.max(np.abs(c1[0, :2] - ref)) < tol, (B, variant)
 
 
 def test_gpu_halo_variant_twisted_bilayer_20nm_fp32(tb):
@@ -541,6 +545,10 @@ def test_gpu_halo_variant_twisted_bilayer_20nm_fp32(tb):
         c1, _, phi1, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, variant))
         assert np.array_equal(phi0, phi1), variant
         assert np.max(np.abs(c1[0, 0] - ref[0])) < 2e-5, variant
+    c2, _, phi2, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 193))
+    c3, _, phi3, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 1665))
+    assert np.array_equal(phi2, phi3)
+    assert np.max(np.abs(c3[0, 0] - ref[0])) < 2e-5
 
 
 def test_gpu_lean_build_without_fp64_and_bond_map(tb):
