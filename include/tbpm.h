@@ -337,6 +337,13 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
                                         halo lists are built on first use; a matrix
                                         with a block referencing over 2048 other rows
                                         keeps the plain kernel */
+#define TBPM_VARIANT_CLUSTER 2048    /* FP64, one state, one sample of at most
+                                        16 x 1024 rows, at most 12 entries per row:
+                                        every time step in one thread-block-cluster
+                                        launch, the vectors in the blocks' shared
+                                        memory (distributed shared memory for the
+                                        gathers), a cluster barrier per term;
+                                        otherwise ignored */
 #define TBPM_VARIANT_PIPE 1024       /* with TBPM_VARIANT_HALO, interior terms: a
                                         persistent grid (one block per SM) with two
                                         shared-memory stages, the next block's halo,

@@ -59,6 +59,7 @@ TBPM_VARIANT_SPLIT2 = 128
 TBPM_VARIANT_SPLIT4 = 256
 TBPM_VARIANT_HALO = 512
 TBPM_VARIANT_PIPE = 1024
+TBPM_VARIANT_CLUSTER = 2048
 
 
 class TbpmError(RuntimeError):

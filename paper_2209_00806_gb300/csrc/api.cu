@@ -666,7 +666,8 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
         return fail(c, TBPM_E_INVALID_ARG, "threads must be 64, 128 or 256");
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
                                   (3 << kVariantFusedTileShift) | kVariantWide | kVariantSplit2 |
-                                  kVariantSplit4 | kVariantHalo | kVariantPipe) ||
+                                  kVariantSplit4 | kVariantHalo | kVariantPipe |
+                                  kVariantCluster) ||
         ((variant >> kVariantFusedTileShift) & 3) == 3 ||
         ((variant & kVariantSplit2) && (variant & kVariantSplit4)))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
@@ -983,6 +984,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         CUDA_OR_FAIL(c, cudaEventRecord(ev_all0, c->st));
     }
     std::vector<size_t> step_ev;   // index of the first of 5 events per profiled step
+    bool cluster_run = false;      // the cluster-resident stepping ran (one launch)
 
     for (auto &g : c->groups) {
         const size_t bytes = (size_t)c->H.n_rows * g.B * cs;
@@ -1172,6 +1174,79 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         ra.scale = g.scale;
         ra.scale_f = g.scale_f;
 
+        // cluster-resident stepping: every step of this one FP64 state in one launch
+        const int Kc = (c->variant[precision] & kVariantCluster) && !fp32 && !fused &&
+                               c->groups.size() == 1 && g.B == 1 && c->n_samples == 1 &&
+                               !c->H.cplx && !c->ac_on && !c->qe_on && c->H.val64 &&
+                               c->H.max_width <= kClusterMaxW && n_steps > 0
+                           ? cluster_blocks_for(c->H.n_rows, c->H.max_width, c->H.uniform)
+                           : 0;
+        if (Kc > 0) {
+            if (!c->d_fterms) {
+                rc = dalloc(c, &c->d_fterms, 3 * (size_t)kMaxTerms);
+                if (rc) return rc;
+            }
+            std::vector<FusedTerm> tabs(3 * (size_t)kMaxTerms);
+            ClusterArgs ca;
+            memset(&ca, 0, sizeof(ca));
+            for (int cur0 = 0; cur0 < 3; ++cur0) {
+                int nx = 0;
+                std::vector<Launch> sch = schedule(a, cur0, &nx);
+                ca.next_cur[cur0] = nx;
+                for (size_t k = 0; k < sch.size(); ++k) {
+                    FusedTerm &ft = tabs[cur0 * kMaxTerms + k];
+                    ft.x = sch[k].x;
+                    ft.z = sch[k].z;
+                    ft.out = sch[k].out;
+                    ft.final_term = sch[k].final_term ? 1 : 0;
+                    split_coeff(sch[k].c, 0, &ft.c_hi, &ft.c_lo);
+                    ft.gamma = tsign * sch[k].gamma;
+                }
+            }
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_fterms, tabs.data(), tabs.size() * sizeof(FusedTerm),
+                                            cudaMemcpyHostToDevice, c->st));
+            ca.col = c->H.col;
+            ca.val = c->H.val64;
+            ca.diag = c->H.diag64;
+            ca.slice_ptr = c->H.slice_ptr;
+            ca.fixed_width = c->H.fixed_width;
+            ca.uniform = c->H.uniform;
+            ca.h_uniform = c->H.h_uniform;
+            ca.max_w = std::max(1, c->H.max_width);
+            ca.rows_per_cta = (int)(c->H.n_rows / Kc);
+            ca.psi0 = (const double2 *)g.psi0;
+            for (int k = 0; k < 3; ++k) ca.bufs[k] = (double2 *)g.buf[k];
+            ca.cur0 = g.cur;
+            ca.terms = c->d_fterms;
+            ca.J = M - 1;
+            ca.n_steps = n_steps;
+            const int64_t idx0 = (int64_t)g.s0 * (n_steps + 1);
+            ca.corr = c->d_corr + idx0;
+            ca.norms = c->d_norms + idx0;
+            ca.norm_ref = c->d_norm_ref + g.s0;
+            ca.hard_bound = c->hard_fp64;
+            ca.err = c->d_flags;
+            size_t e0 = 0;
+            if (profile) {
+                e0 = ev_used;
+                ev_used += ev_per_step;
+                step_ev.push_back(e0);
+                for (int q = 0; q < 2; ++q) CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + q], c->st));
+            }
+            cudaError_t e = launch_cluster_steps(ca, Kc, c->st);
+            if (e != cudaSuccess)
+                return fail(c, TBPM_E_CUDA, std::string("cluster steps: ") + cudaGetErrorString(e));
+            if (profile)
+                for (int q = 2; q < 5; ++q) CUDA_OR_FAIL(c, cudaEventRecord(c->events[e0 + q], c->st));
+            CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));    // host table goes out of scope
+            int cur = g.cur;
+            for (int n = 0; n < n_steps; ++n) cur = ca.next_cur[cur];
+            g.cur = cur;
+            launches += 1;
+            cluster_run = true;
+            continue;
+        }
+
         auto run_step = [&](int cur, int *next_cur, bool timed) -> int {
             if (fused) {
                 schedule(a, cur, next_cur);
@@ -1357,8 +1432,10 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             t_fin += a2;
             t_red += a3;
         }
-        // fused: the whole step is one launch; report its per-term share
+        // fused: the whole step is one launch; report its per-term share;
+        // cluster stepping: the whole run is one launch
         S.term_launches = (int64_t)step_ev.size() * (fused ? (M - 1) : n_int);
+        if (cluster_run) S.term_launches = (int64_t)n_steps * (M - 1);
         if (S.term_launches) S.ms_term_avg = t_int / S.term_launches;
         if (!step_ev.empty()) {
             S.ms_final_avg = t_fin / step_ev.size();

@@ -1191,9 +1191,10 @@ cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaSt
 {
     if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
         a.H.col && pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
-        // the pipelined term writes `out`, then the closing reduction reads it
-        cudaError_t e = (a.variant & kVariantSplit2) ? dispatch_pipe<2>(a, fp32, B, st)
-                                                     : dispatch_pipe<1>(a, fp32, B, st);
+        // the pipelined term writes `out`, then the closing reduction reads it;
+        // unsplit rows, as the plain closing term (the states then match the
+        // per-term kernels' bit for bit with or without the row split)
+        cudaError_t e = dispatch_pipe<1>(a, fp32, B, st);
         if (e != cudaSuccess) return e;
         TermArgs r = a;
         r.H.col = nullptr;

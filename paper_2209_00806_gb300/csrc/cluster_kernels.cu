@@ -1,0 +1,215 @@
+// Cluster-resident time stepping for small samples (TBPM_VARIANT_CLUSTER).
+//
+// A sample of up to 16 x 1024 rows -- the 64 x 64 graphene DOS workload has
+// 8192 -- fits, with psi0, psi and the two Clenshaw buffers, in the shared
+// memory of one thread-block cluster.  All time steps of the propagation then
+// run in one launch: each block holds a contiguous range of rows (one row per
+// thread), gathers x from the owning block's shared memory (distributed
+// shared memory across the cluster), and a cluster barrier separates the
+// Clenshaw terms (Sec. 2.2, Eq. psi_t).  The closing term's sums of
+// <psi0|phi> and <phi|phi> are formed per block in a fixed tree and added
+// over the blocks in rank order by block 0 (FP64, deterministic).  Per row
+// the arithmetic and its order are those of the plain term kernel, so the
+// states equal the per-term launches' bit for bit; the launch cost of
+// 15 kernels per step is gone.  FP64 states, one state, real values, at most
+// kClusterMaxW entries per row, within the shared memory of a block.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "tbpm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace tbpm {
+namespace {
+
+__global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int K = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int R = a.rows_per_cta;
+    const int t = threadIdx.x;
+    const int64_t r = (int64_t)rank * R + t;
+    extern __shared__ __align__(16) unsigned char sm[];
+    double2 *vec = reinterpret_cast<double2 *>(sm);                  // [4][R]
+    int32_t *ent = reinterpret_cast<int32_t *>(vec + 4 * R);         // [W][R] owner << 16 | local
+    double *sval = reinterpret_cast<double *>(ent + a.max_w * R);    // [W][R] (general values)
+    __shared__ double2 *remote[16];
+    __shared__ double part[2][3];
+    __shared__ double red[32][3];
+
+    if (t < K) remote[t] = cl.map_shared_rank(vec, t);
+    // this row's entries, as (owning block, local row) pairs
+    int w;
+    int64_t base;
+    if (a.fixed_width) {
+        w = a.fixed_width;
+        base = (r / kSliceRows) * (kSliceRows * (int64_t)w) + r % kSliceRows;
+    } else {
+        const int64_t q = r / kSliceRows;
+        base = a.slice_ptr[q] + r % kSliceRows;
+        w = (int)((a.slice_ptr[q + 1] - a.slice_ptr[q]) / kSliceRows);
+    }
+    for (int k = 0; k < w; ++k) {
+        const int32_t c = a.col[base + (int64_t)k * kSliceRows];
+        ent[k * R + t] = c == (int32_t)r && a.uniform ? -1 : ((c / R) << 16) | (c % R);
+        if (!a.uniform) sval[k * R + t] = a.val[base + (int64_t)k * kSliceRows];
+    }
+    const double d = a.diag[r];
+    vec[t] = a.psi0[r];
+    for (int b = 0; b < 3; ++b)
+        vec[(1 + b) * R + t] = b == a.cur0 ? a.bufs[b][r] : make_double2(0.0, 0.0);
+    cl.sync();
+
+    int cur = a.cur0;
+    for (int n = 1; n <= a.n_steps; ++n) {
+        const FusedTerm *tt = a.terms + cur * kMaxTerms;
+        for (int j = 0; j < a.J; ++j) {
+            const FusedTerm tm = tt[j];
+            const int xb = 1 + (tm.x < 0 ? cur : tm.x);
+            const double2 p = vec[(1 + cur) * R + t];
+            double2 zz = make_double2(0.0, 0.0);
+            if (tm.z >= 0) zz = vec[(1 + tm.z) * R + t];
+            // y = H~ x in the plain kernel's order: diagonal, then the entries
+            double2 y = vec[xb * R + t];
+            y.x *= d;
+            y.y *= d;
+            for (int k = 0; k < w; ++k) {
+                const int32_t e = ent[k * R + t];
+                if (e < 0) continue;                     // padded slot (one-value form)
+                const double h = a.uniform ? a.h_uniform : sval[k * R + t];
+                const double2 x = remote[e >> 16][xb * R + (e & 0xffff)];
+                y.x = fma(h, x.x, y.x);
+                y.y = fma(h, x.y, y.y);
+            }
+            double2 o;
+            {
+                const double re = fma(tm.gamma, y.y, zz.x);
+                const double im = fma(-tm.gamma, y.x, zz.y);
+                o.x = fma(tm.c_hi, p.x, re);
+                o.y = fma(tm.c_hi, p.y, im);
+            }
+            vec[(1 + tm.out) * R + t] = o;
+            if (tm.final_term) {
+                const double2 p0 = vec[t];
+                double v0 = fma(p0.x, o.x, p0.y * o.y);
+                double v1 = fma(p0.x, o.y, -(p0.y * o.x));
+                double v2 = fma(o.x, o.x, o.y * o.y);
+                for (int off = 16; off > 0; off >>= 1) {
+                    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+                    v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+                }
+                if (t % 32 == 0) {
+                    red[t / 32][0] = v0;
+                    red[t / 32][1] = v1;
+                    red[t / 32][2] = v2;
+                }
+                __syncthreads();
+                if (t < 3) {
+                    double s = 0.0;
+                    for (int q = 0; q < (R + 31) / 32; ++q) s += red[q][t];
+                    part[n & 1][t] = s;
+                }
+            }
+            cl.sync();
+        }
+        cur = a.next_cur[cur];
+        // block 0 adds the blocks' sums in rank order (they stay in place for
+        // the next two steps, so no further barrier is needed here)
+        if (rank == 0 && t == 0) {
+            double s[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < K; ++k) {
+                const double *pk = cl.map_shared_rank(&part[n & 1][0], k);
+                s[0] += pk[0];
+                s[1] += pk[1];
+                s[2] += pk[2];
+            }
+            a.corr[n] = make_double2(s[0], s[1]);
+            a.norms[n] = s[2];
+            const double ref = *a.norm_ref;
+            const double drift = ref > 0.0 ? fabs(s[2] / ref - 1.0) : s[2];
+            if (!(s[2] == s[2]) || !(s[0] == s[0]) || !(s[1] == s[1]) || s[2] - s[2] != 0.0)
+                atomicOr(a.err, 2);
+            else if (drift > a.hard_bound)
+                atomicOr(a.err, 1);
+        }
+    }
+    a.bufs[cur][r] = vec[(1 + cur) * R + t];
+    cl.sync();                                           // no block leaves while others read it
+}
+
+}  // namespace
+
+int cluster_blocks_for(int64_t n_rows, int max_w, int uniform)
+{
+    if (n_rows <= 0 || n_rows > 16 * 1024 || max_w > kClusterMaxW) return 0;
+    // 16 blocks (non-portable size) where the device runs such a cluster:
+    // GB300's FP64 rate per SM makes more SMs pay; else 8
+    static int best16 = -1;
+    if (best16 < 0) {
+        best16 = 0;
+        if (cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                 1) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = 16;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(512);
+            cfg.dynamicSmemBytes = 64 * 1024;
+            cfg.attrs = &at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 160 * 1024);
+            if (cudaOccupancyMaxActiveClusters(&n, k_cluster_steps, &cfg) == cudaSuccess && n >= 1)
+                best16 = 1;
+        }
+        cudaGetLastError();
+    }
+    auto fits = [&](int K) {
+        if (n_rows % K || n_rows / K > 1024) return false;
+        const int64_t R = n_rows / K;
+        const int64_t smem = 4 * R * 16 + (int64_t)std::max(1, max_w) * R * (uniform ? 4 : 12);
+        return smem <= 200 * 1024;
+    };
+    if (best16 && fits(16)) return 16;
+    return fits(8) ? 8 : 0;
+}
+
+cudaError_t launch_cluster_steps(const ClusterArgs &a, int K, cudaStream_t st)
+{
+    const int R = a.rows_per_cta;
+    const size_t smem = (size_t)4 * R * sizeof(double2) + (size_t)a.max_w * R * sizeof(int32_t) +
+                        (a.uniform ? 0 : (size_t)a.max_w * R * sizeof(double));
+    cudaError_t e = cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (K > 8) {
+        e = cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = K;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(K);
+    cfg.blockDim = dim3(R);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_cluster_steps, a);
+}
+
+}  // namespace tbpm

@@ -71,6 +71,7 @@ constexpr int kVariantSplit2 = 128;     // each row's entries over 2 threads
 constexpr int kVariantSplit4 = 256;     // each row's entries over 4 threads
 constexpr int kVariantHalo = 512;       // gathers from a shared-memory copy of the block's halo
 constexpr int kVariantPipe = 1024;      // with kVariantHalo: persistent, two stages in flight
+constexpr int kVariantCluster = 2048;   // small FP64 samples: all steps in one cluster launch
 
 // Staged-gather term kernel: rows per block, and the most other rows one
 // block may reference (16-bit positions; the shared copy is sized by the
@@ -290,6 +291,34 @@ struct FusedArgs {
 };
 
 cudaError_t launch_step_fused(const FusedArgs &f, int fp32, int B, int num_sms, cudaStream_t st);
+
+// Cluster-resident time stepping (cluster_kernels.cu): all steps of one FP64
+// state of a sample of up to 16 x 1024 rows in one cluster launch.
+constexpr int kClusterMaxW = 12;           // entries per row it takes
+struct ClusterArgs {
+    const int32_t *col;
+    const double *val;
+    const double *diag;
+    const int64_t *slice_ptr;
+    int fixed_width, uniform, max_w, rows_per_cta;
+    double h_uniform;
+    const double2 *psi0;
+    double2 *bufs[3];
+    int cur0;
+    const FusedTerm *terms;     // [3][kMaxTerms] schedules by the buffer holding psi
+    int J;                      // terms per step
+    int next_cur[3];
+    int n_steps;
+    double2 *corr;              // C_n, n = 1 .. n_steps (state 0 of sample 0)
+    double *norms;
+    const double *norm_ref;
+    double hard_bound;
+    int *err;
+};
+// Blocks of the cluster for n_rows rows (16 where the device runs such a
+// cluster, else 8), or 0 when the sample does not fit.
+int cluster_blocks_for(int64_t n_rows, int max_w, int uniform);
+cudaError_t launch_cluster_steps(const ClusterArgs &a, int K, cudaStream_t st);
 int fused_tile_rows(int fp32, int B, int log4_mult);
 int fused_grid(int fp32, int B, int num_sms);
 

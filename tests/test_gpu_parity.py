@@ -65,11 +65,13 @@ def test_gpu_fp64_ragged_rows_launch_shapes(tb, cfg):
     assert np.max(np.abs(c[0] - ref)) < 1e-10
 
 
-def test_gpu_fp64_graphene_dos_full_workload(tb):
-    """64x64 pristine periodic graphene, 1024 steps: oracle and Bloch exact."""
+@pytest.mark.parametrize("variant", [1, 2049])
+def test_gpu_fp64_graphene_dos_full_workload(tb, variant):
+    """64x64 pristine periodic graphene, 1024 steps: oracle and Bloch exact;
+    per-term launches (1) and the cluster-resident stepping (2049)."""
     w = workloads.graphene_dos()
     th = w.thetas()[0]
-    c, st, _, _ = run_gpu(tb, w.sample, w.s, th, w.n_steps)
+    c, st, _, _ = run_gpu(tb, w.sample, w.s, th, w.n_steps, cfg=(1, 64, variant))
     ref = run_oracle(w.sample, w.s, th, w.n_steps)
     assert np.max(np.abs(c[0, 0] - ref[0])) < 1e-10
     times = w.tau * np.arange(w.n_steps + 1)
@@ -78,6 +80,57 @@ def test_gpu_fp64_graphene_dos_full_workload(tb):
     en, d = tb.dos(c[0].mean(axis=0), w.tau, *w.e_range, w.n_energies)
     en2, d2 = oracle.dos(ref.mean(axis=0), w.tau, *w.e_range, w.n_energies)
     assert np.max(np.abs(d - d2)) < 1e-9
+    if variant & 2048:
+        assert st["kernel_launches"] == 1 + 2 + 1    # states, C_0 term + reduce, all steps
+
+
+@pytest.mark.parametrize("kind", ["graphene_dos", "disordered", "random", "too_wide"])
+def test_gpu_cluster_stepping_is_bit_identical(tb, kind):
+    """TBPM_VARIANT_CLUSTER: the same states as the per-term kernels bit for
+    bit (C within rounding of its block-order sums), on pristine and
+    disordered graphene with vacancies (general values), a ragged random
+    graph (rows of 0 .. 8 entries), and a sample with wider rows, which
+    falls back to the per-term kernels."""
+    if kind == "graphene_dos":
+        smp, s = lattice.graphene(64, 64, pbc=True), 9.0
+    elif kind == "disordered":
+        smp = lattice.graphene(50, 41, pbc=True, seed=3, onsite_w=1.0, vacancy_frac=0.02,
+                               bond_sigma=0.05)
+        s = 9.5
+    else:
+        smp = lattice.random_graph(4000 if kind == "random" else 3000,
+                                   5000 if kind == "random" else 15000, seed=21, onsite_w=2.0)
+        s = 1.02 * np.max(np.abs(np.linalg.eigvalsh(exact.dense_h(smp))))
+    th = rng.phases(55, 1, smp.n_orb)
+    c0, _, phi0, n0 = run_gpu(tb, smp, s, th, 80, cfg=(1, 64, 1))
+    c1, st, phi1, n1 = run_gpu(tb, smp, s, th, 80, cfg=(1, 64, 2049))
+    assert np.array_equal(phi0, phi1)
+    assert np.max(np.abs(c0 - c1)) < 1e-13 and np.max(np.abs(n0 - n1)) < 1e-13
+    ref = run_oracle(smp, s, th, 80)
+    assert np.max(np.abs(c1[0] - ref)) < 1e-10
+    widest = np.max(np.bincount(np.concatenate([smp.hop_i, smp.hop_j]), minlength=smp.n_orb))
+    assert (kind == "too_wide") == (widest > 12)
+    assert st["kernel_launches"] == (4 if widest <= 12 else 4 + 80 * 15)
+
+
+def test_gpu_cluster_stepping_resume_and_backward(tb):
+    """The cluster stepping continues a propagation (TBPM_PROP_RESUME) and runs
+    backward in time (TBPM_PROP_BACKWARD, C(-t) = conj C(t)) like the
+    per-term kernels."""
+    N = tb._native
+    smp = lattice.graphene(40, 40, pbc=True, seed=4, onsite_w=0.6)
+    th = rng.phases(56, 1, smp.n_orb)
+    with tb.Propagator() as p:
+        p.build_sample(smp, 9.5)
+        p.launch_config(0, 1, 64, 2049)
+        p.set_phase_states(th)
+        full = p.propagate(Z, 50, 0)
+        phi_full = p.states()
+        p.propagate(Z, 20, 0)
+        p.propagate(Z, 30, 0, flags=N.TBPM_PROP_RESUME)
+        assert np.max(np.abs(p.states() - phi_full)) < 1e-12
+        back = p.propagate(Z, 50, 0, flags=N.TBPM_PROP_BACKWARD)
+    assert np.max(np.abs(back[0, 0] - np.conj(full[0, 0]))) < 1e-12
 
 
 def test_gpu_multi_sample_batch_fp64_and_fp32(tb):
