@@ -1814,7 +1814,8 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                                 kVariantHalo, kVariantZigZag | kVariantHalo,
                                 kVariantHalo | kVariantPipe,
                                 kVariantZigZag | kVariantHalo | kVariantPipe,
-                                kVariantZigZag | kVariantHalo | kVariantPipe | kVariantSplit2};
+                                kVariantZigZag | kVariantHalo | kVariantPipe | kVariantSplit2,
+                                kVariantZigZag | kVariantCluster};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
     for (int B : widths)
@@ -1824,6 +1825,12 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                 // values and a matrix whose halo lists fit
                 if ((V & kVariantHalo) && (T != thread_opts[0] || c->H.cplx ||
                                            !halo_launchable(precision == TBPM_FP32, B, false, 0)))
+                    continue;
+                // the cluster stepping takes one FP64 state of a small real sample
+                if ((V & kVariantCluster) &&
+                    (T != thread_opts[0] || precision != TBPM_FP64 || B != 1 || c->H.cplx ||
+                     c->n_samples != 1 ||
+                     !cluster_blocks_for(c->H.n_rows, c->H.max_width, c->H.uniform)))
                     continue;
                 if ((V & kVariantHalo) && !c->H.halo_ptr) {
                     std::string msg;

@@ -110,7 +110,7 @@ def test_gpu_cluster_stepping_is_bit_identical(tb, kind):
     assert np.max(np.abs(c1[0] - ref)) < 1e-10
     widest = np.max(np.bincount(np.concatenate([smp.hop_i, smp.hop_j]), minlength=smp.n_orb))
     assert (kind == "too_wide") == (widest > 12)
-    assert st["kernel_launches"] == (4 if widest <= 12 else 4 + 80 * 15)
+    assert st["kernel_launches"] == (4 if widest <= 12 else 3 + 80 * 16)
 
 
 def test_gpu_cluster_stepping_resume_and_backward(tb):
