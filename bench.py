@@ -605,6 +605,41 @@ def run_tbg(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
+    # end to end through the C ABI from pinned host buffers (bonds, phases in;
+    # the averaged correlation and the norms out), flakes up to 600 nm: the
+    # 1.2 um bond list alone is 90 GB of host memory
+    e2e = None
+    if not args.no_e2e and args.side <= 600:
+        h_hi = ds.hop_i.cpu().pin_memory()
+        h_hj = ds.hop_j.cpu().pin_memory()
+        h_hv = ds.hop_v.cpu().pin_memory()
+        h_th = theta.cpu().pin_memory()
+        h_c = torch.empty((1, NT + 1), dtype=torch.complex128).pin_memory()
+
+        def host_step():
+            N.tbpm_build_hamiltonian(prop.ctx, ds.n_orb, None, ds.n_hop, h_hi.data_ptr(),
+                                     h_hj.data_ptr(), h_hv.data_ptr(), s, 1, None, N.TBPM_HOST,
+                                     bflags)
+            N.tbpm_set_phase_states(prop.ctx, S, h_th.data_ptr(), N.TBPM_HOST)
+            N.tbpm_propagate(prop.ctx, z, NT, N.TBPM_FP32, None, N.TBPM_HOST, 0)
+            N.tbpm_correlation(prop.ctx, h_c.data_ptr(), N.TBPM_HOST)
+            return tb.dos(h_c.numpy()[0], tau, -s, s, 4096)
+
+        host_step()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        h2d = sum(x.numel() * x.element_size() for x in (h_hi, h_hj, h_hv, h_th))
+        d2h = h_c.numel() * h_c.element_size() + S * (NT + 1) * 8
+        e2e = {"value": units_per_step * args.steps / dt, "unit": "orbital-Chebyshev-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * dt / args.steps,
+               "note": "whole step: H2D of bonds and phases, build, propagation, state "
+                       "average and DOS"}
+        del h_hi, h_hj, h_hv, h_th
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
         if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm = peaks.get("hbm_gbs") or 6800.0
@@ -634,7 +669,7 @@ def run_tbg(args):
                        "launch": tuned, "build_flags": "FP32 only, no bond map",
                        "value_is": "propagation rate (time-step loop, CUDA events); build separate",
                        "l2": f"inputs larger than L2 (state vectors {8 * S * ds.n_orb / 1e6:.0f} MB)"},
-            "roofline": roof,
+            "roofline": roof, "e2e": e2e,
             "build_ms_per_step": acc["ms_build"] / args.steps,
             "generator_s": gen_s,
             "value_including_build": units_per_step * args.steps / (ms * 1e-3),
@@ -667,21 +702,33 @@ def run_differentiable(args):
     d = {k: torch.as_tensor(getattr(smp, k), device=dev) for k in ("hop_i", "hop_j", "hop_v", "onsite")}
     p = tb.Propagator(local, stream.cuda_stream)
 
-    def dos_of(hv, on):
+    def dos_of(hv, on, flags=0):
         p.build(smp.n_orb, on, d["hop_i"], d["hop_j"], hv, w.s)
         p.set_phase_states(theta)
-        N.tbpm_propagate(p.ctx, w.z, NT, N.TBPM_FP64, None)
+        N.tbpm_propagate(p.ctx, w.z, NT, N.TBPM_FP64, None, None, flags)
         return tb.dos(p.correlation()[0], w.tau, *w.e_range, w.n_energies)[1]
 
     target = dos_of(torch.as_tensor(pw.sample.hop_v, device=dev),
                     torch.zeros(smp.n_orb, dtype=torch.float64, device=dev))
 
+    phases = {"fwd": [], "adj": []}
+
     def one_step():
-        D = dos_of(d["hop_v"], d["onsite"])
-        loss = float(np.sum((D - target) ** 2))
+        ef = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ef[0].record(stream)
+        D = dos_of(d["hop_v"], d["onsite"], N.TBPM_PROP_PROFILE)
+        ef[1].record(stream)
+        phases["st"] = p.stats()
+        loss = float(np.sum((D - target) ** 2))      # the example loss (user code)
         g = tb.dos_adjoint(2.0 * (D - target), NT, w.tau, *w.e_range)
         gbar = p.correlation_adjoint(NT, torch.as_tensor(g[None, :], device=dev))
+        ef[2].record(stream)
         gh, go = p.adjoint(w.z, NT, gbar, K=64)
+        ef[3].record(stream)
+        ef[3].synchronize()
+        phases["fwd"].append(ef[0].elapsed_time(ef[1]))
+        phases["adj"].append(ef[2].elapsed_time(ef[3]))
+        phases["adj_launches"] = p.stats()["kernel_launches"]
         return loss, gh, go
 
     for _ in range(args.warmup):
@@ -698,6 +745,27 @@ def run_differentiable(args):
     ms = e0.elapsed_time(e1)
     M = len(tb.tbpm_bessel_coefficients(w.z))
     units = smp.n_orb * S * NT * (M - 1) * args.steps
+    # FP64 forward term: HBM and FP64-pipe rooflines (measured FP64 FMA peak);
+    # the adjoint's sparse products: the forward pass, the per-segment
+    # recomputation, the per-step polynomials and the conjugate terms,
+    # about N (4M - 5) per state
+    st = phases["st"]
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    tf, _ = N.tbpm_fp64_fma_rate(local, 400000)
+    flops = float(smp.n_orb * S * 10 + st["nnz_true"] * S * 4)
+    ms_t = st["ms_term_avg"]
+    roof = {"bound": "alu", "achieved": flops / (ms_t * 1e-3) / 1e9, "peak": tf * 1e3,
+            "unit": "GFLOP/s", "frac": flops / (ms_t * 1e-3) / 1e9 / (tf * 1e3),
+            "traffic": None, "kernel": "FP64 interior Clenshaw term of the forward pass",
+            "peak_source": "measured: FP64 FMA probe (tbpm_fp64_fma_rate)",
+            "hbm": {"achieved": st["bytes_term"] / (ms_t * 1e-3) / 1e9, "peak": hbm,
+                    "frac": st["bytes_term"] / (ms_t * 1e-3) / 1e9 / hbm},
+            "ms_per_launch": ms_t, "flops_per_launch": flops,
+            "algorithmic_bytes_per_launch": st["bytes_term"]}
+    adj_ms = statistics.median(phases["adj"])
+    adj_units = smp.n_orb * S * NT * (4 * M - 5)
     line = {"metric": "orbital-Chebyshev-steps/s", "value": units / (ms * 1e-3),
             "unit": "orbital-Chebyshev-steps/s (forward steps of a loss+gradient evaluation)",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -710,6 +778,10 @@ def run_differentiable(args):
                        "gradients": "all t_b and eps_i"},
             "loss": loss, "grad_norm_hop": float(torch.linalg.norm(gh)),
             "grad_norm_onsite": float(torch.linalg.norm(go)),
+            "roofline": roof,
+            "forward_ms": statistics.median(phases["fwd"]), "adjoint_ms": adj_ms,
+            "adjoint_products_per_s": adj_units / (adj_ms * 1e-3),
+            "adjoint_kernel_launches": phases["adj_launches"],
             "gpu_launches": int(p.stats()["kernel_launches"]), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     p.close()

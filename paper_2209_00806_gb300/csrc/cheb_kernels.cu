@@ -1181,7 +1181,10 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
         pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform))
         return (a.variant & kVariantSplit2) ? dispatch_pipe<2>(a, fp32, B, st)
                                             : dispatch_pipe<1>(a, fp32, B, st);
+    // the one-stage staged-gather kernel does not split rows: with a row
+    // split requested, the plain split kernel keeps the requested order
     if ((a.variant & kVariantHalo) && a.lcol && !a.cplx &&
+        !(a.variant & (kVariantSplit2 | kVariantSplit4)) &&
         halo_launchable(fp32, B, false, a.halo_max))
         return dispatch_halo<false>(a, fp32, B, st);
     return dispatch<false>(a, fp32, B, threads, true, st);
