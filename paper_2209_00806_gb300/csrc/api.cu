@@ -1211,6 +1211,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             ca.slice_ptr = c->H.slice_ptr;
             ca.fixed_width = c->H.fixed_width;
             ca.uniform = c->H.uniform;
+            ca.zero_diag = c->H.zero_diag;
             ca.h_uniform = c->H.h_uniform;
             ca.max_w = std::max(1, c->H.max_width);
             ca.rows_per_cta = (int)(c->H.n_rows / Kc);

@@ -491,6 +491,7 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
     out.n_rows = n_rows;
     out.n_slices = n_slices;
     out.n_orb_user = in.n_orb;
+    out.zero_diag = in.onsite == nullptr;
 
     CK(cudaMalloc(&out.user_to_row, in.n_orb * sizeof(int32_t)));
     CK(cudaMalloc(&out.orb_sample, in.n_orb * sizeof(int32_t)));

@@ -666,6 +666,8 @@ struct PipeShape {
 
 // RS threads share a row (entries part, part + RS, ... as in term_row's
 // row split, so the states equal the plain split kernel's bit for bit).
+constexpr int kPipeUnroll = 8;
+
 template <typename V, int C, int RS>
 __global__ void __launch_bounds__(kHaloRows * C * RS, 1) k_term_halo_pipe(TermArgs a, PipeShape ps)
 {
@@ -749,12 +751,13 @@ __global__ void __launch_bounds__(kHaloRows * C * RS, 1) k_term_halo_pipe(TermAr
         Cv<V, SPL> y = ld_halo16<V, C>(stg, lr, l);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
-        for (int k = part; k < w; k += 4 * RS) {
-            int hp[4];
-            V h[4];
-            bool ok[4];
+        // eight entries a round: more shared-memory loads in flight per thread
+        for (int k = part; k < w; k += kPipeUnroll * RS) {
+            int hp[kPipeUnroll];
+            V h[kPipeUnroll];
+            bool ok[kPipeUnroll];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kPipeUnroll; ++u) {
                 const int ku = k + u * RS;
                 ok[u] = ku < w;
                 hp[u] = ok[u] ? (int)lcs[ku * kSliceRows] : lr;
@@ -765,11 +768,11 @@ __global__ void __launch_bounds__(kHaloRows * C * RS, 1) k_term_halo_pipe(TermAr
                     h[u] = ok[u] ? vs[ku * kSliceRows] : (V)0;
                 }
             }
-            Cv<V, SPL> xv[4];
+            Cv<V, SPL> xv[kPipeUnroll];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(stg, hp[u], l);
+            for (int u = 0; u < kPipeUnroll; ++u) xv[u] = ld_halo16<V, C>(stg, hp[u], l);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kPipeUnroll; ++u) {
                 if (ok[u]) {
 #pragma unroll
                     for (int j = 0; j < SPL; ++j) {

@@ -76,9 +76,14 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
             double2 zz = make_double2(0.0, 0.0);
             if (tm.z >= 0) zz = vec[(1 + tm.z) * R + t];
             // y = H~ x in the plain kernel's order: diagonal, then the entries
-            double2 y = vec[xb * R + t];
-            y.x *= d;
-            y.y *= d;
+            // (a zero diagonal contributes only signed zeros: skipped, the sums
+            // stay equal to the plain kernel's)
+            double2 y = make_double2(0.0, 0.0);
+            if (!a.zero_diag) {
+                y = vec[xb * R + t];
+                y.x *= d;
+                y.y *= d;
+            }
             for (int k = 0; k < w; ++k) {
                 const int32_t e = ent[k * R + t];
                 if (e < 0) continue;                     // padded slot (one-value form)

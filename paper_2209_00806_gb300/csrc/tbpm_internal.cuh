@@ -301,6 +301,7 @@ struct ClusterArgs {
     const double *diag;
     const int64_t *slice_ptr;
     int fixed_width, uniform, max_w, rows_per_cta;
+    int zero_diag;              // every onsite energy is zero
     double h_uniform;
     const double2 *psi0;
     double2 *bufs[3];
@@ -371,6 +372,7 @@ struct BuildOutput {
     int fixed_width = 0;             // every slice has this width (0: widths vary)
     int64_t bandwidth = 0;           // max |col - row| over the stored entries
     int uniform = 0;                 // all off-diagonal values are equal
+    int zero_diag = 0;               // no onsite energies were given (H_ii = 0)
     int cplx = 0;                    // values are complex (re, im) per entry
     double h_uniform = 0.0;          // that value (H~ units)
     // halo lists of the staged-gather term kernel (built on first use)
