@@ -261,6 +261,13 @@ __global__ void k_bond_rows(int64_t n_hop, const int64_t *hi, const int64_t *hj,
     rows[2 * b + 1] = user_to_row[hj[b]];
 }
 
+// Clears *zero unless every onsite energy is zero.
+__global__ void k_zero_onsite(int64_t n, const double *onsite, int *zero)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && onsite[i] != 0.0) atomicAnd(zero, 0);
+}
+
 // Clears *same unless every hopping equals the first one (after scaling).
 __global__ void k_uniform(int64_t n_hop, const double *hv, double inv_s, int *same)
 {
@@ -491,7 +498,6 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
     out.n_rows = n_rows;
     out.n_slices = n_slices;
     out.n_orb_user = in.n_orb;
-    out.zero_diag = in.onsite == nullptr;
 
     CK(cudaMalloc(&out.user_to_row, in.n_orb * sizeof(int32_t)));
     CK(cudaMalloc(&out.orb_sample, in.n_orb * sizeof(int32_t)));
@@ -611,6 +617,16 @@ int build_sell(const BuildInput &in, int keep64, int keep32, int detect_uniform,
                        cudaMemcpyHostToDevice, st));
 
     out.n_hop = in.n_hop;
+    out.zero_diag = in.onsite == nullptr;
+    if (in.onsite) {          // a diagonal of zeros passed explicitly
+        CK(cudaMemsetAsync(err, 0xff, sizeof(int), st));
+        k_zero_onsite<<<blocks_for(in.n_orb, T), T, 0, st>>>(in.n_orb, in.onsite, err);
+        CK(cudaGetLastError());
+        int zero = 0;
+        CK(cudaMemcpyAsync(&zero, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        out.zero_diag = zero != 0;
+    }
     if (detect_uniform && in.n_hop > 0 && vw == 1) {
         // one hopping value everywhere (e.g. pristine or onsite-disordered
         // lattices): the term kernels then need no value loads

@@ -666,10 +666,10 @@ struct PipeShape {
 
 // RS threads share a row (entries part, part + RS, ... as in term_row's
 // row split, so the states equal the plain split kernel's bit for bit).
-constexpr int kPipeUnroll = 8;
+constexpr int kPipeUnroll = 4;
 
 template <typename V, int C, int RS>
-__global__ void __launch_bounds__(kHaloRows * C * RS, 1) k_term_halo_pipe(TermArgs a, PipeShape ps)
+__global__ void __launch_bounds__(kHaloRows * C * RS) k_term_halo_pipe(TermArgs a, PipeShape ps)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     constexpr int SPL = 16 / (2 * sizeof(V));
@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(kHaloRows * C * RS, 1) k_term_halo_pipe(TermAr
         Cv<V, SPL> y = ld_halo16<V, C>(stg, lr, l);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
-        // eight entries a round: more shared-memory loads in flight per thread
+        // four entries a round (eight measured no faster)
         for (int k = part; k < w; k += kPipeUnroll * RS) {
             int hp[kPipeUnroll];
             V h[kPipeUnroll];
@@ -843,7 +843,21 @@ cudaError_t launch_pipe_t(const TermArgs &a, int num_sms, cudaStream_t st)
         if (e != cudaSuccess) return e;
         conf = smem;
     }
-    const int grid = std::min<int64_t>(num_sms, ps.n_hb);
+    // as many resident blocks per SM as shared memory and registers allow
+    // (one for the twisted bilayer's ~200 KB stages, several for lattices
+    // with short rows), the persistent grid a multiple of the SM count
+    static int occ_cache[2][2][2] = {};
+    static int occ_smem[2][2][2] = {};
+    int &occ = occ_cache[sizeof(V) == 4][C / 4][RS - 1];
+    if (occ_smem[sizeof(V) == 4][C / 4][RS - 1] != smem) {
+        int nb = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_term_halo_pipe<V, C, RS>,
+                                                          kHaloRows * C * RS, smem) != cudaSuccess)
+            nb = 1;
+        occ = std::max(1, nb);
+        occ_smem[sizeof(V) == 4][C / 4][RS - 1] = smem;
+    }
+    const int grid = (int)std::min<int64_t>((int64_t)num_sms * occ, ps.n_hb);
     k_term_halo_pipe<V, C, RS><<<grid, kHaloRows * C * RS, smem, st>>>(a, ps);
     return cudaGetLastError();
 }
