@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--force-e2e", action="store_true",
+                    help="tbg: the end-to-end leg also above 600 nm (the 1.2 um bond list is "
+                         "90 GB of pinned host memory)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shape (profiling runs)")
@@ -609,7 +612,7 @@ def run_tbg(args):
     # the averaged correlation and the norms out), flakes up to 600 nm: the
     # 1.2 um bond list alone is 90 GB of host memory
     e2e = None
-    if not args.no_e2e and args.side <= 600:
+    if not args.no_e2e and (args.side <= 600 or args.force_e2e):
         h_hi = ds.hop_i.cpu().pin_memory()
         h_hj = ds.hop_j.cpu().pin_memory()
         h_hv = ds.hop_v.cpu().pin_memory()
