@@ -291,8 +291,39 @@ __global__ void __launch_bounds__(kAcRows) k_ac_observe(AcArgs a)
         u1x.x *= sx; u1x.y *= sx; u1y.x *= sy; u1y.y *= sy;
     }
     // conj(g_a) u_b for ab = xx, xy, yx, yy
-    A v[8];
     const C2<A> ga[2] = {gx, gy}, ub[2] = {u1x, u1y};
+    if constexpr (sizeof(A) == 4) {
+        // FP32 form: exact float-pair products, the block's rows summed as
+        // float pairs in fixed parts (FP64-grade), one conversion per value
+        __shared__ FF redf[kAcRows][8];
+        __shared__ FF redp[kAcRows];
+#pragma unroll
+        for (int ia = 0; ia < 2; ++ia)
+#pragma unroll
+            for (int ib = 0; ib < 2; ++ib) {
+                FF re, im, nr;
+                ff_dot3(ga[ia].x, ga[ia].y, ub[ib].x, ub[ib].y, re, im, nr);
+                redf[threadIdx.x][(2 * ia + ib) * 2 + 0] = re;
+                redf[threadIdx.x][(2 * ia + ib) * 2 + 1] = im;
+            }
+        __syncthreads();
+        constexpr int P = kAcRows / 8;                  // parts per value
+        {
+            const int v = threadIdx.x % 8, part = threadIdx.x / 8;
+            FF acc = redf[part][v];
+            for (int row = part + P; row < kAcRows; row += P) acc = ff_add(acc, redf[row][v]);
+            redp[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            FF acc = redp[threadIdx.x];
+            for (int part = 1; part < P; ++part) acc = ff_add(acc, redp[part * 8 + threadIdx.x]);
+            a.block_partial[((int64_t)blockIdx.x * (B / 4) + quad) * 8 + threadIdx.x] =
+                ff_to_double(acc);
+        }
+        return;
+    }
+    A v[8];
 #pragma unroll
     for (int ia = 0; ia < 2; ++ia)
 #pragma unroll

@@ -964,6 +964,11 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         if (rc == TBPM_E_UNSUPPORTED) halo = false;
         else if (rc) return fail(c, rc, msg);
     }
+    if (halo && (c->variant[precision] & kVariantPipe) && !c->H.uniform && !c->H.vpack[fp32]) {
+        std::string msg;
+        rc = build_packed_values(c->H, fp32, c->st, msg);
+        if (rc) return fail(c, rc, msg);
+    }
     SellView Hv;
     Hv.slice_ptr = c->H.slice_ptr;
     Hv.col = c->H.col;
@@ -1026,6 +1031,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             base.halo_ptr = c->H.halo_ptr;
             base.halo_rows = c->H.halo_rows;
             base.lcol = c->H.lcol;
+            base.pslice = c->H.pslice;
+            base.vpack = c->H.vpack[fp32];
             base.halo_max = c->H.halo_max;
             base.halo_ent_max = c->H.halo_ent_max;
             base.num_sms = c->num_sms;
@@ -1178,7 +1185,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         const int Kc = (c->variant[precision] & kVariantCluster) && !fp32 && !fused &&
                                c->groups.size() == 1 && g.B == 1 && c->n_samples == 1 &&
                                !c->H.cplx && !c->ac_on && !c->qe_on && c->H.val64 &&
-                               c->H.max_width <= kClusterMaxW && n_steps > 0
+                               c->H.max_width <= kClusterMaxW && n_steps > 0 &&
+                               M - 1 <= kClusterMaxTerms
                            ? cluster_blocks_for(c->H.n_rows, c->H.max_width, c->H.uniform)
                            : 0;
         if (Kc > 0) {
@@ -1417,6 +1425,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         S.bytes_term = vb + (double)c->H.nnz_true * entry + (double)c->n_orb * valb;
         if (halo_used)
             S.bytes_term += 4.0 * (double)c->H.halo_total + 8.0 * (double)(c->H.n_rows / kHaloRows + 1);
+
     }
     if (profile) {
         float ms = 0.f;
@@ -1815,7 +1824,6 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                                 kVariantHalo, kVariantZigZag | kVariantHalo,
                                 kVariantHalo | kVariantPipe,
                                 kVariantZigZag | kVariantHalo | kVariantPipe,
-                                kVariantZigZag | kVariantHalo | kVariantPipe | kVariantSplit2,
                                 kVariantZigZag | kVariantCluster};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];

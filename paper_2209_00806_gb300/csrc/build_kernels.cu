@@ -291,6 +291,14 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // position of its column in that list.  Distinct columns are found with an
 // open-addressing set in shared memory (bounded probes) and sorted by a
 // bitonic sort, so the lists do not depend on thread timing.
+//
+// The positions (and, for the pipelined kernel, a copy of the values) are
+// stored "packed": within a slice, the entries of a row come in groups of
+// four adjacent numbers, entry k of local row lr at
+//   pslice[q] + (k / 4) * 128 + lr * 4 + k % 4,
+// with each slice's width rounded up to a multiple of four (the extra slots
+// point at the own row with value 0).  A thread then reads four positions
+// in one 8-byte load and four FP32 values in one 16-byte load.
 constexpr int kHaloHash = 4096;          // set slots per block (load <= 1/2)
 constexpr int kHaloThreads = 256;
 
@@ -348,27 +356,32 @@ __device__ void halo_collect(int64_t hb, const int64_t *slice_ptr, const int32_t
     }
 }
 
+// Packed entries of each slice: 32 x (width rounded up to 4).
+__global__ void k_packed_slice_entries(int64_t n_slices, const int64_t *slice_ptr, int64_t *ent)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_slices) return;
+    const int64_t w = (slice_ptr[q + 1] - slice_ptr[q]) / kSliceRows;
+    ent[q] = (w + 3) / 4 * 4 * kSliceRows;
+}
+
 // Pass 1: halo size of every block (kHaloRows + distinct external rows), or
 // -1 when the block overflows the set.
 __global__ void __launch_bounds__(kHaloThreads) k_halo_count(const int64_t *slice_ptr,
-                                                             const int32_t *col, int64_t *size,
-                                                             int64_t *ent)
+                                                             const int32_t *col, int64_t *size)
 {
     __shared__ int32_t keys[kHaloHash];
     __shared__ int32_t ext[kHaloMaxExt];
     __shared__ int n_ext, overflow;
     halo_collect(blockIdx.x, slice_ptr, col, keys, ext, &n_ext, &overflow);
-    if (threadIdx.x == 0) {
-        size[blockIdx.x] = overflow ? -1 : (int64_t)kHaloRows + n_ext;
-        const int64_t q0 = blockIdx.x * (int64_t)(kHaloRows / kSliceRows);
-        ent[blockIdx.x] = slice_ptr[q0 + kHaloRows / kSliceRows] - slice_ptr[q0];
-    }
+    if (threadIdx.x == 0) size[blockIdx.x] = overflow ? -1 : (int64_t)kHaloRows + n_ext;
 }
 
-// Pass 2: the lists (at halo_ptr[hb]) and the per-entry positions.
+// Pass 2: the lists (at halo_ptr[hb]) and the per-entry positions, packed.
 __global__ void __launch_bounds__(kHaloThreads) k_halo_fill(const int64_t *slice_ptr,
                                                             const int32_t *col,
                                                             const int64_t *halo_ptr,
+                                                            const int64_t *pslice,
                                                             int32_t *halo_rows, uint16_t *lcol)
 {
     __shared__ int32_t keys[kHaloHash];
@@ -381,23 +394,48 @@ __global__ void __launch_bounds__(kHaloThreads) k_halo_fill(const int64_t *slice
     int32_t *out = halo_rows + halo_ptr[hb];
     for (int k = threadIdx.x; k < kHaloRows + n; k += kHaloThreads)
         out[k] = k < kHaloRows ? (int32_t)(r0 + k) : ext[k - kHaloRows];
-    const int64_t q0 = r0 / kSliceRows, q1 = q0 + kHaloRows / kSliceRows;
-    const int64_t e0 = slice_ptr[q0], e1 = slice_ptr[q1];
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += kHaloThreads) {
-        const int32_t c = col[e];
-        int pos;
-        if (c >= r0 && c < r0 + kHaloRows) {
-            pos = (int)(c - r0);
-        } else {
-            int lo = 0, hi = n - 1;                         // ext is sorted and holds c
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (ext[mid] < c) lo = mid + 1; else hi = mid;
+    const int64_t q0 = r0 / kSliceRows;
+    for (int qq = 0; qq < kHaloRows / kSliceRows; ++qq) {
+        const int64_t q = q0 + qq;
+        const int64_t e0 = slice_ptr[q];
+        const int w = (int)((slice_ptr[q + 1] - e0) / kSliceRows);
+        const int w4 = (w + 3) / 4 * 4;
+        for (int idx = threadIdx.x; idx < w4 * kSliceRows; idx += kHaloThreads) {
+            const int k = idx / kSliceRows, lr = idx % kSliceRows;
+            int pos = qq * kSliceRows + lr;                 // padding: the own row
+            if (k < w) {
+                const int32_t c = col[e0 + idx];
+                if (c >= r0 && c < r0 + kHaloRows) {
+                    pos = (int)(c - r0);
+                } else {
+                    int lo = 0, hi = n - 1;                 // ext is sorted and holds c
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (ext[mid] < c) lo = mid + 1; else hi = mid;
+                    }
+                    pos = kHaloRows + lo;
+                }
             }
-            pos = kHaloRows + lo;
+            lcol[pslice[q] + (k / 4) * (4 * kSliceRows) + lr * 4 + k % 4] = (uint16_t)pos;
         }
-        lcol[e] = (uint16_t)pos;
     }
+}
+
+// Packed copy of the values (see above), padding slots 0.
+template <typename T>
+__global__ void k_pack_values(int64_t n_rows, const int64_t *slice_ptr, const int64_t *pslice,
+                              const T *val, T *vpack)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    const int64_t q = r / kSliceRows;
+    const int lr = (int)(r % kSliceRows);
+    const int64_t e0 = slice_ptr[q];
+    const int w = (int)((slice_ptr[q + 1] - e0) / kSliceRows);
+    const int w4 = (w + 3) / 4 * 4;
+    for (int k = 0; k < w4; ++k)
+        vpack[pslice[q] + (k / 4) * (4 * kSliceRows) + lr * 4 + k % 4] =
+            k < w ? val[e0 + (int64_t)k * kSliceRows + lr] : (T)0;
 }
 
 }  // namespace
@@ -407,22 +445,32 @@ int build_halo(BuildOutput &b, cudaStream_t st, std::string &msg)
     if (b.halo_ptr) return TBPM_OK;
     if (b.n_rows % kHaloRows) { msg = "rows are not a multiple of the halo block"; return TBPM_E_UNSUPPORTED; }
     const int64_t nb = b.n_rows / kHaloRows;
-    int64_t *size = nullptr, *ent = nullptr;
+    const int64_t ns = b.n_slices;
+    int64_t *size = nullptr, *ent = nullptr, *pslice = nullptr;
     CK(cudaMalloc(&size, (nb + 1) * sizeof(int64_t)));
-    CK(cudaMalloc(&ent, nb * sizeof(int64_t)));
-    k_halo_count<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, size, ent);
+    CK(cudaMalloc(&ent, (ns + 1) * sizeof(int64_t)));
+    CK(cudaMalloc(&pslice, (ns + 1) * sizeof(int64_t)));
+    // packed slice offsets
+    k_packed_slice_entries<<<blocks_for(ns, 256), 256, 0, st>>>(ns, b.slice_ptr, ent);
     CK(cudaGetLastError());
-    std::vector<int64_t> hs(nb), he(nb);
-    CK(cudaMemcpyAsync(hs.data(), size, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(he.data(), ent, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    int rc0 = scan_exclusive(ent, pslice, ns, st, msg);
     cudaFree(ent);
+    if (rc0) { cudaFree(size); cudaFree(pslice); return rc0; }
+    std::vector<int64_t> hp(ns + 1);
+    CK(cudaMemcpyAsync(hp.data(), pslice, (ns + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    k_halo_count<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, size);
+    CK(cudaGetLastError());
+    std::vector<int64_t> hs(nb);
+    CK(cudaMemcpyAsync(hs.data(), size, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int spb = kHaloRows / kSliceRows;          // slices per halo block
     int64_t emx = 0;
-    for (int64_t k = 0; k < nb; ++k) emx = std::max(emx, he[k]);
+    for (int64_t k = 0; k < nb; ++k) emx = std::max(emx, hp[(k + 1) * spb] - hp[k * spb]);
     int64_t mx = 0;
     for (int64_t k = 0; k < nb; ++k) {
         if (hs[k] < 0) {
             cudaFree(size);
+            cudaFree(pslice);
             msg = "a row block references more than " + std::to_string(kHaloMaxExt) +
                   " other rows: no halo lists for this matrix";
             return TBPM_E_UNSUPPORTED;
@@ -433,38 +481,64 @@ int build_halo(BuildOutput &b, cudaStream_t st, std::string &msg)
     CK(cudaMalloc(&ptr, (nb + 1) * sizeof(int64_t)));
     int rc = scan_exclusive(size, ptr, nb, st, msg);
     cudaFree(size);
-    if (rc) { cudaFree(ptr); return rc; }
+    if (rc) { cudaFree(ptr); cudaFree(pslice); return rc; }
     int64_t total = 0;
     CK(cudaMemcpyAsync(&total, ptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     int32_t *rows = nullptr;
     uint16_t *lc = nullptr;
+    const int64_t npack = hp[ns];
     cudaError_t e = cudaMalloc(&rows, total * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&lc, (b.nnz_pad > 0 ? b.nnz_pad : 1) * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&lc, (npack > 0 ? npack : 1) * sizeof(uint16_t));
     if (e != cudaSuccess) {
-        cudaFree(ptr); cudaFree(rows); cudaFree(lc);
+        cudaFree(ptr); cudaFree(rows); cudaFree(lc); cudaFree(pslice);
         msg = std::string("halo lists: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? TBPM_E_OOM : TBPM_E_CUDA;
     }
-    k_halo_fill<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, ptr, rows, lc);
+    k_halo_fill<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, ptr, pslice, rows, lc);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-        cudaFree(ptr); cudaFree(rows); cudaFree(lc);
+        cudaFree(ptr); cudaFree(rows); cudaFree(lc); cudaFree(pslice);
         msg = std::string("halo lists: ") + cudaGetErrorString(e);
         return TBPM_E_CUDA;
     }
     b.halo_ptr = ptr;
     b.halo_rows = rows;
     b.lcol = lc;
+    b.pslice = pslice;
+    b.n_packed = npack;
     b.halo_max = (int)mx;
     b.halo_ent_max = (int)std::min<int64_t>(emx, INT32_MAX);
     b.halo_total = total;
     return TBPM_OK;
 }
 
-namespace {
-}  // namespace
+int build_packed_values(BuildOutput &b, int fp32, cudaStream_t st, std::string &msg)
+{
+    if (!b.pslice) { msg = "no halo lists"; return TBPM_E_STATE; }
+    if (b.vpack[fp32]) return TBPM_OK;
+    const void *val = fp32 ? (const void *)b.val32 : (const void *)b.val64;
+    if (!val || b.cplx) { msg = "no real values of this precision"; return TBPM_E_STATE; }
+    const size_t bytes = (size_t)std::max<int64_t>(b.n_packed, 1) * (fp32 ? 4 : 8);
+    void *vp = nullptr;
+    CK(cudaMalloc(&vp, bytes));
+    if (fp32)
+        k_pack_values<float><<<blocks_for(b.n_rows, 256), 256, 0, st>>>(
+            b.n_rows, b.slice_ptr, b.pslice, (const float *)val, (float *)vp);
+    else
+        k_pack_values<double><<<blocks_for(b.n_rows, 256), 256, 0, st>>>(
+            b.n_rows, b.slice_ptr, b.pslice, (const double *)val, (double *)vp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(vp);
+        msg = std::string("packed values: ") + cudaGetErrorString(e);
+        return TBPM_E_CUDA;
+    }
+    b.vpack[fp32] = vp;
+    return TBPM_OK;
+}
 
 void free_build(BuildOutput &b)
 {
@@ -481,6 +555,9 @@ void free_build(BuildOutput &b)
     cudaFree(b.halo_ptr);
     cudaFree(b.halo_rows);
     cudaFree(b.lcol);
+    cudaFree(b.pslice);
+    cudaFree(b.vpack[0]);
+    cudaFree(b.vpack[1]);
     b = BuildOutput();
 }
 

@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(kHaloRows * L, 8 / L) k_term_halo(TermArgs a)
         base = __ldg(a.H.slice_ptr + q);
         w = (int)((__ldg(a.H.slice_ptr + q + 1) - base) / kSliceRows);
     }
-    const uint16_t *lcp = a.lcol + base + (r % kSliceRows);
+    const uint16_t *lcp = a.lcol + a.pslice[q] + (r % kSliceRows) * 4;     // packed
     const V *valp = reinterpret_cast<const V *>(a.H.val) + base + (r % kSliceRows);
     const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
     cp_async_wait_all();
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kHaloRows * L, 8 / L) k_term_halo(TermArgs a)
         for (int u = 0; u < 4; ++u) {
             const int ku = k + u;
             ok[u] = ku < w;
-            hp[u] = ok[u] ? (int)__ldg(lcp + (int64_t)ku * kSliceRows) : lr;
+            hp[u] = ok[u] ? (int)__ldg(lcp + (ku >> 2) * (4 * kSliceRows) + (ku & 3)) : lr;
             if (a.uniform) {
                 ok[u] = ok[u] && hp[u] != lr;        // padded slots point at the own row
                 h[u] = Coef<V>::hu(a);
@@ -664,33 +664,23 @@ struct PipeShape {
     int n_hb;           // halo blocks
 };
 
-// RS threads share a row (entries part, part + RS, ... as in term_row's
-// row split, so the states equal the plain split kernel's bit for bit).
-constexpr int kPipeUnroll = 4;
-
-template <typename V, int C, int RS>
-__global__ void __launch_bounds__(kHaloRows * C * RS) k_term_halo_pipe(TermArgs a, PipeShape ps)
+// Per thread: four entries of its row a round, their positions in one
+// 8-byte and their values in one 16-byte (FP32) shared-memory load.
+template <typename V, int C>
+__global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, PipeShape ps)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     constexpr int SPL = 16 / (2 * sizeof(V));
-    constexpr int NT = kHaloRows * C * RS;
+    constexpr int NT = kHaloRows * C;
+    constexpr int SPB = kHaloRows / kSliceRows;      // slices per halo block
     const int tid = threadIdx.x;
-    const int l = tid % C, part = (tid / C) % RS, lr = tid / (C * RS);
+    const int l = tid % C, lr = tid / C;
     const unsigned char *xg = reinterpret_cast<const unsigned char *>(a.x);
     const int64_t G = gridDim.x;
     auto block_at = [&](int64_t i) -> int64_t {        // i-th block of this CTA, or -1
         const int64_t k = blockIdx.x + i * G;
         if (k >= ps.n_hb) return -1;
         return a.reverse ? ps.n_hb - 1 - k : k;
-    };
-    auto ent_range = [&](int64_t q, int64_t *e0, int *w) {
-        if (a.fixed_width) {
-            *w = a.fixed_width;
-            *e0 = q * (kSliceRows * (int64_t)a.fixed_width);
-        } else {
-            *e0 = __ldg(a.H.slice_ptr + q);
-            *w = (int)((__ldg(a.H.slice_ptr + q + 1) - *e0) / kSliceRows);
-        }
     };
     auto issue = [&](int64_t hb, int s) {
         unsigned char *stg = sm + (int64_t)s * ps.stage_bytes;
@@ -701,12 +691,8 @@ __global__ void __launch_bounds__(kHaloRows * C * RS) k_term_halo_pipe(TermArgs 
             const int64_t g = __ldg(a.halo_rows + h0 + h);
             cp_async16(stg + (h * C + (c ^ halo_swz<C>(h))) * 16, xg + (g * C + c) * 16);
         }
-        int64_t e0, e1;
-        int w;
-        ent_range(hb * (kHaloRows / kSliceRows), &e0, &w);
-        if (a.fixed_width) e1 = e0 + (int64_t)kHaloRows * w;
-        else e1 = __ldg(a.H.slice_ptr + (hb + 1) * (kHaloRows / kSliceRows));
-        const int E = (int)(e1 - e0);                    // a multiple of 32
+        const int64_t e0 = __ldg(a.pslice + hb * SPB);
+        const int E = (int)(__ldg(a.pslice + (hb + 1) * SPB) - e0);   // a multiple of 128
         unsigned char *lc = stg + ps.halo_bytes;
         for (int idx = tid; idx < E / 8; idx += NT)
             cp_async16(lc + idx * 16, a.lcol + e0 + idx * 8);
@@ -714,7 +700,7 @@ __global__ void __launch_bounds__(kHaloRows * C * RS) k_term_halo_pipe(TermArgs 
             constexpr int per = 16 / sizeof(V);
             unsigned char *vs = lc + ps.lcol_bytes;
             for (int idx = tid; idx < E / per; idx += NT)
-                cp_async16(vs + idx * 16, reinterpret_cast<const V *>(a.H.val) + e0 + idx * per);
+                cp_async16(vs + idx * 16, reinterpret_cast<const V *>(a.vpack) + e0 + idx * per);
         }
         cp_async_commit();
     };
@@ -727,52 +713,57 @@ __global__ void __launch_bounds__(kHaloRows * C * RS) k_term_halo_pipe(TermArgs 
         else cp_async_commit();                          // an empty group keeps the count
         // own-row streams of block i, in flight while its stage lands
         const int64_t r = hb * kHaloRows + lr;
-        Cv<V, SPL> p, zz;
-        if (part == 0) {
-            p = ld_ro<V, C, SPL>(a.psi, r, l);
-            if (a.z) zz = ld<V, C, SPL>(a.z, r, l);
-        }
-        if (part != 0 || !a.z) {
+        Cv<V, SPL> p = ld_ro<V, C, SPL>(a.psi, r, l), zz;
+        if (a.z) {
+            zz = ld<V, C, SPL>(a.z, r, l);
+        } else {
 #pragma unroll
             for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
         }
-        const V d = part == 0 ? __ldg(reinterpret_cast<const V *>(a.H.diag) + r) : (V)0;
-        int64_t eb, eq;
-        int wb, w;
-        ent_range(hb * (kHaloRows / kSliceRows), &eb, &wb);
-        ent_range(r / kSliceRows, &eq, &w);
+        const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+        const int64_t q = r / kSliceRows;
+        const int w = a.fixed_width ? a.fixed_width
+                                    : (int)((__ldg(a.H.slice_ptr + q + 1) - __ldg(a.H.slice_ptr + q)) /
+                                            kSliceRows);
+        const int64_t off = __ldg(a.pslice + q) - __ldg(a.pslice + hb * SPB) + (r % kSliceRows) * 4;
         cp_async_wait_group<1>();
         __syncthreads();
         const unsigned char *stg = sm + (int64_t)(i & 1) * ps.stage_bytes;
-        const uint16_t *lcs = reinterpret_cast<const uint16_t *>(stg + ps.halo_bytes) + (eq - eb) +
-                              (r % kSliceRows);
-        const V *vs = reinterpret_cast<const V *>(stg + ps.halo_bytes + ps.lcol_bytes) + (eq - eb) +
-                      (r % kSliceRows);
+        const uint16_t *lcs = reinterpret_cast<const uint16_t *>(stg + ps.halo_bytes) + off;
+        const V *vs = reinterpret_cast<const V *>(stg + ps.halo_bytes + ps.lcol_bytes) + off;
         Cv<V, SPL> y = ld_halo16<V, C>(stg, lr, l);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
-        // four entries a round (eight measured no faster)
-        for (int k = part; k < w; k += kPipeUnroll * RS) {
-            int hp[kPipeUnroll];
-            V h[kPipeUnroll];
-            bool ok[kPipeUnroll];
-#pragma unroll
-            for (int u = 0; u < kPipeUnroll; ++u) {
-                const int ku = k + u * RS;
-                ok[u] = ku < w;
-                hp[u] = ok[u] ? (int)lcs[ku * kSliceRows] : lr;
-                if (a.uniform) {
-                    ok[u] = ok[u] && hp[u] != lr;
-                    h[u] = Coef<V>::hu(a);
+        for (int k = 0; k < w; k += 4) {
+            const int g4 = (k >> 2) * (4 * kSliceRows);
+            const uint2 pk = *reinterpret_cast<const uint2 *>(lcs + g4);
+            int hp[4] = {(int)(pk.x & 0xffff), (int)(pk.x >> 16), (int)(pk.y & 0xffff),
+                         (int)(pk.y >> 16)};
+            V h[4];
+            if (!a.uniform) {
+                if constexpr (sizeof(V) == 4) {
+                    const float4 v4 = *reinterpret_cast<const float4 *>(vs + g4);
+                    h[0] = v4.x; h[1] = v4.y; h[2] = v4.z; h[3] = v4.w;
                 } else {
-                    h[u] = ok[u] ? vs[ku * kSliceRows] : (V)0;
+                    const double2 v0 = *reinterpret_cast<const double2 *>(vs + g4);
+                    const double2 v1 = *reinterpret_cast<const double2 *>(vs + g4 + 2);
+                    h[0] = v0.x; h[1] = v0.y; h[2] = v1.x; h[3] = v1.y;
                 }
             }
-            Cv<V, SPL> xv[kPipeUnroll];
+            bool ok[4];
 #pragma unroll
-            for (int u = 0; u < kPipeUnroll; ++u) xv[u] = ld_halo16<V, C>(stg, hp[u], l);
+            for (int u = 0; u < 4; ++u) {
+                ok[u] = k + u < w;
+                if (a.uniform) {
+                    ok[u] = ok[u] && hp[u] != lr;        // padded slots point at the own row
+                    h[u] = Coef<V>::hu(a);
+                }
+            }
+            Cv<V, SPL> xv[4];
 #pragma unroll
-            for (int u = 0; u < kPipeUnroll; ++u) {
+            for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(stg, hp[u], l);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
                 if (ok[u]) {
 #pragma unroll
                     for (int j = 0; j < SPL; ++j) {
@@ -782,51 +773,40 @@ __global__ void __launch_bounds__(kHaloRows * C * RS) k_term_halo_pipe(TermArgs 
                 }
             }
         }
-        if (RS > 1) {           // add the row's parts (lanes C apart in the warp)
-#pragma unroll
-            for (int o = C; o < C * RS; o <<= 1)
-#pragma unroll
-                for (int j = 0; j < SPL; ++j) {
-                    y.re[j] += __shfl_xor_sync(0xffffffffu, y.re[j], o);
-                    y.im[j] += __shfl_xor_sync(0xffffffffu, y.im[j], o);
-                }
-        }
-        if (part == 0) {
-            const V *sc = Coef<V>::scale(a);
-            if (sc) {
-                sc += (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL);
-#pragma unroll
-                for (int j = 0; j < SPL; ++j) {
-                    const V s = sc[l * SPL + j];
-                    p.re[j] *= s;
-                    p.im[j] *= s;
-                    if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
-                }
-            }
-            const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
-            Cv<V, SPL> o;
+        const V *sc = Coef<V>::scale(a);
+        if (sc) {
+            sc += (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL);
 #pragma unroll
             for (int j = 0; j < SPL; ++j) {
-                V re = fma(g, y.im[j], zz.re[j]);
-                V im = fma(-g, y.re[j], zz.im[j]);
-                if (sizeof(V) == 4) {
-                    re = fma(cl, p.re[j], re);
-                    im = fma(cl, p.im[j], im);
-                }
-                o.re[j] = fma(ch, p.re[j], re);
-                o.im[j] = fma(ch, p.im[j], im);
+                const V s = sc[l * SPL + j];
+                p.re[j] *= s;
+                p.im[j] *= s;
+                if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
             }
-            st<V, C, SPL>(a.out, r, l, o);
         }
+        const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
+        Cv<V, SPL> o;
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            V re = fma(g, y.im[j], zz.re[j]);
+            V im = fma(-g, y.re[j], zz.im[j]);
+            if (sizeof(V) == 4) {
+                re = fma(cl, p.re[j], re);
+                im = fma(cl, p.im[j], im);
+            }
+            o.re[j] = fma(ch, p.re[j], re);
+            o.im[j] = fma(ch, p.im[j], im);
+        }
+        st<V, C, SPL>(a.out, r, l, o);
         __syncthreads();                                 // stage i & 1 may be refilled now
         hb = nxt;
     }
     cp_async_wait_group<0>();
 }
 
-int g_pipe_configured[2][2][2] = {};   // dynamic shared bytes allowed, [fp32][C/4][RS-1]
+int g_pipe_configured[2][2] = {};   // dynamic shared bytes allowed, [fp32][C/4]
 
-template <typename V, int C, int RS>
+template <typename V, int C>
 cudaError_t launch_pipe_t(const TermArgs &a, int num_sms, cudaStream_t st)
 {
     PipeShape ps;
@@ -836,9 +816,9 @@ cudaError_t launch_pipe_t(const TermArgs &a, int num_sms, cudaStream_t st)
     ps.stage_bytes = ps.halo_bytes + ps.lcol_bytes + ps.val_bytes;
     ps.n_hb = (int)(a.n_rows / kHaloRows);
     const int smem = 2 * ps.stage_bytes;
-    int &conf = g_pipe_configured[sizeof(V) == 4][C / 4][RS - 1];
+    int &conf = g_pipe_configured[sizeof(V) == 4][C / 4];
     if (smem > conf) {
-        cudaError_t e = cudaFuncSetAttribute(k_term_halo_pipe<V, C, RS>,
+        cudaError_t e = cudaFuncSetAttribute(k_term_halo_pipe<V, C>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         conf = smem;
@@ -846,29 +826,28 @@ cudaError_t launch_pipe_t(const TermArgs &a, int num_sms, cudaStream_t st)
     // as many resident blocks per SM as shared memory and registers allow
     // (one for the twisted bilayer's ~200 KB stages, several for lattices
     // with short rows), the persistent grid a multiple of the SM count
-    static int occ_cache[2][2][2] = {};
-    static int occ_smem[2][2][2] = {};
-    int &occ = occ_cache[sizeof(V) == 4][C / 4][RS - 1];
-    if (occ_smem[sizeof(V) == 4][C / 4][RS - 1] != smem) {
+    static int occ_cache[2][2] = {};
+    static int occ_smem[2][2] = {};
+    int &occ = occ_cache[sizeof(V) == 4][C / 4];
+    if (occ_smem[sizeof(V) == 4][C / 4] != smem) {
         int nb = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_term_halo_pipe<V, C, RS>,
-                                                          kHaloRows * C * RS, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_term_halo_pipe<V, C>,
+                                                          kHaloRows * C, smem) != cudaSuccess)
             nb = 1;
         occ = std::max(1, nb);
-        occ_smem[sizeof(V) == 4][C / 4][RS - 1] = smem;
+        occ_smem[sizeof(V) == 4][C / 4] = smem;
     }
     const int grid = (int)std::min<int64_t>((int64_t)num_sms * occ, ps.n_hb);
-    k_term_halo_pipe<V, C, RS><<<grid, kHaloRows * C * RS, smem, st>>>(a, ps);
+    k_term_halo_pipe<V, C><<<grid, kHaloRows * C, smem, st>>>(a, ps);
     return cudaGetLastError();
 }
 
-template <int RS>
 cudaError_t dispatch_pipe(const TermArgs &a, int fp32, int B, cudaStream_t st)
 {
-    if (fp32) return B == 4 ? launch_pipe_t<float, 2, RS>(a, a.num_sms, st)
-                            : launch_pipe_t<float, 4, RS>(a, a.num_sms, st);
-    return B == 2 ? launch_pipe_t<double, 2, RS>(a, a.num_sms, st)
-                  : launch_pipe_t<double, 4, RS>(a, a.num_sms, st);
+    if (fp32) return B == 4 ? launch_pipe_t<float, 2>(a, a.num_sms, st)
+                            : launch_pipe_t<float, 4>(a, a.num_sms, st);
+    return B == 2 ? launch_pipe_t<double, 2>(a, a.num_sms, st)
+                  : launch_pipe_t<double, 4>(a, a.num_sms, st);
 }
 
 // Interior terms: FP32 groups of 4, 8, 16 states, FP64 of 2, 4, 8; the
@@ -1194,10 +1173,12 @@ bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    // the pipelined kernel does not split rows: with a row split requested,
+    // the plain split kernel below keeps the requested summation order
     if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
+        (a.vpack || a.uniform) && !(a.variant & (kVariantSplit2 | kVariantSplit4)) &&
         pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform))
-        return (a.variant & kVariantSplit2) ? dispatch_pipe<2>(a, fp32, B, st)
-                                            : dispatch_pipe<1>(a, fp32, B, st);
+        return dispatch_pipe(a, fp32, B, st);
     // the one-stage staged-gather kernel does not split rows: with a row
     // split requested, the plain split kernel keeps the requested order
     if ((a.variant & kVariantHalo) && a.lcol && !a.cplx &&
@@ -1210,11 +1191,12 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
     if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
-        a.H.col && pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
+        (a.vpack || a.uniform) && a.H.col &&
+        pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
         // the pipelined term writes `out`, then the closing reduction reads it;
         // unsplit rows, as the plain closing term (the states then match the
         // per-term kernels' bit for bit with or without the row split)
-        cudaError_t e = dispatch_pipe<1>(a, fp32, B, st);
+        cudaError_t e = dispatch_pipe(a, fp32, B, st);
         if (e != cudaSuccess) return e;
         TermArgs r = a;
         r.H.col = nullptr;

@@ -42,8 +42,11 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
     __shared__ double2 *remote[16];
     __shared__ double part[2][3];
     __shared__ double red[32][3];
+    __shared__ FusedTerm tab[3 * kClusterMaxTerms];
 
     if (t < K) remote[t] = cl.map_shared_rank(vec, t);
+    for (int i = t; i < 3 * a.J; i += blockDim.x)
+        tab[i] = a.terms[(i / a.J) * kMaxTerms + i % a.J];
     // this row's entries, as (owning block, local row) pairs
     int w;
     int64_t base;
@@ -67,14 +70,18 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
     cl.sync();
 
     int cur = a.cur0;
+    bool pending = false;                    // a cluster barrier arrived at, not yet waited on
     for (int n = 1; n <= a.n_steps; ++n) {
-        const FusedTerm *tt = a.terms + cur * kMaxTerms;
+        const FusedTerm *tt = tab + cur * a.J;
         for (int j = 0; j < a.J; ++j) {
             const FusedTerm tm = tt[j];
             const int xb = 1 + (tm.x < 0 ? cur : tm.x);
+            // own-row operands (written only by this thread) before the wait
             const double2 p = vec[(1 + cur) * R + t];
             double2 zz = make_double2(0.0, 0.0);
             if (tm.z >= 0) zz = vec[(1 + tm.z) * R + t];
+            if (pending) cl.barrier_wait();      // the gathered vector is complete
+            pending = false;
             // y = H~ x in the plain kernel's order: diagonal, then the entries
             // (a zero diagonal contributes only signed zeros: skipped, the sums
             // stay equal to the plain kernel's)
@@ -122,8 +129,11 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
                     part[n & 1][t] = s;
                 }
             }
-            cl.sync();
+            cl.barrier_arrive();                 // release this term's writes
+            pending = true;
         }
+        if (pending) cl.barrier_wait();          // the step's sums are in place
+        pending = false;
         cur = a.next_cur[cur];
         // block 0 adds the blocks' sums in rank order (they stay in place for
         // the next two steps, so no further barrier is needed here)

@@ -116,7 +116,10 @@ struct TermArgs {
     // staged-gather variant: halo lists and 16-bit column positions
     const int64_t *halo_ptr;
     const int32_t *halo_rows;
-    const uint16_t *lcol;
+    const uint16_t *lcol;             // packed: entry k of row lr of slice q at
+                                      // pslice[q] + (k/4)*128 + lr*4 + k%4
+    const int64_t *pslice;
+    const void *vpack;                // packed values (pipelined kernel), or nullptr
     int halo_max;
     int halo_ent_max;     // most stored entries of one halo block (pipelined form)
     int num_sms;          // grid of the persistent pipelined form
@@ -295,6 +298,7 @@ cudaError_t launch_step_fused(const FusedArgs &f, int fp32, int B, int num_sms, 
 // Cluster-resident time stepping (cluster_kernels.cu): all steps of one FP64
 // state of a sample of up to 16 x 1024 rows in one cluster launch.
 constexpr int kClusterMaxW = 12;           // entries per row it takes
+constexpr int kClusterMaxTerms = 40;       // Chebyshev terms per step it takes (z <= ~25)
 struct ClusterArgs {
     const int32_t *col;
     const double *val;
@@ -378,11 +382,18 @@ struct BuildOutput {
     // halo lists of the staged-gather term kernel (built on first use)
     int64_t *halo_ptr = nullptr;     // [n_rows / kHaloRows + 1]
     int32_t *halo_rows = nullptr;    // own rows, then the other referenced rows
-    uint16_t *lcol = nullptr;        // [nnz_pad] halo position of each entry's column
+    uint16_t *lcol = nullptr;        // [n_packed] halo position of each entry's column, packed
+    int64_t *pslice = nullptr;       // [n_slices + 1] packed offset of each slice
+    int64_t n_packed = 0;            // packed entries (widths rounded up to 4)
+    void *vpack[2] = {nullptr, nullptr}; // packed values, FP64 / FP32 (pipelined kernel)
     int halo_max = 0;                // longest list
-    int halo_ent_max = 0;            // most stored entries of one block
+    int halo_ent_max = 0;            // most packed entries of one block
     int64_t halo_total = 0;          // entries of all lists
 };
+
+// Packed copy of the values of one precision for the pipelined kernel
+// (built on first use).
+int build_packed_values(BuildOutput &b, int fp32, cudaStream_t st, std::string &msg);
 
 // Lanczos estimate of the extreme eigenvalues of H~ (lanczos.cu): n_iter
 // steps from the SplitMix64 start vector of (kLanczosSeed, kLanczosStream);

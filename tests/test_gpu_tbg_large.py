@@ -72,11 +72,20 @@ def test_gpu_tbg_1200nm_builds_and_propagates(tb, ref600):
     N = tb._native
     dev = torch.device("cuda", 0)
     ds = tbg.twisted_bilayer(1200.0, device=dev)
-    theta = rng.phases_torch(workloads.master_seed(5), 8, ds.n_orb, device=dev)
+    n_orb, n_hop = ds.n_orb, ds.n_hop
+    theta = rng.phases_torch(workloads.master_seed(5), 8, n_orb, device=dev)
     torch.cuda.empty_cache()
-    c, nrm, st = _run(tb, ds, theta, 1, N.TBPM_BUILD_NO_FP64 | N.TBPM_BUILD_NO_BOND_MAP,
-                      variant=N.TBPM_VARIANT_ZIGZAG | N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE)
-    assert ds.n_orb > 1.09e8 and ds.n_hop > 3.7e9 and st["nnz_true"] == 2 * ds.n_hop
+    with tb.Propagator() as p:
+        p.build(n_orb, None, ds.hop_i, ds.hop_j, ds.hop_v, S_EV,
+                flags=N.TBPM_BUILD_NO_FP64 | N.TBPM_BUILD_NO_BOND_MAP)
+        del ds                                  # the library keeps its own copy
+        torch.cuda.empty_cache()
+        p.launch_config(1, 8, 64, N.TBPM_VARIANT_ZIGZAG | N.TBPM_VARIANT_HALO |
+                        N.TBPM_VARIANT_PIPE)
+        p.set_phase_states(theta)
+        c = p.propagate(Z, 2, 1)
+        nrm, st = p.norms(), p.stats()
+    assert n_orb > 1.09e8 and n_hop > 3.7e9 and st["nnz_true"] == 2 * n_hop
     assert np.max(np.abs(nrm - 1)) < 1e-5
     assert np.all(np.abs(c) <= 1 + 1e-6) and np.max(np.abs(c[0, :, 0] - 1)) < 1e-6
     if "c" in ref600:
