@@ -489,6 +489,11 @@ def run_gb300(args):
         }
         de = float(r0["res"][0][1] - r0["res"][0][0])
         line["dos_all_ranks"] = {"states": S * world, "integral": float(np.sum(d_all[0]) * de)}
+        if args.workload == "graphene_dos":
+            # latency-bound: time per time step and per Chebyshev term of the
+            # whole workload step (build, states and DOS included)
+            line["latency"] = {"us_per_time_step": 1e3 * r0["ms"] / args.steps / NT,
+                               "us_per_term": 1e3 * r0["ms"] / args.steps / NT / (M - 1)}
         if head == N.TBPM_FP32:
             line["fp32_renormalisations"] = r0["renorm"]
             line["fp32_max_norm_drift"] = r0["drift"]
@@ -497,10 +502,12 @@ def run_gb300(args):
             en, d32 = r0["res"]
             _, d64 = r64["res"]
             # the FP64 term is bound by GB300's FP64 pipe: 10 flops per lane-row
-            # (diagonal 2, combine 8) plus 4 per stored entry; the peak is the
-            # FP64 FMA rate measured here by the library's probe
+            # (diagonal 2, combine 8) plus 4 per stored entry, for the mean group
+            # width of one launch; the peak is the FP64 FMA rate measured here
+            # by the library's probe
             st64 = r64["stats"]
-            flops = float(smp.n_orb * S * 10 + st64["nnz_true"] * S * 4)
+            s_eff = S / max(1, st64["n_groups"])
+            flops = float((smp.n_orb * 10 + st64["nnz_true"] * 4) * s_eff)
             alu = None
             if r64["ms_term"]:
                 ach = flops / (r64["ms_term"] * 1e-3) / 1e9
@@ -561,8 +568,8 @@ def run_tbg(args):
     M = len(tb.tbpm_bessel_coefficients(z))
     units_per_step = ds.n_orb * S * NT * (M - 1)
     prop = tb.Propagator(local, stream.cuda_stream)
-    variant = N.TBPM_VARIANT_ZIGZAG | N.TBPM_VARIANT_SPLIT2 | (
-        N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE if not args.no_halo else N.TBPM_VARIANT_WIDE)
+    variant = N.TBPM_VARIANT_ZIGZAG | (N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE
+                                       if not args.no_halo else N.TBPM_VARIANT_WIDE)
     tau = z / s
 
     # above 600 nm the Hamiltonian is built once, outside the timed steps, and
@@ -588,7 +595,9 @@ def run_tbg(args):
                        ds.hop_v.cpu().pin_memory())
         del ds
         torch.cuda.empty_cache()
-    if args.variant is not None or args.no_autotune:
+    # above 600 nm the launch shape is fixed (the autotuner's candidates
+    # would take minutes on a 1e8-row matrix)
+    if args.variant is not None or args.no_autotune or not rebuild:
         if args.variant is not None:
             variant = args.variant
         prop.launch_config(N.TBPM_FP32, 8, 64, variant)
@@ -782,7 +791,10 @@ def run_differentiable(args):
         if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm = peaks.get("hbm_gbs") or 6800.0
     tf, _ = N.tbpm_fp64_fma_rate(local, 400000)
-    flops = float(smp.n_orb * S * 10 + st["nnz_true"] * S * 4)
+    # one launch advances one state group: the mean group width (3 states run
+    # as 2 + 1), as bytes_term counts it
+    s_eff = S / max(1, st["n_groups"])
+    flops = float((smp.n_orb * 10 + st["nnz_true"] * 4) * s_eff)
     ms_t = st["ms_term_avg"]
     roof = {"bound": "alu", "achieved": flops / (ms_t * 1e-3) / 1e9, "peak": tf * 1e3,
             "unit": "GFLOP/s", "frac": flops / (ms_t * 1e-3) / 1e9 / (tf * 1e3),

@@ -1835,6 +1835,13 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                 if ((V & kVariantHalo) && (T != thread_opts[0] || c->H.cplx ||
                                            !halo_launchable(precision == TBPM_FP32, B, false, 0)))
                     continue;
+                // the fused step needs a banded row order (its dependency window
+                // spans the bandwidth) and, like the TMA kernel, loses on large
+                // matrices: neither is tried where it cannot win
+                if ((V & kVariantFused) &&
+                    (c->H.bandwidth > (1 << 16) || c->H.n_rows > (1 << 22)))
+                    continue;
+                if ((V & kVariantTma) && c->H.n_rows > (1 << 24)) continue;
                 // the cluster stepping takes one FP64 state of a small real sample
                 if ((V & kVariantCluster) &&
                     (T != thread_opts[0] || precision != TBPM_FP64 || B != 1 || c->H.cplx ||

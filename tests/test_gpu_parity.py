@@ -575,7 +575,7 @@ def test_gpu_halo_variant_is_bit_identical(tb, prec, kind):
     widths = (2, 4, 8) if prec == 0 else (4, 8, 16)
     for B in widths:
         # halo and halo + pipelined persistent (zig-zag) against the plain wide
-        # kernel; their row-split forms against the plain row-split kernel
+        # kernel; with the row split requested they keep the plain split kernel
         for plain, variants in ((65, (513, 1537)), (193, (1665,))):
             c0, _, phi0, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, plain))
             for variant in variants:
