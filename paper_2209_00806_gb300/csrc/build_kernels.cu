@@ -262,18 +262,20 @@ __global__ void k_bond_rows(int64_t n_hop, const int64_t *hi, const int64_t *hj,
 }
 
 // Clears *zero unless every onsite energy is zero.
+// (one atomic per block: a disordered diagonal would otherwise send every
+// thread's atomic to the same word)
 __global__ void k_zero_onsite(int64_t n, const double *onsite, int *zero)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n && onsite[i] != 0.0) atomicAnd(zero, 0);
+    if (__syncthreads_or(i < n && onsite[i] != 0.0) && threadIdx.x == 0) atomicAnd(zero, 0);
 }
 
 // Clears *same unless every hopping equals the first one (after scaling).
 __global__ void k_uniform(int64_t n_hop, const double *hv, double inv_s, int *same)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= n_hop) return;
-    if (hv[b] * inv_s != hv[0] * inv_s) atomicAnd(same, 0);
+    const bool diff = b < n_hop && hv[b] * inv_s != hv[0] * inv_s;
+    if (__syncthreads_or(diff) && threadIdx.x == 0) atomicAnd(same, 0);
 }
 
 __global__ void k_to_f32(int64_t n, const double *src, float *dst)
