@@ -811,6 +811,28 @@ std::vector<Launch> schedule(const std::vector<double> &a, int cur, int *next_cu
     return out;
 }
 
+// FP64 one-value form of one term: gh = gamma h (rounded once, here), and
+// gamma d read from d or 2 d with a sign bit when that is exact (|gamma| of
+// 1 or 2: the closing and interior terms), else multiplied on the device.
+void one_value_terms(const BuildOutput &H, double gamma, double *gh, const double **gdiag,
+                     unsigned long long *sign)
+{
+    *gh = gamma * H.h_uniform;
+    *gdiag = nullptr;
+    *sign = gamma < 0 ? (1ull << 63) : 0ull;
+    const double ag = fabs(gamma);
+    if (ag == 1.0) *gdiag = H.diag64;
+    else if (ag == 2.0) *gdiag = H.diag2_64;
+}
+
+void one_value_table(const BuildOutput &H, FusedTerm &ft)
+{
+    const double *gd = nullptr;
+    one_value_terms(H, ft.gamma, &ft.gh, &gd, &ft.gd_sign);
+    const double ag = fabs(ft.gamma);
+    ft.gd_sel = ag == 2.0 ? 2 : ag == 1.0 ? 1 : 0;
+}
+
 void split_coeff(double c, int fp32, double *hi, double *lo)
 {
     if (fp32) {
@@ -969,6 +991,12 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         rc = build_packed_values(c->H, fp32, c->st, msg);
         if (rc) return fail(c, rc, msg);
     }
+    // FP64 one-value form: 2 d for the interior terms' gamma d
+    if (!fp32 && c->H.uniform && !c->H.zero_diag && !c->H.diag2_64) {
+        std::string msg;
+        rc = build_diag2(c->H, c->st, msg);
+        if (rc) return fail(c, rc, msg);
+    }
     SellView Hv;
     Hv.slice_ptr = c->H.slice_ptr;
     Hv.col = c->H.col;
@@ -1023,6 +1051,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         base.fixed_width = c->H.fixed_width;
         base.h_uniform = c->H.h_uniform;
         base.h_uniform_f = (float)c->H.h_uniform;
+        base.zero_diag = c->H.zero_diag;
         base.psi0 = g.psi0;
         base.partial = c->d_partial;
         base.block_partial = c->d_block_partial;
@@ -1134,6 +1163,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                     ft.c_hi_f = (float)ft.c_hi;
                     ft.c_lo_f = (float)ft.c_lo;
                     ft.gamma_f = (float)ft.gamma;
+                    one_value_table(c->H, ft);
                 }
             }
             CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_fterms, tabs.data(), tabs.size() * sizeof(FusedTerm),
@@ -1142,6 +1172,9 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                                             c->st));
             CUDA_OR_FAIL(c, cudaStreamSynchronize(c->st));    // host table goes out of scope
             fa.H = Hv;
+            fa.uniform = c->H.uniform;
+            fa.zero_diag = c->H.zero_diag;
+            fa.diag2 = c->H.diag2_64;
             fa.psi0 = g.psi0;
             for (int k = 0; k < 3; ++k) fa.bufs[k] = g.buf[k];
             fa.items = c->d_items;
@@ -1209,6 +1242,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                     ft.final_term = sch[k].final_term ? 1 : 0;
                     split_coeff(sch[k].c, 0, &ft.c_hi, &ft.c_lo);
                     ft.gamma = tsign * sch[k].gamma;
+                    one_value_table(c->H, ft);
                 }
             }
             CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_fterms, tabs.data(), tabs.size() * sizeof(FusedTerm),
@@ -1319,6 +1353,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 t.gamma_f = (float)t.gamma;
                 t.scale = g.scale;
                 t.scale_f = g.scale_f;
+                one_value_terms(c->H, t.gamma, &t.gh, &t.gdiag, &t.gdiag_sign);
                 cudaError_t e;
                 if (L.final_term)
                     e = launch_final(t, fp32, g.B, threads, c->st);

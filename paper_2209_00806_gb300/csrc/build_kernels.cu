@@ -379,6 +379,24 @@ __global__ void __launch_bounds__(kHaloThreads) k_halo_count(const int64_t *slic
     if (threadIdx.x == 0) size[blockIdx.x] = overflow ? -1 : (int64_t)kHaloRows + n_ext;
 }
 
+// Bank-parity colouring of the external halo slots.  The pipelined term
+// kernel reads a neighbour's lanes with the row's C threads, so one
+// quarter-warp reads the neighbours of rows 2m and 2m+1 of a slice at the
+// same entry k; with 64-byte rows the two reads fall on the same half of
+// the shared-memory banks -- one extra wavefront -- when their slots have
+// equal parity (reads of the same slot are a broadcast).  The slots of a
+// block's external rows are a free permutation, so they are 2-coloured by
+// slot parity to cut the pair graph (a node per halo row, an edge per pair
+// and entry): greedy local moves in index order for a few passes, the
+// colour counts kept within a few of the slot counts, then restored by the
+// least harmful moves.  Own rows keep slots 0 .. kHaloRows-1.  Integer
+// gains and a fixed order: the layout depends on the matrix alone.
+constexpr int kColorMaxEnt = 12288;      // packed entries of the blocks that are coloured
+constexpr int kColorPasses = 4;
+constexpr int kColorMaxNodes = kHaloRows + kHaloMaxExt;
+constexpr int kColorSmem = (kColorMaxNodes + 1) * 4 + kColorMaxNodes * 4 + kColorMaxEnt * 2 * 2 +
+                           kColorMaxNodes * 2 + kColorMaxNodes;
+
 // Pass 2: the lists (at halo_ptr[hb]) and the per-entry positions, packed.
 __global__ void __launch_bounds__(kHaloThreads) k_halo_fill(const int64_t *slice_ptr,
                                                             const int32_t *col,
@@ -389,20 +407,32 @@ __global__ void __launch_bounds__(kHaloThreads) k_halo_fill(const int64_t *slice
     __shared__ int32_t keys[kHaloHash];
     __shared__ int32_t ext[kHaloMaxExt];
     __shared__ int n_ext, overflow;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    int32_t *offs = reinterpret_cast<int32_t *>(dyn);                   // [nodes + 1]
+    int32_t *cursor = offs + (kColorMaxNodes + 1);                      // [nodes]
+    uint16_t *posbuf = reinterpret_cast<uint16_t *>(cursor + kColorMaxNodes);  // [entries]
+    uint16_t *adj = posbuf + kColorMaxEnt;                              // [entries]
+    uint16_t *slot = adj + kColorMaxEnt;                                // [nodes]
+    uint8_t *color = reinterpret_cast<uint8_t *>(slot + kColorMaxNodes);       // [nodes]
+    const int tid = threadIdx.x;
     const int64_t hb = blockIdx.x;
     halo_collect(hb, slice_ptr, col, keys, ext, &n_ext, &overflow);
     const int n = n_ext;
+    const int H = kHaloRows + n;
     const int64_t r0 = hb * kHaloRows;
-    int32_t *out = halo_rows + halo_ptr[hb];
-    for (int k = threadIdx.x; k < kHaloRows + n; k += kHaloThreads)
-        out[k] = k < kHaloRows ? (int32_t)(r0 + k) : ext[k - kHaloRows];
     const int64_t q0 = r0 / kSliceRows;
-    for (int qq = 0; qq < kHaloRows / kSliceRows; ++qq) {
+    constexpr int SPB = kHaloRows / kSliceRows;
+    const int64_t pb = pslice[q0];
+    const int64_t E = pslice[q0 + SPB] - pb;
+    const bool colour = E <= kColorMaxEnt && n > 1;
+    // node of every packed entry: the own row (its local index), or
+    // kHaloRows + its index in ext
+    for (int qq = 0; qq < SPB; ++qq) {
         const int64_t q = q0 + qq;
         const int64_t e0 = slice_ptr[q];
         const int w = (int)((slice_ptr[q + 1] - e0) / kSliceRows);
         const int w4 = (w + 3) / 4 * 4;
-        for (int idx = threadIdx.x; idx < w4 * kSliceRows; idx += kHaloThreads) {
+        for (int idx = tid; idx < w4 * kSliceRows; idx += kHaloThreads) {
             const int k = idx / kSliceRows, lr = idx % kSliceRows;
             int pos = qq * kSliceRows + lr;                 // padding: the own row
             if (k < w) {
@@ -418,9 +448,127 @@ __global__ void __launch_bounds__(kHaloThreads) k_halo_fill(const int64_t *slice
                     pos = kHaloRows + lo;
                 }
             }
-            lcol[pslice[q] + (k / 4) * (4 * kSliceRows) + lr * 4 + k % 4] = (uint16_t)pos;
+            const int64_t at = pslice[q] + (k / 4) * (4 * kSliceRows) + lr * 4 + k % 4;
+            if (colour) posbuf[at - pb] = (uint16_t)pos;
+            else lcol[at] = (uint16_t)pos;
         }
     }
+    int32_t *out = halo_rows + halo_ptr[hb];
+    for (int k = tid; k < kHaloRows; k += kHaloThreads) out[k] = (int32_t)(r0 + k);
+    if (!colour) {
+        for (int i = tid; i < n; i += kHaloThreads) out[kHaloRows + i] = ext[i];
+        return;
+    }
+    // the pair graph in CSR form (edges of equal nodes are broadcasts: left out)
+    for (int v = tid; v < H; v += kHaloThreads) cursor[v] = 0;
+    __syncthreads();
+    auto for_pairs = [&](auto fn) {
+        for (int qq = 0; qq < SPB; ++qq) {
+            const int base = (int)(pslice[q0 + qq] - pb);
+            const int w4 = (int)((pslice[q0 + qq + 1] - pslice[q0 + qq]) / kSliceRows);
+            for (int idx = tid; idx < w4 * (kSliceRows / 2); idx += kHaloThreads) {
+                const int k = idx / (kSliceRows / 2), m = idx % (kSliceRows / 2);
+                const int i0 = base + (k / 4) * (4 * kSliceRows) + (2 * m) * 4 + k % 4;
+                const int u = posbuf[i0], v = posbuf[i0 + 4];   // rows 2m and 2m+1
+                if (u != v) fn(u, v);
+            }
+        }
+    };
+    for_pairs([&](int u, int v) {
+        atomicAdd(&cursor[u], 1);
+        atomicAdd(&cursor[v], 1);
+    });
+    __syncthreads();
+    if (tid < 32) {                                     // exclusive scan of the degrees
+        int run = 0;
+        for (int v0 = 0; v0 < H; v0 += 32) {
+            const int v = v0 + tid;
+            const int d = v < H ? cursor[v] : 0;
+            int incl = d;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (tid >= o) incl += t;
+            }
+            if (v < H) offs[v] = cursor[v] = run + incl - d;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (tid == 0) offs[H] = run;
+    }
+    __syncthreads();
+    for_pairs([&](int u, int v) {
+        adj[atomicAdd(&cursor[u], 1)] = (uint16_t)v;
+        adj[atomicAdd(&cursor[v], 1)] = (uint16_t)u;
+    });
+    for (int v = tid; v < H; v += kHaloThreads)
+        color[v] = (uint8_t)(v < kHaloRows ? (v & 1) : ((v - kHaloRows) & 1));   // the sorted layout
+    __syncthreads();
+    if (tid < 32) {
+        const int target = (n + 1) / 2;                 // even slots among kHaloRows .. H-1
+        const int cap = 2 + n / 32;
+        int e0 = target;                                // colour-0 external rows
+        // cut gained by moving v to the other colour, summed by the warp
+        auto gain = [&](int v) {
+            const int cv = color[v];
+            int s = 0;
+            for (int e = offs[v] + tid; e < offs[v + 1]; e += 32) s += color[adj[e]] == cv ? 1 : -1;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            return s;
+        };
+        for (int pass = 0; pass < kColorPasses; ++pass) {
+            bool moved = false;
+            for (int v = kHaloRows; v < H; ++v) {
+                const int g = gain(v);
+                const int ne0 = e0 + (color[v] == 0 ? -1 : 1);
+                __syncwarp();
+                if (g > 0 && abs(ne0 - target) <= cap) {
+                    if (tid == 0) color[v] ^= 1;
+                    e0 = ne0;
+                    moved = true;
+                }
+                __syncwarp();
+            }
+            if (!moved) break;
+        }
+        // restore the counts: move the majority colour's least harmful rows
+        while (e0 != target) {
+            const int cm = e0 > target ? 0 : 1;
+            int best = INT32_MAX, bg = INT32_MIN;
+            for (int v = kHaloRows + tid; v < H; v += 32) {
+                if (color[v] != cm) continue;
+                int s = 0;
+                for (int e = offs[v]; e < offs[v + 1]; ++e) s += color[adj[e]] == cm ? 1 : -1;
+                if (s > bg) { bg = s; best = v; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {          // largest gain, then lowest row
+                const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+                const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                if (og > bg || (og == bg && ob < best)) { bg = og; best = ob; }
+            }
+            __syncwarp();
+            if (tid == 0) color[best] ^= 1;
+            __syncwarp();
+            e0 += cm == 0 ? -1 : 1;
+        }
+        // slots: colour c takes kHaloRows + c, + 2 + c, ... in row order
+        int c0 = 0, c1 = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + tid;
+            const int c = i < n ? color[kHaloRows + i] : 0;
+            const unsigned m1 = __ballot_sync(0xffffffffu, i < n && c == 1);
+            const unsigned m0 = __ballot_sync(0xffffffffu, i < n && c == 0);
+            const unsigned below = (1u << tid) - 1u;
+            if (i < n) {
+                const int rk = c ? c1 + __popc(m1 & below) : c0 + __popc(m0 & below);
+                slot[kHaloRows + i] = (uint16_t)(kHaloRows + 2 * rk + c);
+            }
+            c0 += __popc(m0);
+            c1 += __popc(m1);
+        }
+    }
+    for (int v = tid; v < kHaloRows; v += kHaloThreads) slot[v] = (uint16_t)v;
+    __syncthreads();
+    for (int i = tid; i < n; i += kHaloThreads) out[slot[kHaloRows + i]] = ext[i];
+    for (int e = tid; e < (int)E; e += kHaloThreads) lcol[pb + e] = slot[posbuf[e]];
 }
 
 // Packed copy of the values (see above), padding slots 0.
@@ -497,8 +645,12 @@ int build_halo(BuildOutput &b, cudaStream_t st, std::string &msg)
         msg = std::string("halo lists: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? TBPM_E_OOM : TBPM_E_CUDA;
     }
-    k_halo_fill<<<(unsigned)nb, kHaloThreads, 0, st>>>(b.slice_ptr, b.col, ptr, pslice, rows, lc);
-    e = cudaGetLastError();
+    e = cudaFuncSetAttribute(k_halo_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, kColorSmem);
+    if (e == cudaSuccess) {
+        k_halo_fill<<<(unsigned)nb, kHaloThreads, kColorSmem, st>>>(b.slice_ptr, b.col, ptr, pslice,
+                                                                     rows, lc);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaFree(ptr); cudaFree(rows); cudaFree(lc); cudaFree(pslice);
@@ -542,8 +694,34 @@ int build_packed_values(BuildOutput &b, int fp32, cudaStream_t st, std::string &
     return TBPM_OK;
 }
 
+namespace {
+__global__ void k_twice(int64_t n, const double *src, double *dst)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] + src[i];
+}
+}  // namespace
+
+int build_diag2(BuildOutput &b, cudaStream_t st, std::string &msg)
+{
+    if (b.diag2_64) return TBPM_OK;
+    if (!b.diag64) { msg = "no FP64 diagonal"; return TBPM_E_STATE; }
+    double *d2 = nullptr;
+    CK(cudaMalloc(&d2, (size_t)std::max<int64_t>(b.n_rows, 1) * sizeof(double)));
+    k_twice<<<blocks_for(b.n_rows, 256), 256, 0, st>>>(b.n_rows, b.diag64, d2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFree(d2);
+        msg = std::string("2 d: ") + cudaGetErrorString(e);
+        return TBPM_E_CUDA;
+    }
+    b.diag2_64 = d2;
+    return TBPM_OK;
+}
+
 void free_build(BuildOutput &b)
 {
+    cudaFree(b.diag2_64);
     cudaFree(b.user_to_row);
     cudaFree(b.orb_sample);
     cudaFree(b.slice_ptr);

@@ -189,6 +189,149 @@ template <typename V> struct Val2;
 template <> struct Val2<double> { typedef double2 type; };
 template <> struct Val2<float> { typedef float2 type; };
 
+// FP64 one-value form (every off-diagonal entry equal to h): a row's
+// neighbours are added first, s = x_k1 + x_k2 + ... in stored order, and
+// gamma enters through gd = gamma d_r and gh = gamma h:
+//   out = z + (-i)(gd x_r + gh s) + c psi,
+// evaluated per component as fma(c, psi, fma(gh, s, fma(gd, x_r, z))) with
+// the signs of (-i).  That is 2(E-1) adds and 6 FMAs per state and row for E
+// entries (4 FMAs without a diagonal), against 6 + 2E operations when the
+// product is formed entry by entry; GB300 runs the FP64 form at its FP64
+// instruction rate, so the count sets its time.  (The FP32 form, bound by
+// memory, keeps the entry-by-entry order of the general form.)  gd is read
+// when the host formed it exactly (|gamma| = 1 or 2), else multiplied.
+__device__ __forceinline__ double gdiag_at(const TermArgs &a, int64_t r)
+{
+    if (a.gdiag) return xor_sign(__ldg(a.gdiag + r), a.gdiag_sign);
+    return a.gamma * __ldg(reinterpret_cast<const double *>(a.H.diag) + r);
+}
+
+// the combine above for SPL states; xo is unused when zero_diag
+template <int SPL>
+__device__ __forceinline__ Cv<double, SPL> combine_sum(const TermArgs &a, double gd,
+                                                       const Cv<double, SPL> &xo,
+                                                       const Cv<double, SPL> &s,
+                                                       const Cv<double, SPL> &p,
+                                                       const Cv<double, SPL> &zz)
+{
+    const double gh = a.gh, ch = a.c_hi;
+    Cv<double, SPL> o;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+        double re = zz.re[j], im = zz.im[j];
+        if (!a.zero_diag) {
+            re = fma(gd, xo.im[j], re);
+            im = fma(-gd, xo.re[j], im);
+        }
+        re = fma(gh, s.im[j], re);
+        im = fma(-gh, s.re[j], im);
+        o.re[j] = fma(ch, p.re[j], re);
+        o.im[j] = fma(ch, p.im[j], im);
+    }
+    return o;
+}
+
+template <int L, int SPL, int RS>
+__device__ __forceinline__ Cv<double, SPL> term_row_sum(const TermArgs &a, int64_t r, int l,
+                                                        const double *sc, int part)
+{
+    typedef double V;
+    Cv<V, SPL> p, zz;
+    if (a.variant & kVariantStreamHints) {
+        p = ld_cs<V, L, SPL>(a.psi, r, l);
+        if (a.z) zz = ld_cs<V, L, SPL>(a.z, r, l);
+    } else {
+        p = ld_ro<V, L, SPL>(a.psi, r, l);
+        if (a.z) zz = ld<V, L, SPL>(a.z, r, l);
+    }
+    if (!a.z) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
+    }
+    Cv<V, SPL> xo;
+    V gd = 0;
+    if (!a.zero_diag) {
+        xo = ld_ro<V, L, SPL>(a.x, r, l);
+        gd = gdiag_at(a, r);
+    }
+    const int64_t q = r / kSliceRows;
+    const int lr = (int)(r % kSliceRows);
+    int64_t base;
+    int w;
+    if (a.fixed_width) {
+        w = a.fixed_width;
+        base = q * (kSliceRows * (int64_t)w);
+    } else {
+        base = __ldg(a.H.slice_ptr + q);
+        w = (int)((__ldg(a.H.slice_ptr + q + 1) - base) / kSliceRows);
+    }
+    const int32_t *colp = a.H.col + base + lr;
+    Cv<V, SPL> s;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) { s.re[j] = 0; s.im[j] = 0; }
+    // entries part, part + RS, ...: a row's entries precede its padding
+    // (column = own row), so the part's first slot starts the sum or the
+    // part has none
+    auto group = [&](int k, auto first) {
+        int32_t c[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int ku = k + u * RS;
+            ok[u] = ku < w;
+            c[u] = ok[u] ? __ldg(colp + (int64_t)ku * kSliceRows) : (int32_t)r;
+            ok[u] = ok[u] && c[u] != (int32_t)r;
+        }
+        Cv<V, SPL> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_ro<V, L, SPL>(a.x, c[u], l);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (decltype(first)::value && u == 0) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    s.re[j] = ok[0] ? xv[0].re[j] : 0.0;
+                    s.im[j] = ok[0] ? xv[0].im[j] : 0.0;
+                }
+            } else if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    s.re[j] += xv[u].re[j];
+                    s.im[j] += xv[u].im[j];
+                }
+            }
+        }
+    };
+    if (part < w) {
+        group(part, std::true_type{});
+        for (int k = part + 4 * RS; k < w; k += 4 * RS) group(k, std::false_type{});
+    }
+    if (RS > 1) {
+#pragma unroll
+        for (int o = 1; o < RS; o <<= 1)
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                s.re[j] += __shfl_xor_sync(0xffffffffu, s.re[j], o);
+                s.im[j] += __shfl_xor_sync(0xffffffffu, s.im[j], o);
+            }
+    }
+    if (sc) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const V sv = sc[l * SPL + j];
+            p.re[j] *= sv;
+            p.im[j] *= sv;
+            if (a.x_is_psi) {
+                s.re[j] *= sv;
+                s.im[j] *= sv;
+                xo.re[j] *= sv;
+                xo.im[j] *= sv;
+            }
+        }
+    }
+    return combine_sum<SPL>(a, gd, xo, s, p, zz);
+}
+
 // CX: complex matrix values (re, im) per stored entry (Peierls phases);
 // otherwise real values.  RS > 1 splits each row's entries over RS adjacent
 // threads (part = 0 .. RS-1 takes entries part, part + RS, ...; shuffles add
@@ -197,6 +340,9 @@ template <typename V, int L, int SPL, bool CX, int RS = 1>
 __device__ __forceinline__ Cv<V, SPL> term_row(const TermArgs &a, int64_t r, int l,
                                                const V *sc, int part = 0)
 {
+    if constexpr (sizeof(V) == 8 && !CX) {
+        if (a.uniform) return term_row_sum<L, SPL, RS>(a, r, l, sc, part);
+    }
     Cv<V, SPL> p, zz;
     if (a.variant & kVariantStreamHints) {
         p = ld_cs<V, L, SPL>(a.psi, r, l);
@@ -506,6 +652,70 @@ __device__ __forceinline__ Cv<V, SPL> ld_halo(const unsigned char *xs, int h, in
     return o;
 }
 
+// The FP64 one-value form (term_row_sum) with the neighbours gathered from
+// the block's shared copy by their packed 16-bit positions.
+template <int L, int SPL>
+__device__ __forceinline__ Cv<double, SPL> halo_row_sum(const TermArgs &a, const unsigned char *xs,
+                                                        int lr, int l, int w, const uint16_t *lcp,
+                                                        const double *sc, double gd,
+                                                        Cv<double, SPL> p, const Cv<double, SPL> &zz)
+{
+    typedef double V;
+    Cv<V, SPL> xo, s;
+    if (!a.zero_diag) xo = ld_halo<V, L, SPL>(xs, lr, l);
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) { s.re[j] = 0; s.im[j] = 0; }
+    auto group = [&](int k, auto first) {
+        int hp[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int ku = k + u;
+            ok[u] = ku < w;
+            hp[u] = ok[u] ? (int)__ldg(lcp + (ku >> 2) * (4 * kSliceRows) + (ku & 3)) : lr;
+            ok[u] = ok[u] && hp[u] != lr;            // padded slots point at the own row
+        }
+        Cv<V, SPL> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_halo<V, L, SPL>(xs, hp[u], l);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (decltype(first)::value && u == 0) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    s.re[j] = ok[0] ? xv[0].re[j] : 0.0;
+                    s.im[j] = ok[0] ? xv[0].im[j] : 0.0;
+                }
+            } else if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    s.re[j] += xv[u].re[j];
+                    s.im[j] += xv[u].im[j];
+                }
+            }
+        }
+    };
+    if (w > 0) {
+        group(0, std::true_type{});
+        for (int k = 4; k < w; k += 4) group(k, std::false_type{});
+    }
+    if (sc) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const V sv = sc[l * SPL + j];
+            p.re[j] *= sv;
+            p.im[j] *= sv;
+            if (a.x_is_psi) {
+                s.re[j] *= sv;
+                s.im[j] *= sv;
+                xo.re[j] *= sv;
+                xo.im[j] *= sv;
+            }
+        }
+    }
+    return combine_sum<SPL>(a, gd, xo, s, p, zz);
+}
+
 // 64 registers a thread (1024 resident threads per SM, no spills).
 template <typename V, int L, int SPL, bool FINAL>
 __global__ void __launch_bounds__(kHaloRows * L, 8 / L) k_term_halo(TermArgs a)
@@ -548,9 +758,25 @@ __global__ void __launch_bounds__(kHaloRows * L, 8 / L) k_term_halo(TermArgs a)
     const uint16_t *lcp = a.lcol + a.pslice[q] + (r % kSliceRows) * 4;     // packed
     const V *valp = reinterpret_cast<const V *>(a.H.val) + base + (r % kSliceRows);
     const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+    V gd = 0;
+    if constexpr (sizeof(V) == 8) {
+        if (a.uniform && !a.zero_diag) gd = gdiag_at(a, r);
+    }
     cp_async_wait_all();
     __syncthreads();
 
+    Cv<V, SPL> o;
+    if constexpr (sizeof(V) == 8) {
+        if (a.uniform) {                 // FP64 one-value form: neighbours summed first
+            o = halo_row_sum<L, SPL>(a, xs, lr, l, w, lcp, sc, gd, p, zz);
+            st<V, L, SPL>(a.out, r, l, o);
+            if constexpr (FINAL) {
+                const Cv<V, SPL> p0 = ld_ro<V, L, SPL>(a.psi0, r, l);
+                final_reduce<V, L, SPL, kHaloRows>(a, hb, lr, l, o, p0);
+            }
+            return;
+        }
+    }
     Cv<V, SPL> y = ld_halo<V, L, SPL>(xs, lr, l);
 #pragma unroll
     for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
@@ -594,7 +820,6 @@ __global__ void __launch_bounds__(kHaloRows * L, 8 / L) k_term_halo(TermArgs a)
         }
     }
     const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
-    Cv<V, SPL> o;
 #pragma unroll
     for (int j = 0; j < SPL; ++j) {
         V re = fma(g, y.im[j], zz.re[j]);
@@ -644,13 +869,15 @@ template <int N> __device__ __forceinline__ void cp_async_wait_group()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Lane l of halo row h in a stage: rows of C 16-byte chunks, chunk l of
+// each row read by the row's thread l (a quarter-warp reads two whole rows,
+// so no chunk permutation changes its bank conflicts); xl = stage + 16 l.
 template <typename V, int C>
-__device__ __forceinline__ Cv<V, 16 / (2 * sizeof(V))> ld_halo16(const unsigned char *xs, int h,
-                                                                  int l)
+__device__ __forceinline__ Cv<V, 16 / (2 * sizeof(V))> ld_halo16(const unsigned char *xl, int h)
 {
     constexpr int SPL = 16 / (2 * sizeof(V));
     typedef typename LaneT<V, SPL>::type Lane;
-    const Lane v = *reinterpret_cast<const Lane *>(xs + (h * C + (l ^ halo_swz<C>(h))) * 16);
+    const Lane v = *reinterpret_cast<const Lane *>(xl + h * (C * 16));
     Cv<V, SPL> o;
     unpack(v, o);
     return o;
@@ -664,8 +891,79 @@ struct PipeShape {
     int n_hb;           // halo blocks
 };
 
+// The FP64 one-value form (term_row_sum) for the pipelined kernel: one
+// FP64 state per 16-byte lane, four packed positions a round, the next
+// round's read before this round's gathers; sc: this lane's state scale.
+template <int C>
+__device__ __forceinline__ Cv<double, 1> pipe_row_sum(const TermArgs &a, const unsigned char *xl,
+                                                      int lr, int w, const uint16_t *lcs, double gd,
+                                                      Cv<double, 1> p, const Cv<double, 1> &zz,
+                                                      const double *sc)
+{
+    typedef double V;
+    Cv<V, 1> xo, s;
+    if (!a.zero_diag) xo = ld_halo16<V, C>(xl, lr);
+    s.re[0] = 0;
+    s.im[0] = 0;
+    uint2 pk = make_uint2(0u, 0u);
+    if (w > 0) pk = *reinterpret_cast<const uint2 *>(lcs);
+    auto group = [&](int k, auto first) {
+        const int hp[4] = {(int)(pk.x & 0xffff), (int)(pk.x >> 16), (int)(pk.y & 0xffff),
+                           (int)(pk.y >> 16)};
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ok[u] = k + u < w && hp[u] != lr;   // padding: the own row
+        Cv<V, 1> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(xl, hp[u]);
+        if (k + 4 < w) pk = *reinterpret_cast<const uint2 *>(lcs + ((k + 4) >> 2) * (4 * kSliceRows));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (decltype(first)::value && u == 0) {
+                s.re[0] = ok[0] ? xv[0].re[0] : 0.0;
+                s.im[0] = ok[0] ? xv[0].im[0] : 0.0;
+            } else if (ok[u]) {
+                s.re[0] += xv[u].re[0];
+                s.im[0] += xv[u].im[0];
+            }
+        }
+    };
+    if (w > 0) {
+        group(0, std::true_type{});
+        for (int k = 4; k < w; k += 4) group(k, std::false_type{});
+    }
+    if (sc) {
+        const V sv = *sc;
+        p.re[0] *= sv;
+        p.im[0] *= sv;
+        if (a.x_is_psi) {
+            s.re[0] *= sv;
+            s.im[0] *= sv;
+            xo.re[0] *= sv;
+            xo.im[0] *= sv;
+        }
+    }
+    return combine_sum<1>(a, gd, xo, s, p, zz);
+}
+
+// Where block j's lists start and how long they are.
+struct PipeMeta {
+    int64_t h0;         // first halo row of the block's list
+    int64_t e0;         // first packed entry of the block's four slices
+    int H;              // halo rows
+    int E;              // packed entries (a multiple of 128)
+};
+
+constexpr int kPipeIdx = (kHaloRows + kHaloMaxExt + kHaloRows - 1) / kHaloRows;  // halo rows per thread
+
 // Per thread: four entries of its row a round, their positions in one
-// 8-byte and their values in one 16-byte (FP32) shared-memory load.
+// 8-byte and their values in one 16-byte (FP32) shared-memory load, the
+// next four's loads issued before this four's gathers.  The global loads
+// that address the copies are software-pipelined across the CTA's blocks:
+// the list bounds of block i+3 and the halo row numbers of block i+2 are
+// loaded while block i computes, so issuing block i+1's copies waits on no
+// global load (with one resident block per SM every warp would otherwise
+// wait on that chain together).
 template <typename V, int C>
 __global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, PipeShape ps)
 {
@@ -682,35 +980,75 @@ __global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, Pi
         if (k >= ps.n_hb) return -1;
         return a.reverse ? ps.n_hb - 1 - k : k;
     };
-    auto issue = [&](int64_t hb, int s) {
-        unsigned char *stg = sm + (int64_t)s * ps.stage_bytes;
-        const int64_t h0 = a.halo_ptr[hb];
-        const int H = (int)(a.halo_ptr[hb + 1] - h0);
-        for (int idx = tid; idx < H * C; idx += NT) {
-            const int h = idx / C, c = idx % C;
-            const int64_t g = __ldg(a.halo_rows + h0 + h);
-            cp_async16(stg + (h * C + (c ^ halo_swz<C>(h))) * 16, xg + (g * C + c) * 16);
+    auto meta_of = [&](int64_t hb) {
+        PipeMeta m = {0, 0, 0, 0};
+        if (hb >= 0) {
+            m.h0 = __ldg(a.halo_ptr + hb);
+            m.H = (int)(__ldg(a.halo_ptr + hb + 1) - m.h0);
+            m.e0 = __ldg(a.pslice + hb * SPB);
+            m.E = (int)(__ldg(a.pslice + (hb + 1) * SPB) - m.e0);
         }
-        const int64_t e0 = __ldg(a.pslice + hb * SPB);
-        const int E = (int)(__ldg(a.pslice + (hb + 1) * SPB) - e0);   // a multiple of 128
+        return m;
+    };
+    // halo rows lr, lr + 128, ... of a block: the x rows this thread copies
+    auto rows_of = [&](const PipeMeta &m, int32_t (&g)[kPipeIdx]) {
+#pragma unroll
+        for (int k = 0; k < kPipeIdx; ++k) {       // predicated, not a loop exit: the
+            const int h = lr + k * kHaloRows;      // loads stay ahead of their use
+            g[k] = h < m.H ? __ldg(a.halo_rows + m.h0 + h) : 0;
+        }
+    };
+    // this thread's row of block hb: its entry count and packed offset
+    auto row_of = [&](int64_t hb, const PipeMeta &m, int &w, int &off) {
+        w = 0;
+        off = 0;
+        if (hb < 0) return;
+        const int64_t q = (hb * kHaloRows + lr) / kSliceRows;
+        w = a.fixed_width ? a.fixed_width
+                          : (int)((__ldg(a.H.slice_ptr + q + 1) - __ldg(a.H.slice_ptr + q)) / kSliceRows);
+        off = (int)(__ldg(a.pslice + q) - m.e0) + (lr % kSliceRows) * 4;
+    };
+    auto issue = [&](const PipeMeta &m, const int32_t (&g)[kPipeIdx], int s) {
+        unsigned char *stg = sm + (int64_t)s * ps.stage_bytes;
+#pragma unroll
+        for (int k = 0; k < kPipeIdx; ++k) {
+            const int h = lr + k * kHaloRows;
+            if (h < m.H) cp_async16(stg + (h * C + l) * 16, xg + ((int64_t)g[k] * C + l) * 16);
+        }
         unsigned char *lc = stg + ps.halo_bytes;
-        for (int idx = tid; idx < E / 8; idx += NT)
-            cp_async16(lc + idx * 16, a.lcol + e0 + idx * 8);
+        for (int idx = tid; idx < m.E / 8; idx += NT)
+            cp_async16(lc + idx * 16, a.lcol + m.e0 + idx * 8);
         if (!a.uniform) {
             constexpr int per = 16 / sizeof(V);
             unsigned char *vs = lc + ps.lcol_bytes;
-            for (int idx = tid; idx < E / per; idx += NT)
-                cp_async16(vs + idx * 16, reinterpret_cast<const V *>(a.vpack) + e0 + idx * per);
+            for (int idx = tid; idx < m.E / per; idx += NT)
+                cp_async16(vs + idx * 16, reinterpret_cast<const V *>(a.vpack) + m.e0 + idx * per);
         }
         cp_async_commit();
     };
 
+    // prologue: block 0's copies, then the bounds and rows one and two ahead
     int64_t hb = block_at(0);
-    if (hb >= 0) issue(hb, 0);
+    int32_t g1[kPipeIdx];
+    PipeMeta m1, m2;
+    int w, off;
+    {
+        const PipeMeta m0 = meta_of(hb);
+        m1 = meta_of(block_at(1));
+        m2 = meta_of(block_at(2));
+        int32_t g0[kPipeIdx];
+        rows_of(m0, g0);
+        rows_of(m1, g1);
+        row_of(hb, m0, w, off);
+        if (hb >= 0) issue(m0, g0, 0);
+    }
     for (int64_t i = 0; hb >= 0; ++i) {
         const int64_t nxt = block_at(i + 1);
-        if (nxt >= 0) issue(nxt, (int)((i + 1) & 1));
+        if (nxt >= 0) issue(m1, g1, (int)((i + 1) & 1));
         else cp_async_commit();                          // an empty group keeps the count
+        const PipeMeta m3 = meta_of(block_at(i + 3));
+        int w1, off1;
+        row_of(nxt, m1, w1, off1);
         // own-row streams of block i, in flight while its stage lands
         const int64_t r = hb * kHaloRows + lr;
         Cv<V, SPL> p = ld_ro<V, C, SPL>(a.psi, r, l), zz;
@@ -721,39 +1059,64 @@ __global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, Pi
             for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
         }
         const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
-        const int64_t q = r / kSliceRows;
-        const int w = a.fixed_width ? a.fixed_width
-                                    : (int)((__ldg(a.H.slice_ptr + q + 1) - __ldg(a.H.slice_ptr + q)) /
-                                            kSliceRows);
-        const int64_t off = __ldg(a.pslice + q) - __ldg(a.pslice + hb * SPB) + (r % kSliceRows) * 4;
+        V gd = 0;
+        if constexpr (sizeof(V) == 8) {
+            if (a.uniform && !a.zero_diag) gd = gdiag_at(a, r);
+        }
         cp_async_wait_group<1>();
         __syncthreads();
+        rows_of(m2, g1);                                 // block i+2's rows, used next round
         const unsigned char *stg = sm + (int64_t)(i & 1) * ps.stage_bytes;
+        const unsigned char *xl = stg + l * 16;
         const uint16_t *lcs = reinterpret_cast<const uint16_t *>(stg + ps.halo_bytes) + off;
         const V *vs = reinterpret_cast<const V *>(stg + ps.halo_bytes + ps.lcol_bytes) + off;
-        Cv<V, SPL> y = ld_halo16<V, C>(stg, lr, l);
+        if constexpr (sizeof(V) == 8) {
+            if (a.uniform) {                 // FP64 one-value form: neighbours summed first
+                const Cv<V, SPL> o = pipe_row_sum<C>(a, xl, lr, w, lcs, gd, p, zz,
+                                                     Coef<V>::scale(a) ? Coef<V>::scale(a) +
+                                                         (int64_t)a.chunk_sample[r / kChunkRows] *
+                                                             (C * SPL) + l * SPL
+                                                                       : nullptr);
+                st<V, C, SPL>(a.out, r, l, o);
+                __syncthreads();                         // stage i & 1 may be refilled now
+                hb = nxt;
+                m1 = m2;
+                m2 = m3;
+                w = w1;
+                off = off1;
+                continue;
+            }
+        }
+        Cv<V, SPL> y = ld_halo16<V, C>(xl, lr);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
-        for (int k = 0; k < w; k += 4) {
+        // four positions and values a round; the next round's loaded first
+        uint2 pk = make_uint2(0u, 0u);
+        V hv[4] = {0, 0, 0, 0};
+        auto load4 = [&](int k) {
             const int g4 = (k >> 2) * (4 * kSliceRows);
-            const uint2 pk = *reinterpret_cast<const uint2 *>(lcs + g4);
-            int hp[4] = {(int)(pk.x & 0xffff), (int)(pk.x >> 16), (int)(pk.y & 0xffff),
-                         (int)(pk.y >> 16)};
-            V h[4];
+            pk = *reinterpret_cast<const uint2 *>(lcs + g4);
             if (!a.uniform) {
                 if constexpr (sizeof(V) == 4) {
                     const float4 v4 = *reinterpret_cast<const float4 *>(vs + g4);
-                    h[0] = v4.x; h[1] = v4.y; h[2] = v4.z; h[3] = v4.w;
+                    hv[0] = v4.x; hv[1] = v4.y; hv[2] = v4.z; hv[3] = v4.w;
                 } else {
                     const double2 v0 = *reinterpret_cast<const double2 *>(vs + g4);
                     const double2 v1 = *reinterpret_cast<const double2 *>(vs + g4 + 2);
-                    h[0] = v0.x; h[1] = v0.y; h[2] = v1.x; h[3] = v1.y;
+                    hv[0] = v0.x; hv[1] = v0.y; hv[2] = v1.x; hv[3] = v1.y;
                 }
             }
+        };
+        if (w > 0) load4(0);
+        for (int k = 0; k < w; k += 4) {
+            const int hp[4] = {(int)(pk.x & 0xffff), (int)(pk.x >> 16), (int)(pk.y & 0xffff),
+                               (int)(pk.y >> 16)};
+            V h[4];
             bool ok[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 ok[u] = k + u < w;
+                h[u] = hv[u];
                 if (a.uniform) {
                     ok[u] = ok[u] && hp[u] != lr;        // padded slots point at the own row
                     h[u] = Coef<V>::hu(a);
@@ -761,7 +1124,8 @@ __global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, Pi
             }
             Cv<V, SPL> xv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(stg, hp[u], l);
+            for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(xl, hp[u]);
+            if (k + 4 < w) load4(k + 4);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (ok[u]) {
@@ -800,6 +1164,10 @@ __global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, Pi
         st<V, C, SPL>(a.out, r, l, o);
         __syncthreads();                                 // stage i & 1 may be refilled now
         hb = nxt;
+        m1 = m2;
+        m2 = m3;
+        w = w1;
+        off = off1;
     }
     cp_async_wait_group<0>();
 }

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
         if (!a.uniform) sval[k * R + t] = a.val[base + (int64_t)k * kSliceRows];
     }
     const double d = a.diag[r];
+    const double d2 = d + d;                 // 2 d, exact: gamma d of the interior terms
     vec[t] = a.psi0[r];
     for (int b = 0; b < 3; ++b)
         vec[(1 + b) * R + t] = b == a.cur0 ? a.bufs[b][r] : make_double2(0.0, 0.0);
@@ -82,25 +83,54 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
             if (tm.z >= 0) zz = vec[(1 + tm.z) * R + t];
             if (pending) cl.barrier_wait();      // the gathered vector is complete
             pending = false;
-            // y = H~ x in the plain kernel's order: diagonal, then the entries
-            // (a zero diagonal contributes only signed zeros: skipped, the sums
-            // stay equal to the plain kernel's)
-            double2 y = make_double2(0.0, 0.0);
-            if (!a.zero_diag) {
-                y = vec[xb * R + t];
-                y.x *= d;
-                y.y *= d;
-            }
-            for (int k = 0; k < w; ++k) {
-                const int32_t e = ent[k * R + t];
-                if (e < 0) continue;                     // padded slot (one-value form)
-                const double h = a.uniform ? a.h_uniform : sval[k * R + t];
-                const double2 x = remote[e >> 16][xb * R + (e & 0xffff)];
-                y.x = fma(h, x.x, y.x);
-                y.y = fma(h, x.y, y.y);
-            }
             double2 o;
-            {
+            if (a.uniform) {
+                // the one-value form of the per-term kernels: the neighbours
+                // summed in stored order (padding, -1, only after a row's
+                // entries), then fma(c, psi, fma(gh, s, fma(gd, x_r, z)))
+                double2 s = make_double2(0.0, 0.0);
+                if (w > 0) {
+                    const int32_t e = ent[t];
+                    if (e >= 0) s = remote[e >> 16][xb * R + (e & 0xffff)];
+                }
+                for (int k = 1; k < w; ++k) {
+                    const int32_t e = ent[k * R + t];
+                    if (e < 0) continue;
+                    const double2 x = remote[e >> 16][xb * R + (e & 0xffff)];
+                    s.x += x.x;
+                    s.y += x.y;
+                }
+                double re = zz.x, im = zz.y;
+                if (!a.zero_diag) {
+                    const double gd = tm.gd_sel == 2 ? xor_sign(d2, tm.gd_sign)
+                                    : tm.gd_sel == 1 ? xor_sign(d, tm.gd_sign)
+                                                     : tm.gamma * d;
+                    const double2 xo = vec[xb * R + t];
+                    re = fma(gd, xo.y, re);
+                    im = fma(-gd, xo.x, im);
+                }
+                re = fma(tm.gh, s.y, re);
+                im = fma(-tm.gh, s.x, im);
+                o.x = fma(tm.c_hi, p.x, re);
+                o.y = fma(tm.c_hi, p.y, im);
+            } else {
+                // y = H~ x in the plain kernel's order: diagonal, then the entries
+                // (a zero diagonal contributes only signed zeros: skipped, the
+                // sums stay equal to the plain kernel's)
+                double2 y = make_double2(0.0, 0.0);
+                if (!a.zero_diag) {
+                    y = vec[xb * R + t];
+                    y.x *= d;
+                    y.y *= d;
+                }
+                for (int k = 0; k < w; ++k) {
+                    const int32_t e = ent[k * R + t];
+                    if (e < 0) continue;
+                    const double h = sval[k * R + t];
+                    const double2 x = remote[e >> 16][xb * R + (e & 0xffff)];
+                    y.x = fma(h, x.x, y.x);
+                    y.y = fma(h, x.y, y.y);
+                }
                 const double re = fma(tm.gamma, y.y, zz.x);
                 const double im = fma(-tm.gamma, y.x, zz.y);
                 o.x = fma(tm.c_hi, p.x, re);

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tbpm_internal.cuh"
 
 namespace tbpm {
@@ -108,6 +110,83 @@ __device__ __forceinline__ Cf<V, SPL> fused_row(const FusedArgs &f, const FusedT
     const V d = __ldg(reinterpret_cast<const V *>(f.H.diag) + r);
     Cf<V, SPL> y;
     unpf(x_ro ? __ldg(xl + r * L + l) : __ldcg(xl + r * L + l), y);
+    if constexpr (sizeof(V) == 8) {
+        if (f.uniform) {
+            // FP64 one-value form, as in the per-term kernels: neighbours
+            // summed in stored order (padding -- the own row -- skipped),
+            // then fma(c, psi, fma(gh, s, fma(gd, x_r, z)))
+            Cf<V, SPL> sm;
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) { sm.re[j] = 0; sm.im[j] = 0; }
+            auto group = [&](int k, auto first) {
+                int32_t c[4];
+                bool ok[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ok[u] = k + u < w;
+                    c[u] = ok[u] ? __ldg(colp + (int64_t)(k + u) * kSliceRows) : (int32_t)r;
+                    ok[u] = ok[u] && c[u] != (int32_t)r;
+                }
+                Cf<V, SPL> xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    unpf(x_ro ? __ldg(xl + (int64_t)c[u] * L + l) : __ldcg(xl + (int64_t)c[u] * L + l),
+                         xv[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (decltype(first)::value && u == 0) {
+#pragma unroll
+                        for (int j = 0; j < SPL; ++j) {
+                            sm.re[j] = ok[0] ? xv[0].re[j] : 0.0;
+                            sm.im[j] = ok[0] ? xv[0].im[j] : 0.0;
+                        }
+                    } else if (ok[u]) {
+#pragma unroll
+                        for (int j = 0; j < SPL; ++j) {
+                            sm.re[j] += xv[u].re[j];
+                            sm.im[j] += xv[u].im[j];
+                        }
+                    }
+                }
+            };
+            if (w > 0) {
+                group(0, std::true_type{});
+                for (int k = 4; k < w; k += 4) group(k, std::false_type{});
+            }
+            if (sc) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    const V sv = sc[l * SPL + j];
+                    p.re[j] *= sv;
+                    p.im[j] *= sv;
+                    if (x_ro) {
+                        sm.re[j] *= sv;
+                        sm.im[j] *= sv;
+                        y.re[j] *= sv;
+                        y.im[j] *= sv;
+                    }
+                }
+            }
+            const V gd = f.zero_diag     ? 0.0
+                         : tm.gd_sel == 2 ? xor_sign(__ldg(f.diag2 + r), tm.gd_sign)
+                         : tm.gd_sel == 1 ? xor_sign(d, tm.gd_sign)
+                                          : tm.gamma * d;
+            Cf<V, SPL> o;
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                V re = zz.re[j], im = zz.im[j];
+                if (!f.zero_diag) {
+                    re = fma(gd, y.im[j], re);            // y holds x_r here
+                    im = fma(-gd, y.re[j], im);
+                }
+                re = fma(tm.gh, sm.im[j], re);
+                im = fma(-tm.gh, sm.re[j], im);
+                o.re[j] = fma(tm.c_hi, p.re[j], re);
+                o.im[j] = fma(tm.c_hi, p.im[j], im);
+            }
+            return o;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
     for (int k = 0; k < w; k += 4) {

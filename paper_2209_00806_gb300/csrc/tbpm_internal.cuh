@@ -113,6 +113,12 @@ struct TermArgs {
     int fixed_width;      // slices all this wide: base = 32 q w, no slice_ptr loads
     double h_uniform;
     float h_uniform_f;
+    // FP64 one-value form: out = z + (-i)(gd x + gh s) + c psi with s the sum of
+    // the neighbours, gd = gamma d, gh = gamma h_uniform (rounded once, here)
+    double gh;
+    const double *gdiag;  // gamma d already formed (d or 2d) when |gamma| is 1 or 2, else nullptr
+    unsigned long long gdiag_sign;  // sign bit applied to gdiag (gamma < 0)
+    int zero_diag;        // every onsite energy is zero: no diagonal term
     // staged-gather variant: halo lists and 16-bit column positions
     const int64_t *halo_ptr;
     const int32_t *halo_rows;
@@ -269,10 +275,28 @@ struct FusedTerm {
     int x, z, out, final_term;
     double c_hi, c_lo, gamma;
     float c_hi_f, c_lo_f, gamma_f;
+    // FP64 one-value form (cluster stepping): gh = gamma h_uniform; gamma d
+    // is d (gd_sel 1) or 2d (gd_sel 2) with the sign bit gd_sign when
+    // |gamma| is 1 or 2, else gamma * d (gd_sel 0)
+    double gh;
+    int gd_sel;
+    unsigned long long gd_sign;
 };
+
+#ifdef __CUDACC__
+// v with its sign bit flipped by sgn (0 or 1 << 63): an integer operation,
+// off the FP64 pipe
+__device__ __forceinline__ double xor_sign(double v, unsigned long long sgn)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)sgn);
+}
+#endif
 
 struct FusedArgs {
     SellView H;
+    int uniform;                // FP64 one-value form (terms' gh, gd_sel)
+    int zero_diag;
+    const double *diag2;        // 2 d (FP64 one-value form) or nullptr
     const void *psi;            // current state (read only during the step)
     const void *psi0;
     void *bufs[3];
@@ -389,7 +413,11 @@ struct BuildOutput {
     int halo_max = 0;                // longest list
     int halo_ent_max = 0;            // most packed entries of one block
     int64_t halo_total = 0;          // entries of all lists
+    double *diag2_64 = nullptr;      // 2 d (FP64 one-value form; built on first use)
 };
+
+// 2 d for the FP64 one-value form's interior terms (gamma = +-2), exact.
+int build_diag2(BuildOutput &b, cudaStream_t st, std::string &msg);
 
 // Packed copy of the values of one precision for the pipelined kernel
 // (built on first use).

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tbpm_internal.cuh"
 
 namespace tbpm {
@@ -241,54 +243,130 @@ __global__ void __launch_bounds__(1024) k_term_tma(TermArgs a, int tile_rows, in
         const V *valp = sval + (es - eb) + (lr % kSliceRows);
         const V d = sdiag[lr];
         unp(sx[lr * L + l], y);
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
         const Lane *xg = reinterpret_cast<const Lane *>(a.x);
-        for (int kk = 0; kk < w; kk += 4) {
-            int32_t c[4];
-            V h[4];
+        const V *sc = CoefT<V>::scale(a);
+        if (sc) sc += (int64_t)a.chunk_sample[r / kChunkRows] * B;
+        Cx<V, SPL> o;
+        bool summed = false;
+        if constexpr (sizeof(V) == 8) {
+            if (a.uniform) {
+                // FP64 one-value form, as in the per-term kernels: the
+                // neighbours summed in stored order, then
+                // fma(c, psi, fma(gh, s, fma(gd, x_r, z)))
+                summed = true;
+                Cx<V, SPL> sm;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool ok = kk + u < w;
-                c[u] = ok ? colp[(kk + u) * kSliceRows] : (int32_t)r;
-                h[u] = ok ? valp[(kk + u) * kSliceRows] : (V)0;
-            }
-            Cx<V, SPL> xv[4];
+                for (int j = 0; j < SPL; ++j) { sm.re[j] = 0; sm.im[j] = 0; }
+                auto group = [&](int kk, auto first) {
+                    int32_t c[4];
+                    bool ok[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) unp(__ldg(xg + (int64_t)c[u] * L + l), xv[u]);
+                    for (int u = 0; u < 4; ++u) {
+                        ok[u] = kk + u < w;
+                        c[u] = ok[u] ? colp[(kk + u) * kSliceRows] : (int32_t)r;
+                        ok[u] = ok[u] && c[u] != (int32_t)r;     // padding: the own row
+                    }
+                    Cx<V, SPL> xv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (kk + u < w) {
+                    for (int u = 0; u < 4; ++u) unp(__ldg(xg + (int64_t)c[u] * L + l), xv[u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (decltype(first)::value && u == 0) {
+#pragma unroll
+                            for (int j = 0; j < SPL; ++j) {
+                                sm.re[j] = ok[0] ? xv[0].re[j] : 0.0;
+                                sm.im[j] = ok[0] ? xv[0].im[j] : 0.0;
+                            }
+                        } else if (ok[u]) {
+#pragma unroll
+                            for (int j = 0; j < SPL; ++j) {
+                                sm.re[j] += xv[u].re[j];
+                                sm.im[j] += xv[u].im[j];
+                            }
+                        }
+                    }
+                };
+                if (w > 0) {
+                    group(0, std::true_type{});
+                    for (int kk = 4; kk < w; kk += 4) group(kk, std::false_type{});
+                }
+                if (sc) {
 #pragma unroll
                     for (int j = 0; j < SPL; ++j) {
-                        y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
-                        y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                        const V sv = sc[l * SPL + j];
+                        p.re[j] *= sv;
+                        p.im[j] *= sv;
+                        if (a.x_is_psi) {
+                            sm.re[j] *= sv;
+                            sm.im[j] *= sv;
+                            y.re[j] *= sv;
+                            y.im[j] *= sv;
+                        }
                     }
+                }
+                const V gd = a.zero_diag ? 0.0
+                             : a.gdiag   ? xor_sign(__ldg(a.gdiag + r), a.gdiag_sign)
+                                         : a.gamma * d;
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    V re = zz.re[j], im = zz.im[j];
+                    if (!a.zero_diag) {
+                        re = fma(gd, y.im[j], re);            // y holds x_r here
+                        im = fma(-gd, y.re[j], im);
+                    }
+                    re = fma(a.gh, sm.im[j], re);
+                    im = fma(-a.gh, sm.re[j], im);
+                    o.re[j] = fma(ch, p.re[j], re);
+                    o.im[j] = fma(ch, p.im[j], im);
                 }
             }
         }
-        const V *sc = CoefT<V>::scale(a);
-        if (sc) {
-            sc += (int64_t)a.chunk_sample[r / kChunkRows] * B;
+        if (!summed) {
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
+            for (int kk = 0; kk < w; kk += 4) {
+                int32_t c[4];
+                V h[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = kk + u < w;
+                    c[u] = ok ? colp[(kk + u) * kSliceRows] : (int32_t)r;
+                    h[u] = ok ? valp[(kk + u) * kSliceRows] : (V)0;
+                }
+                Cx<V, SPL> xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) unp(__ldg(xg + (int64_t)c[u] * L + l), xv[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (kk + u < w) {
+#pragma unroll
+                        for (int j = 0; j < SPL; ++j) {
+                            y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
+                            y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                        }
+                    }
+                }
+            }
+            if (sc) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    const V sv = sc[l * SPL + j];
+                    p.re[j] *= sv;
+                    p.im[j] *= sv;
+                    if (a.x_is_psi) { y.re[j] *= sv; y.im[j] *= sv; }
+                }
+            }
 #pragma unroll
             for (int j = 0; j < SPL; ++j) {
-                const V sv = sc[l * SPL + j];
-                p.re[j] *= sv;
-                p.im[j] *= sv;
-                if (a.x_is_psi) { y.re[j] *= sv; y.im[j] *= sv; }
+                V re = fma(g, y.im[j], zz.re[j]);
+                V im = fma(-g, y.re[j], zz.im[j]);
+                if (sizeof(V) == 4) {
+                    re = fma(cl, p.re[j], re);
+                    im = fma(cl, p.im[j], im);
+                }
+                o.re[j] = fma(ch, p.re[j], re);
+                o.im[j] = fma(ch, p.im[j], im);
             }
-        }
-        Cx<V, SPL> o;
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-            V re = fma(g, y.im[j], zz.re[j]);
-            V im = fma(-g, y.re[j], zz.im[j]);
-            if (sizeof(V) == 4) {
-                re = fma(cl, p.re[j], re);
-                im = fma(cl, p.im[j], im);
-            }
-            o.re[j] = fma(ch, p.re[j], re);
-            o.im[j] = fma(ch, p.im[j], im);
         }
         reinterpret_cast<Lane *>(a.out)[r * L + l] = pk(o);
         __syncthreads();          // stage s is free again

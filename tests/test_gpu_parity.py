@@ -206,15 +206,27 @@ def test_gpu_fp32_norm_carry_renormalises(tb):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_gpu_uniform_hopping_form_is_exact(tb, prec):
-    """Pristine-hopping lattices take the one-value form (no value loads);
-    it must give the very same states as the general form."""
+@pytest.mark.parametrize("backward", [False, True])
+def test_gpu_uniform_hopping_form(tb, prec, backward):
+    """Lattices with one hopping value take the one-value form (no value
+    loads).  FP32: the very same states as the general form.  FP64: the
+    neighbours are summed before the one multiply by gamma h and gamma d is
+    folded into the combine (2 FP64 operations fewer per state and row), so
+    it agrees with the general form to rounding; forward and backward
+    (gamma < 0: the sign-flipped 2 d) against the oracle."""
     smp = lattice.graphene(30, 29, pbc=True, seed=3, onsite_w=1.0, vacancy_frac=0.03)
     th = rng.phases(14, 4, smp.n_orb)
-    a, _, pa, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec)
-    b, _, pb, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, bflags=16)
-    assert np.array_equal(pa, pb) and np.array_equal(a, b)
+    fl = 16 if backward else 0
+    a, _, pa, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, flags=fl)
+    b, _, pb, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, flags=fl, bflags=16)
+    if prec == 1:
+        assert np.array_equal(pa, pb) and np.array_equal(a, b)
+    else:
+        assert np.max(np.abs(pa - pb)) < 1e-13 and np.max(np.abs(a - b)) < 1e-13
+        assert not np.array_equal(pa, pb)            # the summed form did run
     ref = run_oracle(smp, 9.5, th, 40)
+    if backward:
+        ref = np.conj(ref)                          # C(-t) = C(t)*
     assert np.max(np.abs(a[0] - ref)) < (1e-10 if prec == 0 else 2e-5)
 
 
