@@ -63,9 +63,6 @@ def parse():
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--force-e2e", action="store_true",
-                    help="tbg: the end-to-end leg also above 600 nm (the 1.2 um bond list is "
-                         "90 GB of pinned host memory)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shape (profiling runs)")
@@ -501,24 +498,25 @@ def run_gb300(args):
             r64 = runs[N.TBPM_FP64]
             en, d32 = r0["res"]
             _, d64 = r64["res"]
-            # the FP64 term is bound by GB300's FP64 pipe: 10 flops per lane-row
-            # (diagonal 2, combine 8) plus 4 per stored entry, for the mean group
-            # width of one launch; the peak is the FP64 FMA rate measured here
-            # by the library's probe
+            # the FP64 term is bound by GB300's FP64 pipe, which issues an add,
+            # a multiply or an FMA at one rate: the library's count of the
+            # FP64 operations of one interior launch (tbpm_stats.ops_term)
+            # against the FMA rate measured here by the library's probe, in
+            # operations (one FMA = one operation = 2 flops)
             st64 = r64["stats"]
-            s_eff = S / max(1, st64["n_groups"])
-            flops = float((smp.n_orb * 10 + st64["nnz_true"] * 4) * s_eff)
+            ops = float(st64["ops_term"])
             alu = None
             if r64["ms_term"]:
-                ach = flops / (r64["ms_term"] * 1e-3) / 1e9
+                ach = ops / (r64["ms_term"] * 1e-3) / 1e9
                 with ClockSampler(local) as pclk:
                     tf, pms = N.tbpm_fp64_fma_rate(local, 400000)
-                peak = tf * 1e3
-                alu = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
-                       "frac": ach / peak, "traffic": None,
+                peak = tf * 1e3 / 2
+                alu = {"bound": "alu", "achieved": ach, "peak": peak,
+                       "unit": "G FP64 ops/s", "frac": ach / peak, "traffic": None,
                        "peak_source": f"measured: FP64 FMA probe (tbpm_fp64_fma_rate, "
-                                      f"{pms:.0f} ms, SM clock {pclk.summary().get('sm_mhz')} MHz)",
-                       "flops_per_launch": flops}
+                                      f"{pms:.0f} ms, SM clock {pclk.summary().get('sm_mhz')} MHz, "
+                                      f"{tf * 1e3:.1f} GFLOP/s)",
+                       "ops_per_launch": ops}
             line["fp64_form"] = {"value": vals[N.TBPM_FP64], "ms_per_step": r64["ms"] / args.steps,
                                  "dtype": "f64", "roofline": roofline(r64, "fp64"),
                                  "roofline_alu": alu,
@@ -531,6 +529,40 @@ def run_gb300(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def host_mem_available():
+    """MemAvailable of the host in bytes (Linux), or None."""
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def pinned_copy(t):
+    """A page-locked host copy of the device tensor t, and the call that
+    unpins it: an exact-size numpy buffer registered with cudaHostRegister
+    (the caching pinned allocator would round a 30 GB request up to
+    32 GiB), filled by one device-to-host copy."""
+    import torch
+    a = np.empty(t.numel(), dtype=torch.empty(0, dtype=t.dtype).numpy().dtype)
+    h = torch.from_numpy(a)
+    cudart = torch.cuda.cudart()
+    nbytes = h.numel() * h.element_size()
+    if nbytes:
+        rc = cudart.cudaHostRegister(h.data_ptr(), nbytes, 0)
+        if int(rc) != 0:
+            raise RuntimeError(f"cudaHostRegister of {nbytes} bytes failed ({rc})")
+    h.copy_(t.reshape(-1))
+    h = h.view(t.shape)
+
+    def unpin():
+        if nbytes:
+            cudart.cudaHostUnregister(a.ctypes.data)
+    return h, unpin
 
 
 def run_tbg(args):
@@ -588,11 +620,18 @@ def run_tbg(args):
     torch.cuda.synchronize(dev)
     first_build_s = time.perf_counter() - tb0
     st0 = prop.stats()
+    # page-locked host copies of the bonds and phases for the end-to-end leg
+    # (at 1.2 um: 90.6 GB of bonds and 7 GB of phases)
+    h_in, e2e_skip = None, None
+    if not args.no_e2e:
+        need = sum(x.numel() * x.element_size() for x in (ds.hop_i, ds.hop_j, ds.hop_v, theta))
+        avail = host_mem_available()
+        if avail is not None and need > 0.6 * avail:
+            e2e_skip = (f"needs {need / 1e9:.1f} GB of page-locked host memory, "
+                        f"{avail / 1e9:.1f} GB available")
+        else:
+            h_in = [pinned_copy(x) for x in (ds.hop_i, ds.hop_j, ds.hop_v, theta)]
     if not rebuild:
-        h_bonds = None
-        if not args.no_e2e and args.force_e2e:
-            h_bonds = (ds.hop_i.cpu().pin_memory(), ds.hop_j.cpu().pin_memory(),
-                       ds.hop_v.cpu().pin_memory())
         del ds
         torch.cuda.empty_cache()
     # above 600 nm the launch shape is fixed (the autotuner's candidates
@@ -635,18 +674,12 @@ def run_tbg(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
-    # end to end through the C ABI from pinned host buffers (bonds, phases in;
-    # the averaged correlation and the norms out), flakes up to 600 nm: the
-    # 1.2 um bond list alone is 90 GB of host memory
+    # end to end through the C ABI from the page-locked host buffers (bonds,
+    # phases in; the averaged correlation and the norms out): every step
+    # copies the whole bond list to the device and builds from it
     e2e = None
-    if not args.no_e2e and (rebuild or args.force_e2e):
-        if rebuild:
-            h_hi = ds.hop_i.cpu().pin_memory()
-            h_hj = ds.hop_j.cpu().pin_memory()
-            h_hv = ds.hop_v.cpu().pin_memory()
-        else:
-            h_hi, h_hj, h_hv = h_bonds
-        h_th = theta.cpu().pin_memory()
+    if h_in is not None:
+        h_hi, h_hj, h_hv, h_th = (h for h, _ in h_in)
         h_c = torch.empty((1, NT + 1), dtype=torch.complex128).pin_memory()
 
         def host_step():
@@ -673,7 +706,9 @@ def run_tbg(args):
                "note": "whole step: H2D of bonds and phases, build, propagation, state "
                        "average and DOS"}
         del h_hi, h_hj, h_hv, h_th
-        h_bonds = None
+        for h, unpin in h_in:
+            unpin()
+        h_in = None
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
         if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm = peaks.get("hbm_gbs") or 6800.0
@@ -713,6 +748,8 @@ def run_tbg(args):
             "fp32_max_norm_drift": acc["drift"],
             "gpu_launches": int(acc["launches"]), "clocks": clk.summary(),
             "dos_integral": float(np.sum(d) * (2 * s / 4096))}
+    if e2e_skip:
+        line["e2e_skipped"] = e2e_skip
     print(json.dumps(line), flush=True)
     prop.close()
     return 0
@@ -791,18 +828,18 @@ def run_differentiable(args):
         if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm = peaks.get("hbm_gbs") or 6800.0
     tf, _ = N.tbpm_fp64_fma_rate(local, 400000)
-    # one launch advances one state group: the mean group width (3 states run
-    # as 2 + 1), as bytes_term counts it
-    s_eff = S / max(1, st["n_groups"])
-    flops = float((smp.n_orb * 10 + st["nnz_true"] * 4) * s_eff)
+    # one launch advances one state group: the library's operation count is
+    # for the mean group width (3 states run as 2 + 1), as bytes_term is
+    ops = float(st["ops_term"])
     ms_t = st["ms_term_avg"]
-    roof = {"bound": "alu", "achieved": flops / (ms_t * 1e-3) / 1e9, "peak": tf * 1e3,
-            "unit": "GFLOP/s", "frac": flops / (ms_t * 1e-3) / 1e9 / (tf * 1e3),
+    peak = tf * 1e3 / 2
+    roof = {"bound": "alu", "achieved": ops / (ms_t * 1e-3) / 1e9, "peak": peak,
+            "unit": "G FP64 ops/s", "frac": ops / (ms_t * 1e-3) / 1e9 / peak,
             "traffic": None, "kernel": "FP64 interior Clenshaw term of the forward pass",
-            "peak_source": "measured: FP64 FMA probe (tbpm_fp64_fma_rate)",
+            "peak_source": "measured: FP64 FMA probe (tbpm_fp64_fma_rate), one FMA = one op",
             "hbm": {"achieved": st["bytes_term"] / (ms_t * 1e-3) / 1e9, "peak": hbm,
                     "frac": st["bytes_term"] / (ms_t * 1e-3) / 1e9 / hbm},
-            "ms_per_launch": ms_t, "flops_per_launch": flops,
+            "ms_per_launch": ms_t, "ops_per_launch": ops,
             "algorithmic_bytes_per_launch": st["bytes_term"]}
     adj_ms = statistics.median(phases["adj"])
     adj_units = smp.n_orb * S * NT * (4 * M - 5)

@@ -119,6 +119,14 @@ typedef struct tbpm_stats {
     double max_norm_drift;   /* max over steps and states of |<phi|phi> - 1| */
     double lanczos_radius;   /* the build's Lanczos estimate of the spectral radius
                                 of H~ (0 when the Gershgorin bound sufficed) */
+    double ops_term;         /* arithmetic operations of one interior term launch
+                                (an FMA, add or multiply on one real lane is one),
+                                same mean group width as bytes_term: per state
+                                and row with E entries, 6 + 2E for the real
+                                general form (8 + 2E in FP32: the coefficient's
+                                low part), 4 + 2E for the FP64 one-value form
+                                (2 + 2E without a diagonal); complex values 4
+                                per entry */
 } tbpm_stats;
 
 /* Library version, major * 10000 + minor * 100 + patch. */

@@ -77,7 +77,8 @@ class tbpm_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_term_avg", ctypes.c_double),
                 ("ms_final_avg", ctypes.c_double), ("ms_reduce_avg", ctypes.c_double),
                 ("term_launches", ctypes.c_int64), ("bytes_term", ctypes.c_double),
-                ("max_norm_drift", ctypes.c_double), ("lanczos_radius", ctypes.c_double)]
+                ("max_norm_drift", ctypes.c_double), ("lanczos_radius", ctypes.c_double),
+                ("ops_term", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -340,7 +340,7 @@ void tbpm::set_thread_error(const std::string &m) { g_last_error = m; }
 
 // ---------------------------------------------------------------------------
 
-extern "C" int tbpm_version(void) { return 10100; }
+extern "C" int tbpm_version(void) { return 10200; }
 
 extern "C" int tbpm_kernel_binary_version(int *version)
 {
@@ -1460,7 +1460,11 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         S.bytes_term = vb + (double)c->H.nnz_true * entry + (double)c->n_orb * valb;
         if (halo_used)
             S.bytes_term += 4.0 * (double)c->H.halo_total + 8.0 * (double)(c->H.n_rows / kHaloRows + 1);
-
+        // arithmetic of the same launch (see tbpm_stats)
+        double per_row = fp32 ? 8.0 : 6.0, per_entry = c->H.cplx ? 4.0 : 2.0;
+        if (!fp32 && c->H.uniform && !c->H.cplx) per_row = c->H.zero_diag ? 2.0 : 4.0;
+        S.ops_term = vb / (4.0 * cs * (double)c->n_orb) *
+                     (per_row * (double)c->n_orb + per_entry * (double)c->H.nnz_true);
     }
     if (profile) {
         float ms = 0.f;

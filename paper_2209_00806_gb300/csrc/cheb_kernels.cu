@@ -466,12 +466,15 @@ __device__ __forceinline__ int64_t block_in_order(const TermArgs &a)
 // FP32: at most 40 registers for 16-byte lanes and 64 for the wide lanes
 // (16 blocks of 64 threads per SM, without spills; the 85-register bound
 // before was 5 % slower per term) -- the kernel is latency-bound, so
-// residency matters; FP64: unconstrained.
+// residency matters; FP64: 64 registers for 16-byte lanes, 85 for the wide
+// lanes (the one-value form's summed path and the general path share the
+// kernel: uncapped, the pair took 94 registers and halved the resident
+// warps).
 // Thread t works on row t / (L RS), lane (t / RS) % L, part t % RS.  Rows are
 // a multiple of 1024, so a warp never straddles the last row (the part
 // shuffles see full warps).
 template <typename V, int L, int SPL, bool CX, int RS>
-__global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 4) : 1) k_term(TermArgs a)
+__global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 4) : (SPL == 1 ? 4 : 3)) k_term(TermArgs a)
 {
     const int64_t t = block_in_order(a) * blockDim.x + threadIdx.x;
     const int64_t r = t / (L * RS);

@@ -217,13 +217,16 @@ def test_gpu_uniform_hopping_form(tb, prec, backward):
     smp = lattice.graphene(30, 29, pbc=True, seed=3, onsite_w=1.0, vacancy_frac=0.03)
     th = rng.phases(14, 4, smp.n_orb)
     fl = 16 if backward else 0
-    a, _, pa, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, flags=fl)
-    b, _, pb, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, flags=fl, bflags=16)
+    a, sa, pa, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, flags=fl)
+    b, sb, pb, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, flags=fl, bflags=16)
+    n, nnz = smp.n_orb, sa["nnz_true"]
     if prec == 1:
         assert np.array_equal(pa, pb) and np.array_equal(a, b)
+        assert sa["ops_term"] == sb["ops_term"] == 4 * (8 * n + 2 * nnz)
     else:
         assert np.max(np.abs(pa - pb)) < 1e-13 and np.max(np.abs(a - b)) < 1e-13
         assert not np.array_equal(pa, pb)            # the summed form did run
+        assert sa["ops_term"] == 4 * (4 * n + 2 * nnz) and sb["ops_term"] == 4 * (6 * n + 2 * nnz)
     ref = run_oracle(smp, 9.5, th, 40)
     if backward:
         ref = np.conj(ref)                          # C(-t) = C(t)*
