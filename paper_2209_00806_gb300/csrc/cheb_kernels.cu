@@ -193,8 +193,8 @@ template <> struct Val2<float> { typedef float2 type; };
 // neighbours are added first, s = x_k1 + x_k2 + ... in stored order, and
 // gamma enters through gd = gamma d_r and gh = gamma h:
 //   out = z + (-i)(gd x_r + gh s) + c psi,
-// evaluated per component as fma(c, psi, fma(gh, s, fma(gd, x_r, z))) with
-// the signs of (-i).  That is 2(E-1) adds and 6 FMAs per state and row for E
+// evaluated per component as fma(gh, s, fma(gd, x_r, fma(c, psi, z))) with
+// the signs of (-i): the own-row product first, the neighbours last.  That is 2(E-1) adds and 6 FMAs per state and row for E
 // entries (4 FMAs without a diagonal), against 6 + 2E operations when the
 // product is formed entry by entry; GB300 runs the FP64 form at its FP64
 // instruction rate, so the count sets its time.  (The FP32 form, bound by
@@ -218,15 +218,14 @@ __device__ __forceinline__ Cv<double, SPL> combine_sum(const TermArgs &a, double
     Cv<double, SPL> o;
 #pragma unroll
     for (int j = 0; j < SPL; ++j) {
-        double re = zz.re[j], im = zz.im[j];
+        double re = fma(ch, p.re[j], zz.re[j]);
+        double im = fma(ch, p.im[j], zz.im[j]);
         if (!a.zero_diag) {
             re = fma(gd, xo.im[j], re);
             im = fma(-gd, xo.re[j], im);
         }
-        re = fma(gh, s.im[j], re);
-        im = fma(-gh, s.re[j], im);
-        o.re[j] = fma(ch, p.re[j], re);
-        o.im[j] = fma(ch, p.im[j], im);
+        o.re[j] = fma(gh, s.im[j], re);
+        o.im[j] = fma(-gh, s.re[j], im);
     }
     return o;
 }

@@ -27,6 +27,28 @@ namespace cg = cooperative_groups;
 namespace tbpm {
 namespace {
 
+// Address of `p` (this block's shared memory) in the shared::cluster
+// window of block `rank`, and a 16-byte load through that window.
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, int rank)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ double2 ld_cluster(uint32_t addr)
+{
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr));
+    return v;
+}
+
+constexpr uint32_t kNoEntry = 0xffffffffu;
+
+// MAXW: the widest row the launch allows (its gather addresses stay in
+// registers: 4 for graphene-like lattices, kClusterMaxW otherwise).
+template <int MAXW>
 __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
 {
     cg::cluster_group cl = cg::this_cluster();
@@ -39,12 +61,10 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
     double2 *vec = reinterpret_cast<double2 *>(sm);                  // [4][R]
     int32_t *ent = reinterpret_cast<int32_t *>(vec + 4 * R);         // [W][R] owner << 16 | local
     double *sval = reinterpret_cast<double *>(ent + a.max_w * R);    // [W][R] (general values)
-    __shared__ double2 *remote[16];
     __shared__ double part[2][3];
     __shared__ double red[32][3];
     __shared__ FusedTerm tab[3 * kClusterMaxTerms];
 
-    if (t < K) remote[t] = cl.map_shared_rank(vec, t);
     for (int i = t; i < 3 * a.J; i += blockDim.x)
         tab[i] = a.terms[(i / a.J) * kMaxTerms + i % a.J];
     // this row's entries, as (owning block, local row) pairs
@@ -69,6 +89,18 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
     for (int b = 0; b < 3; ++b)
         vec[(1 + b) * R + t] = b == a.cur0 ? a.bufs[b][r] : make_double2(0.0, 0.0);
     cl.sync();
+    // gathered entries' shared::cluster addresses in x buffer 0 (a buffer
+    // is R rows further on), fixed for the launch; kNoEntry for padding
+    // (one-value form)
+    uint32_t gsrc[MAXW];
+#pragma unroll
+    for (int k = 0; k < MAXW; ++k) {
+        gsrc[k] = kNoEntry;
+        if (k < w) {
+            const int32_t e = ent[k * R + t];
+            if (e >= 0) gsrc[k] = cluster_addr(vec + (e & 0xffff), e >> 16);
+        }
+    }
 
     int cur = a.cur0;
     bool pending = false;                    // a cluster barrier arrived at, not yet waited on
@@ -81,55 +113,59 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
             const double2 p = vec[(1 + cur) * R + t];
             double2 zz = make_double2(0.0, 0.0);
             if (tm.z >= 0) zz = vec[(1 + tm.z) * R + t];
-            if (pending) cl.barrier_wait();      // the gathered vector is complete
-            pending = false;
+            const int xoff = xb * R;
+            const uint32_t xoff_b = (uint32_t)xoff * (uint32_t)sizeof(double2);
             double2 o;
             if (a.uniform) {
-                // the one-value form of the per-term kernels: the neighbours
-                // summed in stored order (padding, -1, only after a row's
-                // entries), then fma(c, psi, fma(gh, s, fma(gd, x_r, z)))
-                double2 s = make_double2(0.0, 0.0);
-                if (w > 0) {
-                    const int32_t e = ent[t];
-                    if (e >= 0) s = remote[e >> 16][xb * R + (e & 0xffff)];
+                // the one-value form of the per-term kernels: neighbours summed
+                // in stored order (padding only after a row's entries), then
+                // fma(gh, s, fma(gd, x_r, fma(c, psi, z))) -- whose first
+                // product needs nothing of this term's x, so it runs before
+                // the barrier wait
+                double re = fma(tm.c_hi, p.x, zz.x);
+                double im = fma(tm.c_hi, p.y, zz.y);
+                if (pending) cl.barrier_wait();  // the gathered vector is complete
+                pending = false;
+                double2 sm = make_double2(0.0, 0.0);
+                if (gsrc[0] != kNoEntry) sm = ld_cluster(gsrc[0] + xoff_b);
+#pragma unroll
+                for (int k = 1; k < MAXW; ++k) {
+                    if (k < w && gsrc[k] != kNoEntry) {
+                        const double2 x = ld_cluster(gsrc[k] + xoff_b);
+                        sm.x += x.x;
+                        sm.y += x.y;
+                    }
                 }
-                for (int k = 1; k < w; ++k) {
-                    const int32_t e = ent[k * R + t];
-                    if (e < 0) continue;
-                    const double2 x = remote[e >> 16][xb * R + (e & 0xffff)];
-                    s.x += x.x;
-                    s.y += x.y;
-                }
-                double re = zz.x, im = zz.y;
                 if (!a.zero_diag) {
                     const double gd = tm.gd_sel == 2 ? xor_sign(d2, tm.gd_sign)
                                     : tm.gd_sel == 1 ? xor_sign(d, tm.gd_sign)
                                                      : tm.gamma * d;
-                    const double2 xo = vec[xb * R + t];
+                    const double2 xo = vec[xoff + t];
                     re = fma(gd, xo.y, re);
                     im = fma(-gd, xo.x, im);
                 }
-                re = fma(tm.gh, s.y, re);
-                im = fma(-tm.gh, s.x, im);
-                o.x = fma(tm.c_hi, p.x, re);
-                o.y = fma(tm.c_hi, p.y, im);
+                o.x = fma(tm.gh, sm.y, re);
+                o.y = fma(-tm.gh, sm.x, im);
             } else {
+                if (pending) cl.barrier_wait();
+                pending = false;
                 // y = H~ x in the plain kernel's order: diagonal, then the entries
                 // (a zero diagonal contributes only signed zeros: skipped, the
                 // sums stay equal to the plain kernel's)
                 double2 y = make_double2(0.0, 0.0);
                 if (!a.zero_diag) {
-                    y = vec[xb * R + t];
+                    y = vec[xoff + t];
                     y.x *= d;
                     y.y *= d;
                 }
-                for (int k = 0; k < w; ++k) {
-                    const int32_t e = ent[k * R + t];
-                    if (e < 0) continue;
-                    const double h = sval[k * R + t];
-                    const double2 x = remote[e >> 16][xb * R + (e & 0xffff)];
-                    y.x = fma(h, x.x, y.x);
-                    y.y = fma(h, x.y, y.y);
+#pragma unroll
+                for (int k = 0; k < MAXW; ++k) {
+                    if (k < w) {
+                        const double h = sval[k * R + t];
+                        const double2 x = ld_cluster(gsrc[k] + xoff_b);
+                        y.x = fma(h, x.x, y.x);
+                        y.y = fma(h, x.y, y.y);
+                    }
                 }
                 const double re = fma(tm.gamma, y.y, zz.x);
                 const double im = fma(-tm.gamma, y.x, zz.y);
@@ -199,8 +235,8 @@ int cluster_blocks_for(int64_t n_rows, int max_w, int uniform)
     static int best16 = -1;
     if (best16 < 0) {
         best16 = 0;
-        if (cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                 1) == cudaSuccess) {
+        if (cudaFuncSetAttribute(k_cluster_steps<kClusterMaxW>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at;
             at.id = cudaLaunchAttributeClusterDimension;
@@ -213,9 +249,11 @@ int cluster_blocks_for(int64_t n_rows, int max_w, int uniform)
             cfg.attrs = &at;
             cfg.numAttrs = 1;
             int n = 0;
-            cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 160 * 1024);
-            if (cudaOccupancyMaxActiveClusters(&n, k_cluster_steps, &cfg) == cudaSuccess && n >= 1)
+            cudaFuncSetAttribute(k_cluster_steps<kClusterMaxW>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            if (cudaOccupancyMaxActiveClusters(&n, k_cluster_steps<kClusterMaxW>, &cfg) ==
+                    cudaSuccess &&
+                n >= 1)
                 best16 = 1;
         }
         cudaGetLastError();
@@ -230,16 +268,15 @@ int cluster_blocks_for(int64_t n_rows, int max_w, int uniform)
     return fits(8) ? 8 : 0;
 }
 
-cudaError_t launch_cluster_steps(const ClusterArgs &a, int K, cudaStream_t st)
+template <int MAXW>
+cudaError_t launch_cluster_t(const ClusterArgs &a, int K, size_t smem, cudaStream_t st)
 {
-    const int R = a.rows_per_cta;
-    const size_t smem = (size_t)4 * R * sizeof(double2) + (size_t)a.max_w * R * sizeof(int32_t) +
-                        (a.uniform ? 0 : (size_t)a.max_w * R * sizeof(double));
-    cudaError_t e = cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_cluster_steps<MAXW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (K > 8) {
-        e = cudaFuncSetAttribute(k_cluster_steps, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_cluster_steps<MAXW>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -249,12 +286,21 @@ cudaError_t launch_cluster_steps(const ClusterArgs &a, int K, cudaStream_t st)
     at.val.clusterDim.y = 1;
     at.val.clusterDim.z = 1;
     cfg.gridDim = dim3(K);
-    cfg.blockDim = dim3(R);
+    cfg.blockDim = dim3(a.rows_per_cta);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster_steps, a);
+    return cudaLaunchKernelEx(&cfg, k_cluster_steps<MAXW>, a);
+}
+
+cudaError_t launch_cluster_steps(const ClusterArgs &a, int K, cudaStream_t st)
+{
+    const int R = a.rows_per_cta;
+    const size_t smem = (size_t)4 * R * sizeof(double2) + (size_t)a.max_w * R * sizeof(int32_t) +
+                        (a.uniform ? 0 : (size_t)a.max_w * R * sizeof(double));
+    return a.max_w <= 4 ? launch_cluster_t<4>(a, K, smem, st)
+                        : launch_cluster_t<kClusterMaxW>(a, K, smem, st);
 }
 
 }  // namespace tbpm

@@ -114,7 +114,7 @@ __device__ __forceinline__ Cf<V, SPL> fused_row(const FusedArgs &f, const FusedT
         if (f.uniform) {
             // FP64 one-value form, as in the per-term kernels: neighbours
             // summed in stored order (padding -- the own row -- skipped),
-            // then fma(c, psi, fma(gh, s, fma(gd, x_r, z)))
+            // then fma(gh, s, fma(gd, x_r, fma(c, psi, z)))
             Cf<V, SPL> sm;
 #pragma unroll
             for (int j = 0; j < SPL; ++j) { sm.re[j] = 0; sm.im[j] = 0; }
@@ -174,15 +174,14 @@ __device__ __forceinline__ Cf<V, SPL> fused_row(const FusedArgs &f, const FusedT
             Cf<V, SPL> o;
 #pragma unroll
             for (int j = 0; j < SPL; ++j) {
-                V re = zz.re[j], im = zz.im[j];
+                V re = fma(tm.c_hi, p.re[j], zz.re[j]);
+                V im = fma(tm.c_hi, p.im[j], zz.im[j]);
                 if (!f.zero_diag) {
                     re = fma(gd, y.im[j], re);            // y holds x_r here
                     im = fma(-gd, y.re[j], im);
                 }
-                re = fma(tm.gh, sm.im[j], re);
-                im = fma(-tm.gh, sm.re[j], im);
-                o.re[j] = fma(tm.c_hi, p.re[j], re);
-                o.im[j] = fma(tm.c_hi, p.im[j], im);
+                o.re[j] = fma(tm.gh, sm.im[j], re);
+                o.im[j] = fma(-tm.gh, sm.re[j], im);
             }
             return o;
         }

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(1024) k_term_tma(TermArgs a, int tile_rows, in
             if (a.uniform) {
                 // FP64 one-value form, as in the per-term kernels: the
                 // neighbours summed in stored order, then
-                // fma(c, psi, fma(gh, s, fma(gd, x_r, z)))
+                // fma(gh, s, fma(gd, x_r, fma(c, psi, z)))
                 summed = true;
                 Cx<V, SPL> sm;
 #pragma unroll
@@ -309,15 +309,14 @@ __global__ void __launch_bounds__(1024) k_term_tma(TermArgs a, int tile_rows, in
                                          : a.gamma * d;
 #pragma unroll
                 for (int j = 0; j < SPL; ++j) {
-                    V re = zz.re[j], im = zz.im[j];
+                    V re = fma(ch, p.re[j], zz.re[j]);
+                    V im = fma(ch, p.im[j], zz.im[j]);
                     if (!a.zero_diag) {
                         re = fma(gd, y.im[j], re);            // y holds x_r here
                         im = fma(-gd, y.re[j], im);
                     }
-                    re = fma(a.gh, sm.im[j], re);
-                    im = fma(-a.gh, sm.re[j], im);
-                    o.re[j] = fma(ch, p.re[j], re);
-                    o.im[j] = fma(ch, p.im[j], im);
+                    o.re[j] = fma(a.gh, sm.im[j], re);
+                    o.im[j] = fma(-a.gh, sm.re[j], im);
                 }
             }
         }
