@@ -189,10 +189,25 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
                     red[t / 32][2] = v2;
                 }
                 __syncthreads();
-                if (t < 3) {
-                    double s = 0.0;
-                    for (int q = 0; q < (R + 31) / 32; ++q) s += red[q][t];
-                    part[n & 1][t] = s;
+                if (t < 32) {               // warp q's sums in order, loaded at once
+                    const int nq = (R + 31) / 32;
+                    double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+                    if (t < nq) {
+                        w0 = red[t][0];
+                        w1 = red[t][1];
+                        w2 = red[t][2];
+                    }
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                    for (int q = 0; q < nq; ++q) {
+                        s0 += __shfl_sync(0xffffffffu, w0, q);
+                        s1 += __shfl_sync(0xffffffffu, w1, q);
+                        s2 += __shfl_sync(0xffffffffu, w2, q);
+                    }
+                    if (t == 0) {
+                        part[n & 1][0] = s0;
+                        part[n & 1][1] = s1;
+                        part[n & 1][2] = s2;
+                    }
                 }
             }
             cl.barrier_arrive();                 // release this term's writes
@@ -202,23 +217,32 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
         pending = false;
         cur = a.next_cur[cur];
         // block 0 adds the blocks' sums in rank order (they stay in place for
-        // the next two steps, so no further barrier is needed here)
-        if (rank == 0 && t == 0) {
+        // the next two steps, so no further barrier is needed here): lane k
+        // of warp 0 loads block k's, the lanes' values are added in order
+        if (rank == 0 && t < 32) {
+            double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+            if (t < K) {
+                const double *pk = cl.map_shared_rank(&part[n & 1][0], t);
+                w0 = pk[0];
+                w1 = pk[1];
+                w2 = pk[2];
+            }
             double s[3] = {0.0, 0.0, 0.0};
             for (int k = 0; k < K; ++k) {
-                const double *pk = cl.map_shared_rank(&part[n & 1][0], k);
-                s[0] += pk[0];
-                s[1] += pk[1];
-                s[2] += pk[2];
+                s[0] += __shfl_sync(0xffffffffu, w0, k);
+                s[1] += __shfl_sync(0xffffffffu, w1, k);
+                s[2] += __shfl_sync(0xffffffffu, w2, k);
             }
-            a.corr[n] = make_double2(s[0], s[1]);
-            a.norms[n] = s[2];
-            const double ref = *a.norm_ref;
-            const double drift = ref > 0.0 ? fabs(s[2] / ref - 1.0) : s[2];
-            if (!(s[2] == s[2]) || !(s[0] == s[0]) || !(s[1] == s[1]) || s[2] - s[2] != 0.0)
-                atomicOr(a.err, 2);
-            else if (drift > a.hard_bound)
-                atomicOr(a.err, 1);
+            if (t == 0) {
+                a.corr[n] = make_double2(s[0], s[1]);
+                a.norms[n] = s[2];
+                const double ref = *a.norm_ref;
+                const double drift = ref > 0.0 ? fabs(s[2] / ref - 1.0) : s[2];
+                if (!(s[2] == s[2]) || !(s[0] == s[0]) || !(s[1] == s[1]) || s[2] - s[2] != 0.0)
+                    atomicOr(a.err, 2);
+                else if (drift > a.hard_bound)
+                    atomicOr(a.err, 1);
+            }
         }
     }
     a.bufs[cur][r] = vec[(1 + cur) * R + t];
