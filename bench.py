@@ -682,17 +682,30 @@ def run_tbg(args):
         h_hi, h_hj, h_hv, h_th = (h for h, _ in h_in)
         h_c = torch.empty((1, NT + 1), dtype=torch.complex128).pin_memory()
 
+        parts = {"build": 0.0, "states": 0.0, "propagate": 0.0, "correlation_dos": 0.0}
+
         def host_step():
+            t = [time.perf_counter()]
             N.tbpm_build_hamiltonian(prop.ctx, n_orb, None, n_hop, h_hi.data_ptr(),
                                      h_hj.data_ptr(), h_hv.data_ptr(), s, 1, None, N.TBPM_HOST,
                                      bflags)
+            t.append(time.perf_counter())
             N.tbpm_set_phase_states(prop.ctx, S, h_th.data_ptr(), N.TBPM_HOST)
+            torch.cuda.synchronize(dev)
+            t.append(time.perf_counter())
             N.tbpm_propagate(prop.ctx, z, NT, N.TBPM_FP32, None, N.TBPM_HOST, 0)
+            t.append(time.perf_counter())
             N.tbpm_correlation(prop.ctx, h_c.data_ptr(), N.TBPM_HOST)
-            return tb.dos(h_c.numpy()[0], tau, -s, s, 4096)
+            res = tb.dos(h_c.numpy()[0], tau, -s, s, 4096)
+            t.append(time.perf_counter())
+            for k, key in enumerate(parts):
+                parts[key] += t[k + 1] - t[k]
+            return res
 
         host_step()
         torch.cuda.synchronize(dev)
+        for key in parts:
+            parts[key] = 0.0
         t0 = time.perf_counter()
         for _ in range(args.steps):
             host_step()
@@ -703,6 +716,7 @@ def run_tbg(args):
         e2e = {"value": units_per_step * args.steps / dt, "unit": "orbital-Chebyshev-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * dt / args.steps,
+               "ms_parts": {k: 1e3 * v / args.steps for k, v in parts.items()},
                "note": "whole step: H2D of bonds and phases, build, propagation, state "
                        "average and DOS"}
         del h_hi, h_hj, h_hv, h_th

@@ -358,6 +358,13 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
                                         positions and values copied while the current
                                         one computes; FP32 groups of 4 or 8, FP64 of 2
                                         or 4 states, within 224 KB of shared memory */
+#define TBPM_VARIANT_STAGED 4096     /* with TBPM_VARIANT_HALO: one block per 128-row
+                                        block copying its halo, positions and values
+                                        into one shared-memory stage, two blocks per
+                                        SM where the stage allows (one block's copies
+                                        overlap the other's gathers); same shapes as
+                                        TBPM_VARIANT_PIPE, which it takes precedence
+                                        over */
 int tbpm_set_launch_config(tbpm_ctx *ctx, int precision, int max_group, int threads,
                            int variant);
 

@@ -60,6 +60,7 @@ TBPM_VARIANT_SPLIT4 = 256
 TBPM_VARIANT_HALO = 512
 TBPM_VARIANT_PIPE = 1024
 TBPM_VARIANT_CLUSTER = 2048
+TBPM_VARIANT_STAGED = 4096
 
 
 class TbpmError(RuntimeError):

@@ -667,7 +667,7 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
                                   (3 << kVariantFusedTileShift) | kVariantWide | kVariantSplit2 |
                                   kVariantSplit4 | kVariantHalo | kVariantPipe |
-                                  kVariantCluster) ||
+                                  kVariantCluster | kVariantStaged) ||
         ((variant >> kVariantFusedTileShift) & 3) == 3 ||
         ((variant & kVariantSplit2) && (variant & kVariantSplit4)))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
@@ -986,7 +986,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
         if (rc == TBPM_E_UNSUPPORTED) halo = false;
         else if (rc) return fail(c, rc, msg);
     }
-    if (halo && (c->variant[precision] & kVariantPipe) && !c->H.uniform && !c->H.vpack[fp32]) {
+    if (halo && (c->variant[precision] & (kVariantPipe | kVariantStaged)) && !c->H.uniform &&
+        !c->H.vpack[fp32]) {
         std::string msg;
         rc = build_packed_values(c->H, fp32, c->st, msg);
         if (rc) return fail(c, rc, msg);
@@ -1863,6 +1864,8 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                                 kVariantHalo, kVariantZigZag | kVariantHalo,
                                 kVariantHalo | kVariantPipe,
                                 kVariantZigZag | kVariantHalo | kVariantPipe,
+                                kVariantHalo | kVariantStaged,
+                                kVariantZigZag | kVariantHalo | kVariantStaged,
                                 kVariantZigZag | kVariantCluster};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];

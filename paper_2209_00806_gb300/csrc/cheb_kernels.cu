@@ -948,6 +948,106 @@ __device__ __forceinline__ Cv<double, 1> pipe_row_sum(const TermArgs &a, const u
     return combine_sum<1>(a, gd, xo, s, p, zz);
 }
 
+// One row of a staged block: the term for lane l of row r (local row lr)
+// from a shared-memory stage holding the block's halo rows (16-byte lanes,
+// C per row), its packed 16-bit positions and, unless one value serves all,
+// its packed values; w, off: the row's entry count and packed offset.  Four
+// entries a round, their positions in one 8-byte and their values in one
+// 16-byte (FP32) shared load, the next round's read before this round's
+// gathers; same arithmetic and order as term_row.
+template <typename V, int C>
+__device__ __forceinline__ Cv<V, 16 / (2 * sizeof(V))> staged_row(
+    const TermArgs &a, const unsigned char *stg, const PipeShape &ps, int64_t r, int lr, int l,
+    int w, int off, Cv<V, 16 / (2 * sizeof(V))> p, const Cv<V, 16 / (2 * sizeof(V))> &zz, V d,
+    V gd)
+{
+    constexpr int SPL = 16 / (2 * sizeof(V));
+    const unsigned char *xl = stg + l * 16;
+    const uint16_t *lcs = reinterpret_cast<const uint16_t *>(stg + ps.halo_bytes) + off;
+    const V *vs = reinterpret_cast<const V *>(stg + ps.halo_bytes + ps.lcol_bytes) + off;
+    if constexpr (sizeof(V) == 8) {
+        if (a.uniform)                       // FP64 one-value form: neighbours summed first
+            return pipe_row_sum<C>(a, xl, lr, w, lcs, gd, p, zz,
+                                   Coef<V>::scale(a) ? Coef<V>::scale(a) +
+                                       (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL) + l * SPL
+                                                     : nullptr);
+    }
+    Cv<V, SPL> y = ld_halo16<V, C>(xl, lr);
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
+    uint2 pk = make_uint2(0u, 0u);
+    V hv[4] = {0, 0, 0, 0};
+    auto load4 = [&](int k) {
+        const int g4 = (k >> 2) * (4 * kSliceRows);
+        pk = *reinterpret_cast<const uint2 *>(lcs + g4);
+        if (!a.uniform) {
+            if constexpr (sizeof(V) == 4) {
+                const float4 v4 = *reinterpret_cast<const float4 *>(vs + g4);
+                hv[0] = v4.x; hv[1] = v4.y; hv[2] = v4.z; hv[3] = v4.w;
+            } else {
+                const double2 v0 = *reinterpret_cast<const double2 *>(vs + g4);
+                const double2 v1 = *reinterpret_cast<const double2 *>(vs + g4 + 2);
+                hv[0] = v0.x; hv[1] = v0.y; hv[2] = v1.x; hv[3] = v1.y;
+            }
+        }
+    };
+    if (w > 0) load4(0);
+    for (int k = 0; k < w; k += 4) {
+        const int hp[4] = {(int)(pk.x & 0xffff), (int)(pk.x >> 16), (int)(pk.y & 0xffff),
+                           (int)(pk.y >> 16)};
+        V h[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ok[u] = k + u < w;
+            h[u] = hv[u];
+            if (a.uniform) {
+                ok[u] = ok[u] && hp[u] != lr;        // padded slots point at the own row
+                h[u] = Coef<V>::hu(a);
+            }
+        }
+        Cv<V, SPL> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(xl, hp[u]);
+        if (k + 4 < w) load4(k + 4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
+                    y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
+                }
+            }
+        }
+    }
+    const V *sc = Coef<V>::scale(a);
+    if (sc) {
+        sc += (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const V s = sc[l * SPL + j];
+            p.re[j] *= s;
+            p.im[j] *= s;
+            if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
+        }
+    }
+    const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
+    Cv<V, SPL> o;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+        V re = fma(g, y.im[j], zz.re[j]);
+        V im = fma(-g, y.re[j], zz.im[j]);
+        if (sizeof(V) == 4) {
+            re = fma(cl, p.re[j], re);
+            im = fma(cl, p.im[j], im);
+        }
+        o.re[j] = fma(ch, p.re[j], re);
+        o.im[j] = fma(ch, p.im[j], im);
+    }
+    return o;
+}
+
 // Where block j's lists start and how long they are.
 struct PipeMeta {
     int64_t h0;         // first halo row of the block's list
@@ -1069,100 +1169,7 @@ __global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, Pi
         __syncthreads();
         rows_of(m2, g1);                                 // block i+2's rows, used next round
         const unsigned char *stg = sm + (int64_t)(i & 1) * ps.stage_bytes;
-        const unsigned char *xl = stg + l * 16;
-        const uint16_t *lcs = reinterpret_cast<const uint16_t *>(stg + ps.halo_bytes) + off;
-        const V *vs = reinterpret_cast<const V *>(stg + ps.halo_bytes + ps.lcol_bytes) + off;
-        if constexpr (sizeof(V) == 8) {
-            if (a.uniform) {                 // FP64 one-value form: neighbours summed first
-                const Cv<V, SPL> o = pipe_row_sum<C>(a, xl, lr, w, lcs, gd, p, zz,
-                                                     Coef<V>::scale(a) ? Coef<V>::scale(a) +
-                                                         (int64_t)a.chunk_sample[r / kChunkRows] *
-                                                             (C * SPL) + l * SPL
-                                                                       : nullptr);
-                st<V, C, SPL>(a.out, r, l, o);
-                __syncthreads();                         // stage i & 1 may be refilled now
-                hb = nxt;
-                m1 = m2;
-                m2 = m3;
-                w = w1;
-                off = off1;
-                continue;
-            }
-        }
-        Cv<V, SPL> y = ld_halo16<V, C>(xl, lr);
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) { y.re[j] *= d; y.im[j] *= d; }
-        // four positions and values a round; the next round's loaded first
-        uint2 pk = make_uint2(0u, 0u);
-        V hv[4] = {0, 0, 0, 0};
-        auto load4 = [&](int k) {
-            const int g4 = (k >> 2) * (4 * kSliceRows);
-            pk = *reinterpret_cast<const uint2 *>(lcs + g4);
-            if (!a.uniform) {
-                if constexpr (sizeof(V) == 4) {
-                    const float4 v4 = *reinterpret_cast<const float4 *>(vs + g4);
-                    hv[0] = v4.x; hv[1] = v4.y; hv[2] = v4.z; hv[3] = v4.w;
-                } else {
-                    const double2 v0 = *reinterpret_cast<const double2 *>(vs + g4);
-                    const double2 v1 = *reinterpret_cast<const double2 *>(vs + g4 + 2);
-                    hv[0] = v0.x; hv[1] = v0.y; hv[2] = v1.x; hv[3] = v1.y;
-                }
-            }
-        };
-        if (w > 0) load4(0);
-        for (int k = 0; k < w; k += 4) {
-            const int hp[4] = {(int)(pk.x & 0xffff), (int)(pk.x >> 16), (int)(pk.y & 0xffff),
-                               (int)(pk.y >> 16)};
-            V h[4];
-            bool ok[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                ok[u] = k + u < w;
-                h[u] = hv[u];
-                if (a.uniform) {
-                    ok[u] = ok[u] && hp[u] != lr;        // padded slots point at the own row
-                    h[u] = Coef<V>::hu(a);
-                }
-            }
-            Cv<V, SPL> xv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = ld_halo16<V, C>(xl, hp[u]);
-            if (k + 4 < w) load4(k + 4);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (ok[u]) {
-#pragma unroll
-                    for (int j = 0; j < SPL; ++j) {
-                        y.re[j] = fma(h[u], xv[u].re[j], y.re[j]);
-                        y.im[j] = fma(h[u], xv[u].im[j], y.im[j]);
-                    }
-                }
-            }
-        }
-        const V *sc = Coef<V>::scale(a);
-        if (sc) {
-            sc += (int64_t)a.chunk_sample[r / kChunkRows] * (C * SPL);
-#pragma unroll
-            for (int j = 0; j < SPL; ++j) {
-                const V s = sc[l * SPL + j];
-                p.re[j] *= s;
-                p.im[j] *= s;
-                if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
-            }
-        }
-        const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
-        Cv<V, SPL> o;
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-            V re = fma(g, y.im[j], zz.re[j]);
-            V im = fma(-g, y.re[j], zz.im[j]);
-            if (sizeof(V) == 4) {
-                re = fma(cl, p.re[j], re);
-                im = fma(cl, p.im[j], im);
-            }
-            o.re[j] = fma(ch, p.re[j], re);
-            o.im[j] = fma(ch, p.im[j], im);
-        }
+        const Cv<V, SPL> o = staged_row<V, C>(a, stg, ps, r, lr, l, w, off, p, zz, d, gd);
         st<V, C, SPL>(a.out, r, l, o);
         __syncthreads();                                 // stage i & 1 may be refilled now
         hb = nxt;
@@ -1172,6 +1179,105 @@ __global__ void __launch_bounds__(kHaloRows * C) k_term_halo_pipe(TermArgs a, Pi
         off = off1;
     }
     cp_async_wait_group<0>();
+}
+
+// ---- one-stage staged-gather term (TBPM_VARIANT_HALO | TBPM_VARIANT_STAGED) ----
+// One block per 128-row halo block: its halo rows, packed positions and
+// values copied into one shared-memory stage, then its rows computed from it
+// (staged_row, the pipelined kernel's arithmetic).  Without the pipelined
+// kernel's prefetch carried across blocks it fits 64 registers, so two
+// blocks share an SM where the stage allows (~113 KB each): one block's
+// copies, and the dependent loads that address them, overlap the other's
+// gathers, with twice the warps in flight.
+template <typename V, int C>
+__global__ void __launch_bounds__(kHaloRows * C, 2) k_term_staged(TermArgs a, PipeShape ps)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int SPL = 16 / (2 * sizeof(V));
+    constexpr int NT = kHaloRows * C;
+    constexpr int SPB = kHaloRows / kSliceRows;
+    const int tid = threadIdx.x;
+    const int l = tid % C, lr = tid / C;
+    const int64_t hb = block_in_order(a);
+    const int64_t h0 = __ldg(a.halo_ptr + hb);
+    const int H = (int)(__ldg(a.halo_ptr + hb + 1) - h0);
+    const int64_t e0 = __ldg(a.pslice + hb * SPB);
+    const int E = (int)(__ldg(a.pslice + (hb + 1) * SPB) - e0);
+    const unsigned char *xg = reinterpret_cast<const unsigned char *>(a.x);
+    {
+        int32_t g[kPipeIdx];                         // halo rows lr, lr + 128, ...
+#pragma unroll
+        for (int k = 0; k < kPipeIdx; ++k) {
+            const int h = lr + k * kHaloRows;
+            g[k] = h < H ? __ldg(a.halo_rows + h0 + h) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kPipeIdx; ++k) {
+            const int h = lr + k * kHaloRows;
+            if (h < H) cp_async16(sm + (h * C + l) * 16, xg + ((int64_t)g[k] * C + l) * 16);
+        }
+    }
+    unsigned char *lc = sm + ps.halo_bytes;
+    for (int idx = tid; idx < E / 8; idx += NT) cp_async16(lc + idx * 16, a.lcol + e0 + idx * 8);
+    if (!a.uniform) {
+        constexpr int per = 16 / sizeof(V);
+        unsigned char *vs = lc + ps.lcol_bytes;
+        for (int idx = tid; idx < E / per; idx += NT)
+            cp_async16(vs + idx * 16, reinterpret_cast<const V *>(a.vpack) + e0 + idx * per);
+    }
+    cp_async_commit();
+    // own-row streams and the row's entry count, in flight while the stage lands
+    const int64_t r = hb * kHaloRows + lr;
+    Cv<V, SPL> p = ld_ro<V, C, SPL>(a.psi, r, l), zz;
+    if (a.z) {
+        zz = ld<V, C, SPL>(a.z, r, l);
+    } else {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
+    }
+    const V d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+    V gd = 0;
+    if constexpr (sizeof(V) == 8) {
+        if (a.uniform && !a.zero_diag) gd = gdiag_at(a, r);
+    }
+    const int64_t q = r / kSliceRows;
+    const int w = a.fixed_width ? a.fixed_width
+                                : (int)((__ldg(a.H.slice_ptr + q + 1) - __ldg(a.H.slice_ptr + q)) /
+                                        kSliceRows);
+    const int off = (int)(__ldg(a.pslice + q) - e0) + (lr % kSliceRows) * 4;
+    cp_async_wait_group<0>();
+    __syncthreads();
+    const Cv<V, SPL> o = staged_row<V, C>(a, sm, ps, r, lr, l, w, off, p, zz, d, gd);
+    st<V, C, SPL>(a.out, r, l, o);
+}
+
+int g_staged_configured[2][2] = {};   // dynamic shared bytes allowed, [fp32][C/4]
+
+template <typename V, int C>
+cudaError_t launch_staged_t(const TermArgs &a, cudaStream_t st)
+{
+    PipeShape ps;
+    ps.halo_bytes = a.halo_max * C * 16;
+    ps.lcol_bytes = (a.halo_ent_max * 2 + 15) / 16 * 16;
+    ps.val_bytes = a.uniform ? 0 : a.halo_ent_max * (int)sizeof(V);
+    ps.stage_bytes = ps.halo_bytes + ps.lcol_bytes + ps.val_bytes;
+    ps.n_hb = (int)(a.n_rows / kHaloRows);
+    const int smem = ps.stage_bytes;
+    int &conf = g_staged_configured[sizeof(V) == 4][C / 4];
+    if (smem > conf) {
+        cudaError_t e = cudaFuncSetAttribute(k_term_staged<V, C>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        conf = smem;
+    }
+    k_term_staged<V, C><<<(unsigned)ps.n_hb, kHaloRows * C, smem, st>>>(a, ps);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_staged(const TermArgs &a, int fp32, int B, cudaStream_t st)
+{
+    if (fp32) return B == 4 ? launch_staged_t<float, 2>(a, st) : launch_staged_t<float, 4>(a, st);
+    return B == 2 ? launch_staged_t<double, 2>(a, st) : launch_staged_t<double, 4>(a, st);
 }
 
 int g_pipe_configured[2][2] = {};   // dynamic shared bytes allowed, [fp32][C/4]
@@ -1532,6 +1638,12 @@ bool pipe_launchable(int fp32, int B, int halo_max, int ent_max, int uniform)
     return shape && pipe_smem_bytes(fp32, B, halo_max, ent_max, uniform) <= kPipeSmemMax;
 }
 
+bool staged_launchable(int fp32, int B, int halo_max, int ent_max, int uniform)
+{
+    const bool shape = fp32 ? (B == 4 || B == 8) : (B == 2 || B == 4);
+    return shape && pipe_smem_bytes(fp32, B, halo_max, ent_max, uniform) / 2 <= kPipeSmemMax;
+}
+
 bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 {
     // the shared copy (halo rows x B states) must leave room for the
@@ -1543,6 +1655,11 @@ bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    // the one-stage staged kernel, like the pipelined one, keeps rows unsplit
+    if ((a.variant & kVariantHalo) && (a.variant & kVariantStaged) && a.lcol && !a.cplx &&
+        (a.vpack || a.uniform) && !(a.variant & (kVariantSplit2 | kVariantSplit4)) &&
+        staged_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform))
+        return dispatch_staged(a, fp32, B, st);
     // the pipelined kernel does not split rows: with a row split requested,
     // the plain split kernel below keeps the requested summation order
     if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
@@ -1560,6 +1677,15 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
 
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    if ((a.variant & kVariantHalo) && (a.variant & kVariantStaged) && a.lcol && !a.cplx &&
+        (a.vpack || a.uniform) && a.H.col &&
+        staged_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
+        cudaError_t e = dispatch_staged(a, fp32, B, st);   // then the closing reduction
+        if (e != cudaSuccess) return e;
+        TermArgs r = a;
+        r.H.col = nullptr;
+        return dispatch<true>(r, fp32, B, threads, false, st);
+    }
     if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
         (a.vpack || a.uniform) && a.H.col &&
         pipe_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {

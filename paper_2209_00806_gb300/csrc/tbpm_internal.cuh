@@ -72,6 +72,7 @@ constexpr int kVariantSplit4 = 256;     // each row's entries over 4 threads
 constexpr int kVariantHalo = 512;       // gathers from a shared-memory copy of the block's halo
 constexpr int kVariantPipe = 1024;      // with kVariantHalo: persistent, two stages in flight
 constexpr int kVariantCluster = 2048;   // small FP64 samples: all steps in one cluster launch
+constexpr int kVariantStaged = 4096;    // with kVariantHalo: one stage, two blocks per SM
 
 // Staged-gather term kernel: rows per block, and the most other rows one
 // block may reference (16-bit positions; the shared copy is sized by the
@@ -249,6 +250,8 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
 bool halo_launchable(int fp32, int B, bool final_term, int halo_max);
 // The pipelined form serves this shape within the shared-memory budget.
 bool pipe_launchable(int fp32, int B, int halo_max, int ent_max, int uniform);
+// The one-stage staged-gather kernel (kVariantStaged) for that shape.
+bool staged_launchable(int fp32, int B, int halo_max, int ent_max, int uniform);
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 // State average of the correlations (and its adjoint, a broadcast of

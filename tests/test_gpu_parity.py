@@ -168,7 +168,8 @@ def test_gpu_autotune_picks_a_valid_shape(tb):
         p.set_phase_states(th)
         best = p.autotune(Z, precision=1, probe_steps=2)
         assert best["group"] in (2, 4) and best["threads"] in (64, 128, 256)
-        assert best["variant"] in (0, 1, 3, 4, 5, 8, 24, 40, 65, 129, 257, 193, 321)
+        assert best["variant"] in (0, 1, 3, 4, 5, 8, 24, 40, 65, 129, 257, 193, 321, 512, 513,
+                                   1536, 1537, 4608, 4609)
         assert best["ms_per_step"] > 0
         c = p.propagate(Z, 30, 1)
     ref = run_oracle(smp, 9.5, th, 30)
@@ -589,9 +590,10 @@ def test_gpu_halo_variant_is_bit_identical(tb, prec, kind):
     tol = 1e-10 if prec == 0 else 2e-5
     widths = (2, 4, 8) if prec == 0 else (4, 8, 16)
     for B in widths:
-        # halo and halo + pipelined persistent (zig-zag) against the plain wide
-        # kernel; with the row split requested they keep the plain split kernel
-        for plain, variants in ((65, (513, 1537)), (193, (1665,))):
+        # halo, halo + pipelined persistent and halo + one-stage staged (zig-zag)
+        # against the plain wide kernel; with the row split requested they keep
+        # the plain split kernel
+        for plain, variants in ((65, (513, 1537, 4609)), (193, (1665, 4801))):
             c0, _, phi0, _ = run_gpu(tb, smp, s, th, 30, precision=prec, cfg=(B, 64, plain))
             for variant in variants:
                 c1, st, phi1, _ = run_gpu(tb, smp, s, th, 30, precision=prec,
@@ -609,7 +611,7 @@ def test_gpu_halo_variant_twisted_bilayer_20nm_fp32(tb):
     th = rng.phases(93, 8, smp.n_orb)
     c0, _, phi0, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 65))
     ref = oracle.propagate_rows(smp, 12.0, Z, 12, oracle.phase_states(th[:1]))
-    for variant in (513, 1536):
+    for variant in (513, 1536, 4608):
         c1, _, phi1, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, variant))
         assert np.array_equal(phi0, phi1), variant
         assert np.max(np.abs(c1[0, 0] - ref[0])) < 2e-5, variant
