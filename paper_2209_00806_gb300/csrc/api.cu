@@ -1220,7 +1220,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                                c->groups.size() == 1 && g.B == 1 && c->n_samples == 1 &&
                                !c->H.cplx && !c->ac_on && !c->qe_on && c->H.val64 &&
                                c->H.max_width <= kClusterMaxW && n_steps > 0 &&
-                               M - 1 <= kClusterMaxTerms
+                               M - 1 >= 2 && M - 1 <= kClusterMaxTerms
                            ? cluster_blocks_for(c->H.n_rows, c->H.max_width, c->H.uniform)
                            : 0;
         if (Kc > 0) {

@@ -7,8 +7,10 @@
 // thread), gathers x from the owning block's shared memory (distributed
 // shared memory across the cluster), and a cluster barrier separates the
 // Clenshaw terms (Sec. 2.2, Eq. psi_t).  The closing term's sums of
-// <psi0|phi> and <phi|phi> are formed per block in a fixed tree and added
-// over the blocks in rank order by block 0 (FP64, deterministic).  Per row
+// <psi0|phi> and <phi|phi> are formed per block in a fixed tree after the
+// block has arrived at the term's barrier (no later term needs them), and
+// added over the blocks in rank order by block 0 two barriers later (FP64,
+// deterministic).  Per row
 // the arithmetic and its order are those of the plain term kernel, so the
 // states equal the per-term launches' bit for bit; the launch cost of
 // 15 kernels per step is gone.  FP64 states, one state, real values, at most
@@ -48,8 +50,8 @@ constexpr uint32_t kNoEntry = 0xffffffffu;
 
 // MAXW: the widest row the launch allows (its gather addresses stay in
 // registers: 4 for graphene-like lattices, kClusterMaxW otherwise).
-template <int MAXW>
-__global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
+template <int MAXW, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_cluster_steps(ClusterArgs a)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int K = (int)cl.num_blocks();
@@ -104,6 +106,37 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
 
     int cur = a.cur0;
     bool pending = false;                    // a cluster barrier arrived at, not yet waited on
+    // a step whose block parts await block 0's sum, and the barrier waits
+    // until they are all written: the closing term's own barrier completes
+    // before the blocks write their parts, the next one after
+    int sum_step = 0, sum_waits = 0;
+    // block 0, warp 0: lane k loads block k's parts of step m, the lanes'
+    // values are added in rank order; C_m, the norm and the drift checks
+    auto cluster_sum = [&](int m) {
+        double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+        if (t < K) {
+            const double *pk = cl.map_shared_rank(&part[m & 1][0], t);
+            w0 = pk[0];
+            w1 = pk[1];
+            w2 = pk[2];
+        }
+        double sm0 = 0.0, sm1 = 0.0, sm2 = 0.0;
+        for (int k = 0; k < K; ++k) {
+            sm0 += __shfl_sync(0xffffffffu, w0, k);
+            sm1 += __shfl_sync(0xffffffffu, w1, k);
+            sm2 += __shfl_sync(0xffffffffu, w2, k);
+        }
+        if (t == 0) {
+            a.corr[m] = make_double2(sm0, sm1);
+            a.norms[m] = sm2;
+            const double ref = *a.norm_ref;
+            const double drift = ref > 0.0 ? fabs(sm2 / ref - 1.0) : sm2;
+            if (!(sm2 == sm2) || !(sm0 == sm0) || !(sm1 == sm1) || sm2 - sm2 != 0.0)
+                atomicOr(a.err, 2);
+            else if (drift > a.hard_bound)
+                atomicOr(a.err, 1);
+        }
+    };
     for (int n = 1; n <= a.n_steps; ++n) {
         const FusedTerm *tt = tab + cur * a.J;
         for (int j = 0; j < a.J; ++j) {
@@ -116,16 +149,20 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
             const int xoff = xb * R;
             const uint32_t xoff_b = (uint32_t)xoff * (uint32_t)sizeof(double2);
             double2 o;
+            // one-value form: its first product, fma(c, psi, z), needs nothing
+            // of this term's x, so it runs before the barrier wait
+            double re = 0.0, im = 0.0;
+            if (a.uniform) {
+                re = fma(tm.c_hi, p.x, zz.x);
+                im = fma(tm.c_hi, p.y, zz.y);
+            }
+            if (pending) cl.barrier_wait();      // the gathered vector is complete
+            pending = false;
+            if (sum_waits > 0 && --sum_waits == 0 && rank == 0 && t < 32) cluster_sum(sum_step);
             if (a.uniform) {
                 // the one-value form of the per-term kernels: neighbours summed
                 // in stored order (padding only after a row's entries), then
-                // fma(gh, s, fma(gd, x_r, fma(c, psi, z))) -- whose first
-                // product needs nothing of this term's x, so it runs before
-                // the barrier wait
-                double re = fma(tm.c_hi, p.x, zz.x);
-                double im = fma(tm.c_hi, p.y, zz.y);
-                if (pending) cl.barrier_wait();  // the gathered vector is complete
-                pending = false;
+                // fma(gh, s, fma(gd, x_r, fma(c, psi, z)))
                 double2 sm = make_double2(0.0, 0.0);
                 if (gsrc[0] != kNoEntry) sm = ld_cluster(gsrc[0] + xoff_b);
 #pragma unroll
@@ -147,8 +184,6 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
                 o.x = fma(tm.gh, sm.y, re);
                 o.y = fma(-tm.gh, sm.x, im);
             } else {
-                if (pending) cl.barrier_wait();
-                pending = false;
                 // y = H~ x in the plain kernel's order: diagonal, then the entries
                 // (a zero diagonal contributes only signed zeros: skipped, the
                 // sums stay equal to the plain kernel's)
@@ -167,13 +202,19 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
                         y.y = fma(h, x.y, y.y);
                     }
                 }
-                const double re = fma(tm.gamma, y.y, zz.x);
-                const double im = fma(-tm.gamma, y.x, zz.y);
+                re = fma(tm.gamma, y.y, zz.x);
+                im = fma(-tm.gamma, y.x, zz.y);
                 o.x = fma(tm.c_hi, p.x, re);
                 o.y = fma(tm.c_hi, p.y, im);
             }
             vec[(1 + tm.out) * R + t] = o;
+            cl.barrier_arrive();                 // release this term's writes
+            pending = true;
             if (tm.final_term) {
+                // the step's sums, off the critical path: nothing of the next
+                // terms needs them, so they are formed while the other blocks
+                // reach the barrier; block 0 adds the blocks' parts two
+                // barriers on (part is double-buffered by step parity)
                 const double2 p0 = vec[t];
                 double v0 = fma(p0.x, o.x, p0.y * o.y);
                 double v1 = fma(p0.x, o.y, -(p0.y * o.x));
@@ -209,41 +250,21 @@ __global__ void __launch_bounds__(1024, 1) k_cluster_steps(ClusterArgs a)
                         part[n & 1][2] = s2;
                     }
                 }
+                sum_step = n;
+                sum_waits = 2;
             }
-            cl.barrier_arrive();                 // release this term's writes
-            pending = true;
         }
-        if (pending) cl.barrier_wait();          // the step's sums are in place
-        pending = false;
         cur = a.next_cur[cur];
-        // block 0 adds the blocks' sums in rank order (they stay in place for
-        // the next two steps, so no further barrier is needed here): lane k
-        // of warp 0 loads block k's, the lanes' values are added in order
-        if (rank == 0 && t < 32) {
-            double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-            if (t < K) {
-                const double *pk = cl.map_shared_rank(&part[n & 1][0], t);
-                w0 = pk[0];
-                w1 = pk[1];
-                w2 = pk[2];
-            }
-            double s[3] = {0.0, 0.0, 0.0};
-            for (int k = 0; k < K; ++k) {
-                s[0] += __shfl_sync(0xffffffffu, w0, k);
-                s[1] += __shfl_sync(0xffffffffu, w1, k);
-                s[2] += __shfl_sync(0xffffffffu, w2, k);
-            }
-            if (t == 0) {
-                a.corr[n] = make_double2(s[0], s[1]);
-                a.norms[n] = s[2];
-                const double ref = *a.norm_ref;
-                const double drift = ref > 0.0 ? fabs(s[2] / ref - 1.0) : s[2];
-                if (!(s[2] == s[2]) || !(s[0] == s[0]) || !(s[1] == s[1]) || s[2] - s[2] != 0.0)
-                    atomicOr(a.err, 2);
-                else if (drift > a.hard_bound)
-                    atomicOr(a.err, 1);
-            }
-        }
+    }
+    // the last step's parts: its closing barrier, one more, then block 0 adds them
+    if (pending) {
+        cl.barrier_wait();
+        if (sum_waits > 0) --sum_waits;
+    }
+    pending = false;
+    if (sum_waits > 0) {
+        cl.sync();
+        if (rank == 0 && t < 32) cluster_sum(sum_step);
     }
     a.bufs[cur][r] = vec[(1 + cur) * R + t];
     cl.sync();                                           // no block leaves while others read it
@@ -259,7 +280,7 @@ int cluster_blocks_for(int64_t n_rows, int max_w, int uniform)
     static int best16 = -1;
     if (best16 < 0) {
         best16 = 0;
-        if (cudaFuncSetAttribute(k_cluster_steps<kClusterMaxW>,
+        if (cudaFuncSetAttribute(k_cluster_steps<kClusterMaxW, 1024>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at;
@@ -273,9 +294,9 @@ int cluster_blocks_for(int64_t n_rows, int max_w, int uniform)
             cfg.attrs = &at;
             cfg.numAttrs = 1;
             int n = 0;
-            cudaFuncSetAttribute(k_cluster_steps<kClusterMaxW>,
+            cudaFuncSetAttribute(k_cluster_steps<kClusterMaxW, 1024>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-            if (cudaOccupancyMaxActiveClusters(&n, k_cluster_steps<kClusterMaxW>, &cfg) ==
+            if (cudaOccupancyMaxActiveClusters(&n, k_cluster_steps<kClusterMaxW, 1024>, &cfg) ==
                     cudaSuccess &&
                 n >= 1)
                 best16 = 1;
@@ -292,14 +313,14 @@ int cluster_blocks_for(int64_t n_rows, int max_w, int uniform)
     return fits(8) ? 8 : 0;
 }
 
-template <int MAXW>
+template <int MAXW, int MAXT>
 cudaError_t launch_cluster_t(const ClusterArgs &a, int K, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_cluster_steps<MAXW>,
+    cudaError_t e = cudaFuncSetAttribute(k_cluster_steps<MAXW, MAXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (K > 8) {
-        e = cudaFuncSetAttribute(k_cluster_steps<MAXW>,
+        e = cudaFuncSetAttribute(k_cluster_steps<MAXW, MAXT>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
@@ -315,7 +336,7 @@ cudaError_t launch_cluster_t(const ClusterArgs &a, int K, size_t smem, cudaStrea
     cfg.stream = st;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster_steps<MAXW>, a);
+    return cudaLaunchKernelEx(&cfg, k_cluster_steps<MAXW, MAXT>, a);
 }
 
 cudaError_t launch_cluster_steps(const ClusterArgs &a, int K, cudaStream_t st)
@@ -323,8 +344,12 @@ cudaError_t launch_cluster_steps(const ClusterArgs &a, int K, cudaStream_t st)
     const int R = a.rows_per_cta;
     const size_t smem = (size_t)4 * R * sizeof(double2) + (size_t)a.max_w * R * sizeof(int32_t) +
                         (a.uniform ? 0 : (size_t)a.max_w * R * sizeof(double));
-    return a.max_w <= 4 ? launch_cluster_t<4>(a, K, smem, st)
-                        : launch_cluster_t<kClusterMaxW>(a, K, smem, st);
+    // up to 512 rows per block: 128 registers a thread, else 64
+    if (R <= 512)
+        return a.max_w <= 4 ? launch_cluster_t<4, 512>(a, K, smem, st)
+                            : launch_cluster_t<kClusterMaxW, 512>(a, K, smem, st);
+    return a.max_w <= 4 ? launch_cluster_t<4, 1024>(a, K, smem, st)
+                        : launch_cluster_t<kClusterMaxW, 1024>(a, K, smem, st);
 }
 
 }  // namespace tbpm
