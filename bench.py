@@ -600,7 +600,7 @@ def run_tbg(args):
     M = len(tb.tbpm_bessel_coefficients(z))
     units_per_step = ds.n_orb * S * NT * (M - 1)
     prop = tb.Propagator(local, stream.cuda_stream)
-    variant = N.TBPM_VARIANT_ZIGZAG | (N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE
+    variant = N.TBPM_VARIANT_ZIGZAG | (N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_STAGED
                                        if not args.no_halo else N.TBPM_VARIANT_WIDE)
     tau = z / s
 

@@ -53,7 +53,7 @@ def test_gpu_tbg_600nm_first_steps_against_oracle(tb, ref600):
     ds = tbg.twisted_bilayer(600.0, device=dev)
     theta = rng.phases_torch(workloads.master_seed(5), 8, ds.n_orb, device=dev)
     c32, n32, st = _run(tb, ds, theta, 1, N.TBPM_BUILD_NO_FP64 | N.TBPM_BUILD_NO_BOND_MAP,
-                        variant=N.TBPM_VARIANT_ZIGZAG | N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_PIPE)
+                        variant=N.TBPM_VARIANT_ZIGZAG | N.TBPM_VARIANT_HALO | N.TBPM_VARIANT_STAGED)
     c64, n64, _ = _run(tb, ds, theta, 0, N.TBPM_BUILD_NO_FP32 | N.TBPM_BUILD_NO_BOND_MAP)
     assert st["n_rows"] >= ds.n_orb > 2.7e7
     smp = tbg.to_numpy_sample(ds)
@@ -81,7 +81,7 @@ def test_gpu_tbg_1200nm_builds_and_propagates(tb, ref600):
         del ds                                  # the library keeps its own copy
         torch.cuda.empty_cache()
         p.launch_config(1, 8, 64, N.TBPM_VARIANT_ZIGZAG | N.TBPM_VARIANT_HALO |
-                        N.TBPM_VARIANT_PIPE)
+                        N.TBPM_VARIANT_STAGED)
         p.set_phase_states(theta)
         c = p.propagate(Z, 2, 1)
         nrm, st = p.norms(), p.stats()
