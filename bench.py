@@ -546,9 +546,13 @@ def pinned_copy(t):
     """A page-locked host copy of the device tensor t, and the call that
     unpins it: an exact-size numpy buffer registered with cudaHostRegister
     (the caching pinned allocator would round a 30 GB request up to
-    32 GiB), filled by one device-to-host copy."""
+    32 GiB), filled by one device-to-host copy.  The buffer is written by
+    the CPU before it is registered, so that it is backed by the host's
+    large pages: registered untouched, it copied to the device at ~9 GB/s
+    instead of ~200 GB/s."""
     import torch
     a = np.empty(t.numel(), dtype=torch.empty(0, dtype=t.dtype).numpy().dtype)
+    a.fill(0)
     h = torch.from_numpy(a)
     cudart = torch.cuda.cudart()
     nbytes = h.numel() * h.element_size()
