@@ -208,12 +208,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster_steps(ClusterArgs a)
                 o.y = fma(tm.c_hi, p.y, im);
             }
             vec[(1 + tm.out) * R + t] = o;
-            // release this term's writes: the block's threads meet, one
-            // thread orders their stores at cluster scope, then every thread
-            // arrives without a fence of its own
-            __syncthreads();
-            if (t == 0) asm volatile("fence.acq_rel.cluster;" ::: "memory");
-            asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+            cl.barrier_arrive();                 // release this term's writes
             pending = true;
             if (tm.final_term) {
                 // the step's sums, off the critical path: nothing of the next
