@@ -61,6 +61,7 @@ TBPM_VARIANT_HALO = 512
 TBPM_VARIANT_PIPE = 1024
 TBPM_VARIANT_CLUSTER = 2048
 TBPM_VARIANT_STAGED = 4096
+TBPM_VARIANT_PREFETCH = 8192
 
 
 class TbpmError(RuntimeError):

@@ -667,7 +667,7 @@ extern "C" int tbpm_set_launch_config(tbpm_ctx *c, int precision, int max_group,
     if (variant < 0 || variant > (kVariantZigZag | kVariantStreamHints | kVariantTma | kVariantFused |
                                   (3 << kVariantFusedTileShift) | kVariantWide | kVariantSplit2 |
                                   kVariantSplit4 | kVariantHalo | kVariantPipe |
-                                  kVariantCluster | kVariantStaged) ||
+                                  kVariantCluster | kVariantStaged | kVariantPrefetch) ||
         ((variant >> kVariantFusedTileShift) & 3) == 3 ||
         ((variant & kVariantSplit2) && (variant & kVariantSplit4)))
         return fail(c, TBPM_E_INVALID_ARG, "unknown launch variant bits");
@@ -1866,6 +1866,8 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                                 kVariantZigZag | kVariantHalo | kVariantPipe,
                                 kVariantHalo | kVariantStaged,
                                 kVariantZigZag | kVariantHalo | kVariantStaged,
+                                kVariantZigZag | kVariantPrefetch,
+                                kVariantZigZag | kVariantWide | kVariantPrefetch,
                                 kVariantZigZag | kVariantCluster};
     double best = 1e300;
     int bg = c->max_group[precision], bt = c->threads[precision], bv = c->variant[precision];
@@ -1884,6 +1886,8 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                     (c->H.bandwidth > (1 << 16) || c->H.n_rows > (1 << 22)))
                     continue;
                 if ((V & kVariantTma) && c->H.n_rows > (1 << 24)) continue;
+                // the register-pipelined kernel is FP32, real values
+                if ((V & kVariantPrefetch) && (precision != TBPM_FP32 || c->H.cplx)) continue;
                 // the cluster stepping takes one FP64 state of a small real sample
                 if ((V & kVariantCluster) &&
                     (T != thread_opts[0] || precision != TBPM_FP64 || B != 1 || c->H.cplx ||

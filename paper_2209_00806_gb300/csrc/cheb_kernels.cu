@@ -486,6 +486,159 @@ __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 4) : (SP
     if (part == 0) st<V, L, SPL>(a.out, r, l, o);
 }
 
+// Register-pipelined term (TBPM_VARIANT_PREFETCH; FP32, real values): a
+// persistent grid whose threads walk rows with a stride (in zig-zag order
+// when asked).  A row's first four column indices, their values and its
+// diagonal are loaded one row ahead, so the row's own-row loads and its
+// gathers leave together instead of the gathers waiting on the column
+// loads.  Per row the arithmetic and its order are term_row's (plain
+// kernel): the states are bit-identical to it.
+template <typename V>
+struct RowAhead {
+    int64_t base;
+    int w;
+    int32_t c[4];
+    V h[4];
+    V d;
+};
+
+template <typename V, int L, int SPL>
+__device__ __forceinline__ void row_ahead(const TermArgs &a, int64_t r, RowAhead<V> &n)
+{
+    const int64_t q = r / kSliceRows;
+    const int lr = (int)(r % kSliceRows);
+    if (a.fixed_width) {
+        n.w = a.fixed_width;
+        n.base = q * (kSliceRows * (int64_t)n.w);
+    } else {
+        n.base = __ldg(a.H.slice_ptr + q);
+        n.w = (int)((__ldg(a.H.slice_ptr + q + 1) - n.base) / kSliceRows);
+    }
+    const int32_t *colp = a.H.col + n.base + lr;
+    const V *valp = reinterpret_cast<const V *>(a.H.val) + n.base + lr;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const bool ok = u < n.w;
+        n.c[u] = ok ? __ldg(colp + (int64_t)u * kSliceRows) : (int32_t)r;
+        n.h[u] = a.uniform ? Coef<V>::hu(a) : (ok ? __ldg(valp + (int64_t)u * kSliceRows) : (V)0);
+    }
+    n.d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+}
+
+template <typename V, int L, int SPL>
+__global__ void __launch_bounds__(256, SPL <= 2 ? 4 : 3) k_term_pf(TermArgs a)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t rows_per_pass = (int64_t)gridDim.x * blockDim.x / L;
+    const int l = (int)(t % L);
+    int64_t i = t / L;                                   // position in traversal order
+    auto row_of = [&](int64_t k) { return a.reverse ? a.n_rows - 1 - k : k; };
+    RowAhead<V> cur;
+    if (i < a.n_rows) row_ahead<V, L, SPL>(a, row_of(i), cur);
+    for (; i < a.n_rows; i += rows_per_pass) {
+        const int64_t r = row_of(i);
+        Cv<V, SPL> p, zz;
+        if (a.variant & kVariantStreamHints) {
+            p = ld_cs<V, L, SPL>(a.psi, r, l);
+            if (a.z) zz = ld_cs<V, L, SPL>(a.z, r, l);
+        } else {
+            p = ld_ro<V, L, SPL>(a.psi, r, l);
+            if (a.z) zz = ld<V, L, SPL>(a.z, r, l);
+        }
+        if (!a.z) {
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) { zz.re[j] = 0; zz.im[j] = 0; }
+        }
+        Cv<V, SPL> y = ld_ro<V, L, SPL>(a.x, r, l);
+        Cv<V, SPL> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ld_ro<V, L, SPL>(a.x, cur.c[u], l);
+        // the next row's indices, values and diagonal, in flight meanwhile
+        RowAhead<V> nxt;
+        const int64_t i2 = i + rows_per_pass;
+        if (i2 < a.n_rows) row_ahead<V, L, SPL>(a, row_of(i2), nxt);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) { y.re[j] *= cur.d; y.im[j] *= cur.d; }
+        // the first four entries (as term_row's first round), then the rest
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ok[u] = u < cur.w;
+            if (a.uniform) ok[u] = ok[u] && cur.c[u] != (int32_t)r;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) {
+                    y.re[j] = fma(cur.h[u], xv[u].re[j], y.re[j]);
+                    y.im[j] = fma(cur.h[u], xv[u].im[j], y.im[j]);
+                }
+            }
+        }
+        const int64_t lr = r % kSliceRows;
+        for (int k = 4; k < cur.w; k += 4) {
+            int32_t c[4];
+            V h[4];
+            bool okk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ku = k + u;
+                okk[u] = ku < cur.w;
+                c[u] = okk[u] ? __ldg(a.H.col + cur.base + lr + (int64_t)ku * kSliceRows)
+                              : (int32_t)r;
+                if (a.uniform) {
+                    okk[u] = okk[u] && c[u] != (int32_t)r;
+                    h[u] = Coef<V>::hu(a);
+                } else {
+                    h[u] = okk[u] ? __ldg(reinterpret_cast<const V *>(a.H.val) + cur.base + lr +
+                                          (int64_t)ku * kSliceRows)
+                                  : (V)0;
+                }
+            }
+            Cv<V, SPL> xw[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xw[u] = ld_ro<V, L, SPL>(a.x, c[u], l);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (okk[u]) {
+#pragma unroll
+                    for (int j = 0; j < SPL; ++j) {
+                        y.re[j] = fma(h[u], xw[u].re[j], y.re[j]);
+                        y.im[j] = fma(h[u], xw[u].im[j], y.im[j]);
+                    }
+                }
+            }
+        }
+        const V *sc = Coef<V>::scale(a);
+        if (sc) {
+            sc += (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                const V s = sc[l * SPL + j];
+                p.re[j] *= s;
+                p.im[j] *= s;
+                if (a.x_is_psi) { y.re[j] *= s; y.im[j] *= s; }
+            }
+        }
+        const V g = Coef<V>::g(a), ch = Coef<V>::hi(a), cl = Coef<V>::lo(a);
+        Cv<V, SPL> o;
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            V re = fma(g, y.im[j], zz.re[j]);
+            V im = fma(-g, y.re[j], zz.im[j]);
+            if (sizeof(V) == 4) {
+                re = fma(cl, p.re[j], re);
+                im = fma(cl, p.im[j], im);
+            }
+            o.re[j] = fma(ch, p.re[j], re);
+            o.im[j] = fma(ch, p.im[j], im);
+        }
+        st<V, L, SPL>(a.out, r, l, o);
+        cur = nxt;
+    }
+}
+
 // Closing term, one row per thread like k_term, with the sums of
 // <psi0|out> and <out|out> per state into one partial per block, then the
 // last block of each kChunkRows chunk (atomic ticket after a fence) adds the
@@ -1519,6 +1672,46 @@ cudaError_t launch_term_t(const TermArgs &a, int threads, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The register-pipelined kernel: a persistent grid of the SMs times the
+// blocks that fit on one, at most one thread per lane-row.
+template <typename V, int L, int SPL>
+cudaError_t launch_term_pf_t(const TermArgs &a, int threads, cudaStream_t st)
+{
+    static int occ[4] = {0, 0, 0, 0};            // resident blocks per SM by threads 64 .. 512
+    const int ti = threads <= 64 ? 0 : threads <= 128 ? 1 : threads <= 256 ? 2 : 3;
+    if (!occ[ti]) {
+        int nb = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_term_pf<V, L, SPL>, threads, 0) !=
+            cudaSuccess)
+            nb = 1;
+        occ[ti] = std::max(1, nb);
+    }
+    const int64_t n_threads = a.n_rows * L;
+    const int64_t want = (n_threads + threads - 1) / threads;
+    const unsigned blocks = (unsigned)std::min<int64_t>((int64_t)a.num_sms * occ[ti], want);
+    k_term_pf<V, L, SPL><<<blocks, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_pf(const TermArgs &a, int B, int threads, cudaStream_t st)
+{
+    if (a.variant & kVariantWide) {
+        switch (B) {
+        case 4: return launch_term_pf_t<float, 1, 4>(a, threads, st);
+        case 8: return launch_term_pf_t<float, 2, 4>(a, threads, st);
+        case 16: return launch_term_pf_t<float, 4, 4>(a, threads, st);
+        }
+    }
+    switch (B) {
+    case 1: return launch_term_pf_t<float, 1, 1>(a, threads, st);
+    case 2: return launch_term_pf_t<float, 1, 2>(a, threads, st);
+    case 4: return launch_term_pf_t<float, 2, 2>(a, threads, st);
+    case 8: return launch_term_pf_t<float, 4, 2>(a, threads, st);
+    case 16: return launch_term_pf_t<float, 8, 2>(a, threads, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 // Row-split launch (real values, interior terms): RS from the variant bits.
 template <typename V, int L, int SPL>
 cudaError_t launch_term_split(const TermArgs &a, int threads, cudaStream_t st)
@@ -1655,6 +1848,10 @@ bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    // the register-pipelined kernel: FP32, real values, unsplit rows
+    if ((a.variant & kVariantPrefetch) && fp32 && !a.cplx && !(a.variant & kVariantHalo) &&
+        !(a.variant & (kVariantSplit2 | kVariantSplit4)))
+        return dispatch_pf(a, B, threads, st);
     // the one-stage staged kernel, like the pipelined one, keeps rows unsplit
     if ((a.variant & kVariantHalo) && (a.variant & kVariantStaged) && a.lcol && !a.cplx &&
         (a.vpack || a.uniform) && !(a.variant & (kVariantSplit2 | kVariantSplit4)) &&

@@ -73,6 +73,7 @@ constexpr int kVariantHalo = 512;       // gathers from a shared-memory copy of 
 constexpr int kVariantPipe = 1024;      // with kVariantHalo: persistent, two stages in flight
 constexpr int kVariantCluster = 2048;   // small FP64 samples: all steps in one cluster launch
 constexpr int kVariantStaged = 4096;    // with kVariantHalo: one stage, two blocks per SM
+constexpr int kVariantPrefetch = 8192;  // FP32: persistent term kernel, next row's indices loaded ahead
 
 // Staged-gather term kernel: rows per block, and the most other rows one
 // block may reference (16-bit positions; the shared copy is sized by the

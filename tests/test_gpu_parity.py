@@ -169,7 +169,7 @@ def test_gpu_autotune_picks_a_valid_shape(tb):
         best = p.autotune(Z, precision=1, probe_steps=2)
         assert best["group"] in (2, 4) and best["threads"] in (64, 128, 256)
         assert best["variant"] in (0, 1, 3, 4, 5, 8, 24, 40, 65, 129, 257, 193, 321, 512, 513,
-                                   1536, 1537, 4608, 4609)
+                                   1536, 1537, 4608, 4609, 8193, 8257)
         assert best["ms_per_step"] > 0
         c = p.propagate(Z, 30, 1)
     ref = run_oracle(smp, 9.5, th, 30)
@@ -282,18 +282,19 @@ def test_gpu_graph_mode_and_determinism(tb):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_gpu_tma_kernel_is_bit_identical(tb, prec):
     """The TMA-staged term kernel does the same arithmetic in the same order;
-    the wide-lane kernels the same arithmetic per row (bit-identical states)
-    with the closing sums grouped by other blocks (C within rounding)."""
+    the wide-lane and the register-pipelined kernels (8193, 8257) the same
+    arithmetic per row (bit-identical states) with the closing sums grouped
+    by other blocks (C within rounding)."""
     smp = lattice.graphene(33, 31, pbc=True, seed=6, onsite_w=1.0, vacancy_frac=0.02)
     th = rng.phases(12, 4, smp.n_orb)
     outs = []
-    for variant in (0, 4, 5, 65):
+    for variant in (0, 4, 5, 65, 8193, 8257):
         c, _, phi, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, cfg=(4, 256, variant),
                                flags=2 if variant == 5 else 0)
         outs.append((variant, c, phi))
     for variant, c, phi in outs[1:]:
         assert np.array_equal(phi, outs[0][2])
-        if variant == 65:
+        if variant in (65, 8193, 8257):
             assert np.max(np.abs(c - outs[0][1])) < (1e-13 if prec == 0 else 1e-6)
         else:
             assert np.array_equal(c, outs[0][1])
@@ -611,8 +612,9 @@ def test_gpu_halo_variant_twisted_bilayer_20nm_fp32(tb):
     th = rng.phases(93, 8, smp.n_orb)
     c0, _, phi0, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 65))
     ref = oracle.propagate_rows(smp, 12.0, Z, 12, oracle.phase_states(th[:1]))
-    for variant in (513, 1536, 4608):
-        c1, _, phi1, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, variant))
+    for variant in (513, 1536, 4608, 8257):       # 8257: rows of 68 entries, beyond the
+        c1, _, phi1, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1,   # four loaded ahead
+                                 cfg=(8, 64, variant))
         assert np.array_equal(phi0, phi1), variant
         assert np.max(np.abs(c1[0, 0] - ref[0])) < 2e-5, variant
     c2, _, phi2, _ = run_gpu(tb, smp, 12.0, th, 12, precision=1, cfg=(8, 64, 193))
