@@ -1065,8 +1065,8 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             base.vpack = c->H.vpack[fp32];
             base.halo_max = c->H.halo_max;
             base.halo_ent_max = c->H.halo_ent_max;
-            base.num_sms = c->num_sms;
         }
+        base.num_sms = c->num_sms;                  // grid of the persistent term kernels
         ReduceArgs ra;
         ra.partial = c->d_partial;
         ra.partial2 = c->d_partial2;

@@ -1688,7 +1688,8 @@ cudaError_t launch_term_pf_t(const TermArgs &a, int threads, cudaStream_t st)
     }
     const int64_t n_threads = a.n_rows * L;
     const int64_t want = (n_threads + threads - 1) / threads;
-    const unsigned blocks = (unsigned)std::min<int64_t>((int64_t)a.num_sms * occ[ti], want);
+    const unsigned blocks =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, a.num_sms) * occ[ti], want));
     k_term_pf<V, L, SPL><<<blocks, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
