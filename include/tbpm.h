@@ -358,7 +358,7 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
                                         positions and values copied while the current
                                         one computes; FP32 groups of 4 or 8, FP64 of 2
                                         or 4 states, within 224 KB of shared memory */
-#define TBPM_VARIANT_PREFETCH 8192   /* FP32, real values, interior terms: a persistent
+#define TBPM_VARIANT_PREFETCH 8192   /* real values, interior terms: a persistent
                                         grid whose threads walk rows with a stride and
                                         load the next row's first four column indices,
                                         values and diagonal before the current row's

@@ -1886,8 +1886,8 @@ extern "C" int tbpm_autotune(tbpm_ctx *c, int precision, double z, int probe_ste
                     (c->H.bandwidth > (1 << 16) || c->H.n_rows > (1 << 22)))
                     continue;
                 if ((V & kVariantTma) && c->H.n_rows > (1 << 24)) continue;
-                // the register-pipelined kernel is FP32, real values
-                if ((V & kVariantPrefetch) && (precision != TBPM_FP32 || c->H.cplx)) continue;
+                // the register-pipelined kernel takes real values
+                if ((V & kVariantPrefetch) && c->H.cplx) continue;
                 // the cluster stepping takes one FP64 state of a small real sample
                 if ((V & kVariantCluster) &&
                     (T != thread_opts[0] || precision != TBPM_FP64 || B != 1 || c->H.cplx ||

@@ -486,13 +486,14 @@ __global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 6 : 4) : (SP
     if (part == 0) st<V, L, SPL>(a.out, r, l, o);
 }
 
-// Register-pipelined term (TBPM_VARIANT_PREFETCH; FP32, real values): a
+// Register-pipelined term (TBPM_VARIANT_PREFETCH; real values): a
 // persistent grid whose threads walk rows with a stride (in zig-zag order
 // when asked).  A row's first four column indices, their values and its
 // diagonal are loaded one row ahead, so the row's own-row loads and its
 // gathers leave together instead of the gathers waiting on the column
 // loads.  Per row the arithmetic and its order are term_row's (plain
-// kernel): the states are bit-identical to it.
+// kernel; in FP64 with one value, term_row_sum's): the states are
+// bit-identical to it.
 template <typename V>
 struct RowAhead {
     int64_t base;
@@ -523,10 +524,13 @@ __device__ __forceinline__ void row_ahead(const TermArgs &a, int64_t r, RowAhead
         n.h[u] = a.uniform ? Coef<V>::hu(a) : (ok ? __ldg(valp + (int64_t)u * kSliceRows) : (V)0);
     }
     n.d = __ldg(reinterpret_cast<const V *>(a.H.diag) + r);
+    if constexpr (sizeof(V) == 8) {              // FP64 one-value form: gamma d
+        if (a.uniform) n.d = a.zero_diag ? 0.0 : gdiag_at(a, r);
+    }
 }
 
 template <typename V, int L, int SPL>
-__global__ void __launch_bounds__(256, SPL <= 2 ? 4 : 3) k_term_pf(TermArgs a)
+__global__ void __launch_bounds__(256, sizeof(V) == 4 ? (SPL <= 2 ? 4 : 3) : 2) k_term_pf(TermArgs a)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t rows_per_pass = (int64_t)gridDim.x * blockDim.x / L;
@@ -557,6 +561,71 @@ __global__ void __launch_bounds__(256, SPL <= 2 ? 4 : 3) k_term_pf(TermArgs a)
         RowAhead<V> nxt;
         const int64_t i2 = i + rows_per_pass;
         if (i2 < a.n_rows) row_ahead<V, L, SPL>(a, row_of(i2), nxt);
+        if constexpr (sizeof(V) == 8) {
+            if (a.uniform) {
+                // FP64 one-value form (term_row_sum): neighbours summed in
+                // stored order, the first valid entry starting the sum
+                Cv<V, SPL> sm;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = u < cur.w && cur.c[u] != (int32_t)r;
+#pragma unroll
+                    for (int j = 0; j < SPL; ++j) {
+                        if (u == 0) {
+                            sm.re[j] = ok ? xv[0].re[j] : 0.0;
+                            sm.im[j] = ok ? xv[0].im[j] : 0.0;
+                        } else if (ok) {
+                            sm.re[j] += xv[u].re[j];
+                            sm.im[j] += xv[u].im[j];
+                        }
+                    }
+                }
+                const int64_t lr0 = r % kSliceRows;
+                for (int k = 4; k < cur.w; k += 4) {
+                    int32_t c[4];
+                    bool okk[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        okk[u] = k + u < cur.w;
+                        c[u] = okk[u] ? __ldg(a.H.col + cur.base + lr0 + (int64_t)(k + u) * kSliceRows)
+                                      : (int32_t)r;
+                        okk[u] = okk[u] && c[u] != (int32_t)r;
+                    }
+                    Cv<V, SPL> xw[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) xw[u] = ld_ro<V, L, SPL>(a.x, c[u], l);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (okk[u]) {
+#pragma unroll
+                            for (int j = 0; j < SPL; ++j) {
+                                sm.re[j] += xw[u].re[j];
+                                sm.im[j] += xw[u].im[j];
+                            }
+                        }
+                    }
+                }
+                const V *sc = Coef<V>::scale(a);
+                if (sc) {
+                    sc += (int64_t)a.chunk_sample[r / kChunkRows] * (L * SPL);
+#pragma unroll
+                    for (int j = 0; j < SPL; ++j) {
+                        const V sv = sc[l * SPL + j];
+                        p.re[j] *= sv;
+                        p.im[j] *= sv;
+                        if (a.x_is_psi) {
+                            sm.re[j] *= sv;
+                            sm.im[j] *= sv;
+                            y.re[j] *= sv;
+                            y.im[j] *= sv;
+                        }
+                    }
+                }
+                st<V, L, SPL>(a.out, r, l, combine_sum<SPL>(a, cur.d, y, sm, p, zz));
+                cur = nxt;
+                continue;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < SPL; ++j) { y.re[j] *= cur.d; y.im[j] *= cur.d; }
         // the first four entries (as term_row's first round), then the rest
@@ -1694,8 +1763,24 @@ cudaError_t launch_term_pf_t(const TermArgs &a, int threads, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_pf(const TermArgs &a, int B, int threads, cudaStream_t st)
+cudaError_t dispatch_pf(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    if (!fp32) {
+        if (a.variant & kVariantWide) {
+            switch (B) {
+            case 2: return launch_term_pf_t<double, 1, 2>(a, threads, st);
+            case 4: return launch_term_pf_t<double, 2, 2>(a, threads, st);
+            case 8: return launch_term_pf_t<double, 4, 2>(a, threads, st);
+            }
+        }
+        switch (B) {
+        case 1: return launch_term_pf_t<double, 1, 1>(a, threads, st);
+        case 2: return launch_term_pf_t<double, 2, 1>(a, threads, st);
+        case 4: return launch_term_pf_t<double, 4, 1>(a, threads, st);
+        case 8: return launch_term_pf_t<double, 8, 1>(a, threads, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (a.variant & kVariantWide) {
         switch (B) {
         case 4: return launch_term_pf_t<float, 1, 4>(a, threads, st);
@@ -1849,10 +1934,10 @@ bool halo_launchable(int fp32, int B, bool final_term, int halo_max)
 
 cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
-    // the register-pipelined kernel: FP32, real values, unsplit rows
-    if ((a.variant & kVariantPrefetch) && fp32 && !a.cplx && !(a.variant & kVariantHalo) &&
+    // the register-pipelined kernel: real values, unsplit rows
+    if ((a.variant & kVariantPrefetch) && !a.cplx && !(a.variant & kVariantHalo) &&
         !(a.variant & (kVariantSplit2 | kVariantSplit4)))
-        return dispatch_pf(a, B, threads, st);
+        return dispatch_pf(a, fp32, B, threads, st);
     // the one-stage staged kernel, like the pipelined one, keeps rows unsplit
     if ((a.variant & kVariantHalo) && (a.variant & kVariantStaged) && a.lcol && !a.cplx &&
         (a.vpack || a.uniform) && !(a.variant & (kVariantSplit2 | kVariantSplit4)) &&
