@@ -1960,6 +1960,15 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
 
 cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
 {
+    // the register-pipelined term writes `out`, then the closing reduction
+    // reads it (states as the plain closing term's, sums in its order)
+    if ((a.variant & kVariantPrefetch) && !a.cplx && !(a.variant & kVariantHalo) && a.H.col) {
+        cudaError_t e = dispatch_pf(a, fp32, B, threads, st);
+        if (e != cudaSuccess) return e;
+        TermArgs r = a;
+        r.H.col = nullptr;
+        return dispatch<true>(r, fp32, B, threads, false, st);
+    }
     if ((a.variant & kVariantHalo) && (a.variant & kVariantStaged) && a.lcol && !a.cplx &&
         (a.vpack || a.uniform) && a.H.col &&
         staged_launchable(fp32, B, a.halo_max, a.halo_ent_max, a.uniform)) {
