@@ -59,7 +59,10 @@ def parse():
                     help="tbg without --autotune: the plain wide-lane kernel instead of the "
                          "staged-gather one")
     ap.add_argument("--variant", type=int, default=None,
-                    help="tbg: launch variant bits (TBPM_VARIANT_*) instead of the autotuner")
+                    help="launch variant bits (TBPM_VARIANT_*) of the FP32 form instead of the "
+                         "autotuner (group of 8 states for tbg, 4 otherwise; 64 threads)")
+    ap.add_argument("--variant64", type=int, default=None,
+                    help="the same for the FP64 form (group of 4 states, 64 threads)")
     ap.add_argument("--L", type=int, default=2048, help="lattice side of the disordered workload")
     ap.add_argument("--time-steps", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
@@ -361,7 +364,11 @@ def run_gb300(args):
     prop.build(smp.n_orb, d_on, d_hi, d_hj, d_hv, w.s, sample_offsets=offsets, flags=bflags)
     prop.set_phase_states(d_th)
     for prec in legs:
-        if args.no_autotune:
+        fixed = args.variant if prec == N.TBPM_FP32 else args.variant64
+        if fixed is not None:
+            prop.launch_config(prec, 4, 64, fixed)
+            tuned[prec] = {"group": 4, "threads": 64, "variant": fixed}
+        elif args.no_autotune:
             tuned[prec] = {"group": "default", "threads": 256, "variant": 1}
         else:
             tuned[prec] = prop.autotune(w.z, precision=prec, probe_steps=3)
@@ -406,7 +413,10 @@ def run_gb300(args):
         ach = b / (r["ms_term"] * 1e-3) / 1e9
         tr, _ = kernel_traffic()
         traffic = None
-        if tr is not None and key in tr and args.workload == "disordered" and args.L == 2048:
+        prec = N.TBPM_FP32 if key == "fp32" else N.TBPM_FP64
+        # the capture's kernel source and launch variant must be this run's
+        if (tr is not None and key in tr and args.workload == "disordered" and args.L == 2048
+                and tr[key].get("variant") == tuned.get(prec, {}).get("variant")):
             traffic = tr[key]["dram_bytes_per_launch_full_size"]
         return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": traffic, "peak_source": peak_note,
