@@ -1291,6 +1291,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
             continue;
         }
 
+        int final_extra = 0;            // launches of the closing term beyond one
         auto run_step = [&](int cur, int *next_cur, bool timed) -> int {
             if (fused) {
                 schedule(a, cur, next_cur);
@@ -1356,9 +1357,11 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 t.scale_f = g.scale_f;
                 one_value_terms(c->H, t.gamma, &t.gh, &t.gdiag, &t.gdiag_sign);
                 cudaError_t e;
-                if (L.final_term)
-                    e = launch_final(t, fp32, g.B, threads, c->st);
-                else if (t.variant & kVariantTma)
+                if (L.final_term) {
+                    int nl = 1;
+                    e = launch_final(t, fp32, g.B, threads, c->st, &nl);
+                    final_extra = nl - 1;         // a term + reduction-pass closing term
+                } else if (t.variant & kVariantTma)
                     e = launch_term_tma(t, fp32, g.B, c->H.max_width, c->d_flags, c->num_sms, c->st);
                 else
                     e = launch_term(t, fp32, g.B, threads, c->st);
@@ -1403,7 +1406,7 @@ extern "C" int tbpm_propagate(tbpm_ctx *c, double z, int n_steps, int precision,
                 if (rc) return rc;
             }
             g.cur = nxt;
-            launches += fused ? 2 : M;   // term kernels (or the fused step) + one reduction
+            launches += fused ? 2 : M + final_extra;   // term kernels (or the fused step) + one reduction
             if (c->ac_on) launches += 2; // observer + its reduction
             if (c->qe_on) launches += 1; // quasi-eigenstate accumulation
         }

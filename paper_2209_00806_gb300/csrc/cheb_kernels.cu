@@ -1958,8 +1958,10 @@ cudaError_t launch_term(const TermArgs &a, int fp32, int B, int threads, cudaStr
     return dispatch<false>(a, fp32, B, threads, true, st);
 }
 
-cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st)
+cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st,
+                         int *n_launch)
 {
+    if (n_launch) *n_launch = 1;
     // the register-pipelined term writes `out`, then the closing reduction
     // reads it (states as the plain closing term's, sums in its order)
     if ((a.variant & kVariantPrefetch) && !a.cplx && !(a.variant & kVariantHalo) && a.H.col) {
@@ -1967,6 +1969,7 @@ cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaSt
         if (e != cudaSuccess) return e;
         TermArgs r = a;
         r.H.col = nullptr;
+        if (n_launch) *n_launch = 2;      // the term, then the reduction pass
         return dispatch<true>(r, fp32, B, threads, false, st);
     }
     if ((a.variant & kVariantHalo) && (a.variant & kVariantStaged) && a.lcol && !a.cplx &&
@@ -1976,6 +1979,7 @@ cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaSt
         if (e != cudaSuccess) return e;
         TermArgs r = a;
         r.H.col = nullptr;
+        if (n_launch) *n_launch = 2;      // the term, then the reduction pass
         return dispatch<true>(r, fp32, B, threads, false, st);
     }
     if ((a.variant & kVariantHalo) && (a.variant & kVariantPipe) && a.lcol && !a.cplx &&
@@ -1988,6 +1992,7 @@ cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaSt
         if (e != cudaSuccess) return e;
         TermArgs r = a;
         r.H.col = nullptr;
+        if (n_launch) *n_launch = 2;      // the term, then the reduction pass
         return dispatch<true>(r, fp32, B, threads, false, st);
     }
     if ((a.variant & kVariantHalo) && a.lcol && !a.cplx && a.H.col &&

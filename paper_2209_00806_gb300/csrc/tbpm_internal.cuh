@@ -253,7 +253,8 @@ bool halo_launchable(int fp32, int B, bool final_term, int halo_max);
 bool pipe_launchable(int fp32, int B, int halo_max, int ent_max, int uniform);
 // The one-stage staged-gather kernel (kVariantStaged) for that shape.
 bool staged_launchable(int fp32, int B, int halo_max, int ent_max, int uniform);
-cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st);
+cudaError_t launch_final(const TermArgs &a, int fp32, int B, int threads, cudaStream_t st,
+                         int *n_launch = nullptr);   // kernels it launched (1 or 2)
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 // State average of the correlations (and its adjoint, a broadcast of
 // dL/dC-bar / S), complex128 [n_samples][S][n1] <-> [n_samples][n1].

@@ -289,9 +289,12 @@ def test_gpu_tma_kernel_is_bit_identical(tb, prec):
     th = rng.phases(12, 4, smp.n_orb)
     outs = []
     for variant in (0, 4, 5, 65, 8193, 8257):
-        c, _, phi, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, cfg=(4, 256, variant),
-                               flags=2 if variant == 5 else 0)
+        c, st, phi, _ = run_gpu(tb, smp, 9.5, th, 40, precision=prec, cfg=(4, 256, variant),
+                                flags=2 if variant == 5 else 0)
         outs.append((variant, c, phi))
+        if variant == 8257:     # states, C_0 term + reduce; per step 15 terms, the closing
+            # one as the pipelined term + the reduction pass, and the reduce
+            assert st["kernel_launches"] == 3 + 40 * 17
     for variant, c, phi in outs[1:]:
         assert np.array_equal(phi, outs[0][2])
         if variant in (65, 8193, 8257):
