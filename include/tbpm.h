@@ -320,7 +320,9 @@ int tbpm_dos_adjoint(const double *dl_dd, int n_e, int n_steps, double tau, int 
  * FP32 <= 16), each group propagated as one blocked sparse product per term;
  * threads per block is 64, 128 or 256; variant is a set of
  * TBPM_VARIANT_* bits.  Chosen by tbpm_autotune or by hand.  Changing the
- * width or block size drops the current propagation buffers. */
+ * width or block size drops the current propagation buffers.  Defaults:
+ * groups of 8 (FP64) and 16 (FP32) states, 64 threads, variants ZIGZAG (FP64)
+ * and ZIGZAG | WIDE | PREFETCH (FP32). */
 #define TBPM_VARIANT_ZIGZAG 1        /* alternate the row traversal direction per term,
                                         so each term starts on rows still in L2 */
 #define TBPM_VARIANT_STREAM_HINTS 2  /* evict-first loads of the own-row streams */

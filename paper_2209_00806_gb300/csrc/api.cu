@@ -56,7 +56,7 @@ struct tbpm_ctx {
     int threads[2] = {64, 64};   // threads per block per precision (fastest on GB300)
     // term-kernel launch variants (FP64, FP32): the fastest on GB300 for
     // graphene-like lattices; tbpm_autotune re-checks for the actual matrix
-    int variant[2] = {kVariantZigZag, kVariantZigZag | kVariantWide};
+    int variant[2] = {kVariantZigZag, kVariantZigZag | kVariantWide | kVariantPrefetch};
     int num_sms = 0;
     double renorm_fp32 = 1e-5, hard_fp32 = 1e-2, hard_fp64 = 1e-6;   // norm policy
     std::vector<Group> groups;
