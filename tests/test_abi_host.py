@@ -27,6 +27,18 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(tbpm_[a-z_0-9]+)\s*\(", text)))
 
 
+def test_binding_constants_match_the_header(native):
+    """Every integer TBPM_* constant of the header has the same value in the
+    Python binding (variant bits, build and propagation flags, statuses)."""
+    text = (ROOT / "include" / "tbpm.h").read_text()
+    defs = dict(re.findall(r"#define\s+(TBPM_[A-Z0-9_]+)\s+(-?\d+)\b", text))
+    assert len(defs) > 20
+    missing = [k for k in defs if not hasattr(native, k)]
+    assert not missing, missing
+    wrong = {k: (v, getattr(native, k)) for k, v in defs.items() if getattr(native, k) != int(v)}
+    assert not wrong, wrong
+
+
 def test_library_exports_every_declared_symbol(native):
     names = declared_functions()
     assert len(names) >= 14
