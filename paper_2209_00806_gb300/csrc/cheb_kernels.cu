@@ -834,6 +834,90 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(TermArgs a)
     final_reduce<V, L, SPL, kFinalThreads / L>(a, bid, threadIdx.x / L, l, o, p0);
 }
 
+// Reduction-only closing pass, FP32 (after a term kernel that wrote `out`,
+// and the C_0 pass): RPT rows per thread (rows lrow, lrow + ROWS, ... of the
+// block's ROWS * RPT), each row's <psi0|phi> and <phi|phi> terms exact float
+// pairs added in registers, then the block's threads through a [row][value]
+// table in fixed parts as in final_reduce, one FP64 partial per block and
+// the chunk tickets.  The block-table phases then serve RPT times the rows.
+template <int L, int SPL, int RPT>
+__global__ void __launch_bounds__(kFinalThreads) k_final_sums(TermArgs a)
+{
+    constexpr int B = L * SPL;
+    constexpr int ROWS = kFinalThreads / L;          // thread-rows of a block
+    constexpr int NV = B * 3;
+    constexpr int P = kFinalThreads / NV;            // parts per value
+    __shared__ FF redf[ROWS * NV];
+    __shared__ FF redp[P * NV];
+    __shared__ double tot[NV];
+    __shared__ int last;
+    const int64_t bid = block_in_order(a);
+    const int lrow = threadIdx.x / L, l = threadIdx.x % L;
+    const int64_t r0 = bid * (int64_t)(ROWS * RPT) + lrow;
+    FF acc[SPL][3];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int64_t r = r0 + (int64_t)k * ROWS;
+        const Cv<float, SPL> o = ld<float, L, SPL>(a.out, r, l);
+        const Cv<float, SPL> p0 = ld_ro<float, L, SPL>(a.psi0, r, l);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            FF re, im, nr;
+            ff_dot3(p0.re[j], p0.im[j], o.re[j], o.im[j], re, im, nr);
+            if (k == 0) {
+                acc[j][0] = re;
+                acc[j][1] = im;
+                acc[j][2] = nr;
+            } else {
+                acc[j][0] = ff_add(acc[j][0], re);
+                acc[j][1] = ff_add(acc[j][1], im);
+                acc[j][2] = ff_add(acc[j][2], nr);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+        const int v = (l * SPL + j) * 3;
+        redf[lrow * NV + v + 0] = acc[j][0];
+        redf[lrow * NV + v + 1] = acc[j][1];
+        redf[lrow * NV + v + 2] = acc[j][2];
+    }
+    __syncthreads();
+    if (threadIdx.x < P * NV) {
+        const int v = threadIdx.x % NV, part = threadIdx.x / NV;
+        FF s = redf[part * NV + v];
+        for (int row = part + P; row < ROWS; row += P) s = ff_add(s, redf[row * NV + v]);
+        redp[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        FF s = redp[threadIdx.x];
+        for (int part = 1; part < P; ++part) s = ff_add(s, redp[part * NV + threadIdx.x]);
+        tot[threadIdx.x] = ff_to_double(s);
+    }
+    __syncthreads();
+    constexpr int per_chunk = kChunkRows / (ROWS * RPT);   // blocks per chunk
+    const int64_t chunk = bid / per_chunk;
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < NV; ++v) a.block_partial[bid * NV + v] = tot[v];
+        __threadfence();
+        const int ticket = atomicAdd(a.chunk_count + chunk, 1);
+        last = (ticket == per_chunk - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x < NV) {
+            double sum = 0.0;
+            const int64_t b0 = chunk * per_chunk;
+            for (int k = 0; k < per_chunk; ++k)
+                sum += __ldcg(a.block_partial + (b0 + k) * NV + threadIdx.x);
+            a.partial[chunk * NV + threadIdx.x] = sum;
+        }
+        if (threadIdx.x == 0) a.chunk_count[chunk] = 0;     // ready for the next launch
+    }
+}
+
 // ---- staged-gather term (TBPM_VARIANT_HALO) --------------------------------
 // A block of kHaloRows rows first copies its halo -- the x lanes of its own
 // rows, then of every other row its entries reference -- into shared memory
@@ -1810,6 +1894,14 @@ template <typename V, int L, int SPL, bool CX>
 cudaError_t launch_final_t(const TermArgs &a, int threads, bool compute, cudaStream_t st)
 {
     (void)threads;   // the closing term has its own block size
+    if constexpr (sizeof(V) == 4 && !CX) {
+        if (!compute) {           // FP32 reduction-only pass: four rows a thread
+            constexpr int RPT = 4;
+            const unsigned rblocks = (unsigned)(a.n_rows * L / (kFinalThreads * RPT));
+            k_final_sums<L, SPL, RPT><<<rblocks, kFinalThreads, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     const unsigned blocks = (unsigned)(a.n_rows * L / kFinalThreads);
     if (compute)
         k_final<V, L, SPL, true, CX><<<blocks, kFinalThreads, 0, st>>>(a);
