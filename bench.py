@@ -492,6 +492,8 @@ def run_gb300(args):
             "data": "synthetic", "config": cfg,
             "roofline": roofline(r0, name[head]),
             "e2e": e2e, "gpu_launches": int(r0["launches"]),
+            "gpu_launches_counts": "the propagation's kernels (tbpm_stats.kernel_launches); the "
+                                   "Hamiltonian build's ~20 kernels per step are not counted",
             "clocks": r0["clocks"], "cpu_baseline": cpu,
         }
         de = float(r0["res"][0][1] - r0["res"][0][0])
